@@ -1,0 +1,246 @@
+/*
+ * qeq.h -- C ABI of the GB300 shadow charge-equilibration Coulomb library.
+ *
+ * The library evaluates the periodic Coulomb potential operator v = Phi q and
+ * its field on one GPU.  Kaymak et al., "GPU-Accelerated Charge-Equilibration
+ * for Shadow Molecular Dynamics in Python" (arXiv 2503.21176), needs it several
+ * times per shadow MD step (Sec. 3.4 matrix-free C v = u o v + dE_Coul/dv;
+ * Sec. 3.5).  The library also advances that shadow XL-BOMD step.
+ *
+ * Conventions for every call:
+ *  - Array arguments are DEVICE pointers owned by the caller, unless a comment
+ *    says "host".  Positions are row-major [N][3] doubles.  Per-atom scalars are
+ *    [N] doubles.  The library never frees or keeps caller memory past the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is queued on it and the call returns without waiting,
+ *    except where a comment says the call synchronises.
+ *  - The ABI is FP64.  With QEQ_FP32_MIXED the pair sum, spreading, FFT and
+ *    gather run in FP32 internally, and the inputs and outputs stay FP64.
+ *  - Return value: QEQ_OK (0) or a negative QEQ_ERR_* code.  qeq_last_error()
+ *    returns a message for the last failing call on that context.  No C++
+ *    exception crosses the ABI.
+ *  - Units follow the caller.  The water workloads use Angstrom, e, eV, amu
+ *    and fs, with k_e = 14.3996454784 eV*A/e^2.
+ *  - A context is not thread safe.  Use one context per host thread.
+ */
+#ifndef QEQ_GB300_H
+#define QEQ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QEQ_ABI_VERSION 1
+
+enum qeq_status {
+    QEQ_OK = 0,
+    QEQ_ERR_INVALID = -1,     /* bad argument or parameter (message says which) */
+    QEQ_ERR_UNSUPPORTED = -2, /* valid request outside what this build supports */
+    QEQ_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    QEQ_ERR_CUFFT = -4,       /* a cuFFT call failed */
+    QEQ_ERR_NOMEM = -5,       /* device allocation failed */
+    QEQ_ERR_NOLIST = -6,      /* coulomb_apply before any neighbor_build */
+    QEQ_ERR_NONFINITE = -7,   /* NaN or Inf found in the inputs */
+    QEQ_ERR_CAPACITY = -8     /* a neighbour row exceeds the hard width limit */
+};
+
+enum qeq_precision {
+    QEQ_FP64 = 0,       /* every step in FP64 */
+    QEQ_FP32_MIXED = 1  /* FP32 pair sum, spreading, FFT and gather with FP64 sums */
+};
+
+enum qeq_short_model {
+    QEQ_SHORT_NONE = 0, /* no short-range potential */
+    QEQ_SHORT_WATER = 1 /* built-in flexible-water stand-in (not from the paper) */
+};
+
+/*
+ * Parameters of one periodic system.  qeq_params_default() fills the water
+ * workload defaults.
+ *
+ *  n_atoms         N >= 1, at most 2^24 - 1.
+ *  box             orthorhombic edge lengths (Sec. 3.2: "length of the unit
+ *                  cell").  Each edge must be at least (r_cut + skin) / 2.
+ *  alpha           Ewald splitting parameter of Eqs. ewald_real, ewald_rec and
+ *                  ewald_self, in 1/length.
+ *  r_cut           real-space cutoff.  Pairs at distance exactly r_cut are
+ *                  excluded.
+ *  skin            neighbour-list skin.  The list radius is r_cut + skin, and
+ *                  a rebuild is due when an atom has moved more than skin / 2
+ *                  since the last build (Sec. 4.2.3).
+ *  mesh            PME mesh K[3], each between 4 and 4096 (Alg. 2).
+ *  order           B-spline points per dimension p, 4..8 (Alg. 2, step 1).
+ *  precision       enum qeq_precision.
+ *  k_e             Coulomb constant multiplying every term.
+ *  gaussian_self   1 adds the Gaussian self-energy k_e sqrt(2/pi)/sigma_i to
+ *                  Phi_ii.  0 leaves it absorbed in the hardness.
+ *  max_neighbors   initial ELLPACK width (0 = estimate from density).  The
+ *                  list grows by itself on overflow (Sec. 3.1).
+ *  q_tot           total charge Q_tot of the constraint (Eq. linear_qeq).
+ *  krylov_rank     m >= 1, rank of the low-rank kernel update (Sec. 3.5).
+ *  dissipation_k   K_d in 3..7, the XL-BOMD dissipation window.
+ *  dt              MD time step, in the time unit.
+ *  short_range     enum qeq_short_model.
+ *  mass_unit       length^2 * mass / time^2 expressed in the energy unit
+ *                  (103.6427 for A, amu, fs, eV).
+ */
+typedef struct qeq_params {
+    int64_t n_atoms;
+    double box[3];
+    double alpha;
+    double r_cut;
+    double skin;
+    int32_t mesh[3];
+    int32_t order;
+    int32_t precision;
+    int32_t gaussian_self;
+    double k_e;
+    int32_t max_neighbors;
+    int32_t krylov_rank;
+    double q_tot;
+    int32_t dissipation_k;
+    int32_t short_range;
+    double dt;
+    double mass_unit;
+} qeq_params;
+
+typedef struct qeq_ctx qeq_ctx;
+
+/* Fill *p with the defaults: alpha 0.34, r_cut 8, skin 1, mesh 32^3, order 4,
+ * FP64, Gaussian self-energy on, k_e 14.3996454784, rank 2, K_d 5, dt 0.5,
+ * no short-range model.  The caller still sets n_atoms and box. */
+void qeq_params_default(qeq_params *p);
+
+/* Check *p and allocate every device buffer.  The buffers are the cell arrays,
+ * the ELLPACK neighbour list at its initial width, the PME meshes, the
+ * influence table, the cuFFT plans and the Krylov / reduction scratch.
+ * Uses the current CUDA device.
+ * On failure *out is NULL and the return code says why.  Synchronises. */
+int qeq_create(const qeq_params *p, qeq_ctx **out);
+
+/* Free everything qeq_create allocated.  NULL is ignored.  Synchronises the device. */
+void qeq_destroy(qeq_ctx *ctx);
+
+/* Message for the last failing call on ctx ("" when none).  ctx may be NULL,
+ * and then the message is that of the last failing qeq_create. */
+const char *qeq_last_error(const qeq_ctx *ctx);
+
+/* Number of atoms, and the current ELLPACK width (list capacity per row). */
+int qeq_get_sizes(const qeq_ctx *ctx, int64_t *n_atoms, int32_t *width);
+
+/*
+ * Cell-list neighbour build (Sec. 3.1, Alg. 1).
+ * Steps: wrap positions into the box (x + w, w = -(L floor(x / L))); bin into
+ * cells of edge >= r_cut + skin; counting sort by cell (ascending atom id
+ * inside a cell); emit, for every atom, each (j, image) with
+ * |x_j - x_i + s L| < r_cut + skin into an ELLPACK row.  The pair decision
+ * runs in FP64 with a fixed operation order and no fused multiply-add, so
+ * the pair set is exactly the geometric one.
+ * R: device [N][3] positions (any periodic image).
+ * The call synchronises once to read the overflow flag.  When a row does not
+ * fit, the list grows and is rebuilt before returning.
+ * Returns QEQ_OK, or QEQ_ERR_NONFINITE for a non-finite coordinate.
+ */
+int qeq_neighbor_build(qeq_ctx *ctx, const double *R, void *stream);
+
+/*
+ * Copy the current list to HOST memory in original atom numbering (for tests).
+ * counts: host [N] int32, entries per row.  nbr: host [N][width] int32
+ * neighbour atom ids.  shift: host [N][width][3] int8 image vectors s, so that
+ * the displacement is x_j - x_i + s * box.  Unused slots are left untouched.
+ * Any output may be NULL.  Synchronises.
+ */
+int qeq_neighbor_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int8_t *shift);
+
+/*
+ * Largest squared displacement of any atom since the last build, written to
+ * *max_disp2 (host double).  A rebuild is due when it exceeds (skin / 2)^2
+ * (Sec. 4.2.3).  Synchronises.
+ */
+int qeq_neighbor_displacement(qeq_ctx *ctx, const double *R, double *max_disp2, void *stream);
+
+/*
+ * Coulomb apply: v = Phi q with its field (Sec. 3.4, matrix-free form of
+ * C v = u o v + dE_Coul/dv).  Phi is Eq. ewald_real (over the current list,
+ * plain truncation at r_cut, Gaussian-charge correction
+ * -erfc(r / sqrt(sigma_i^2 + sigma_j^2)) / r), plus smooth PME for Eq. ewald_rec
+ * (Alg. 2: spread, FFT, influence function with |b(m)|^2, inverse FFT, gather),
+ * plus the self term of Eq. ewald_self (-2 alpha / sqrt(pi) q_i).  With
+ * gaussian_self it also carries the Gaussian self-energy.
+ * R:      device [N][3] current positions.  They must lie within skin / 2 of the
+ *         positions of the last neighbour build (not checked here; see
+ *         qeq_neighbor_displacement).
+ * q:      device [N] charges.   sigma: device [N] Gaussian widths (0 = point).
+ * v:      device [N] output potential dE_Coul / dq_i.
+ * E:      device [N][3] output field -d v_i / d r_i (nullable).
+ * F:      device [N][3] output Coulomb force q_i E_i (nullable).
+ * energy: device [4] output doubles (nullable): total 1/2 q.v, real-space part,
+ *         reciprocal mesh energy 1/2 sum G |Q^|^2, self part.
+ * Returns QEQ_ERR_NOLIST before the first neighbour build.
+ */
+int qeq_coulomb_apply(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
+                      double *v, double *E, double *F, double *energy, void *stream);
+
+/*
+ * Shadow XL-BOMD state (Sec. 3.5).  Everything is a caller-owned device array:
+ *   R [N][3] positions, V [N][3] velocities, F [N][3] forces of the current
+ *   state, Kf [N] kernel-times-residual of the current state,
+ *   n_hist [K_d + 1][N] auxiliary charges n(t), n(t - dt), ..., q [N] the
+ *   shadow charges q[n] of the current state.
+ * chi, eta, sigma, mass: device [N] parameters (eta is the hardness u).
+ * energies: device [8] doubles written by every evaluation:
+ *   0 kinetic, 1 shadow potential (Eq. qeq_energy + short range),
+ *   2 total, 3 short-range part, 4 Lagrange multiplier lambda,
+ *   5 sum of q, 6 |q[n] - n|, 7 number of Coulomb applies in the evaluation.
+ */
+typedef struct qeq_md_state {
+    double *R;
+    double *V;
+    double *F;
+    double *Kf;
+    double *n_hist;
+    double *q;
+    double *energies;
+} qeq_md_state;
+
+typedef struct qeq_md_params {
+    const double *chi;
+    const double *eta;
+    const double *sigma;
+    const double *mass;
+} qeq_md_params;
+
+/*
+ * Evaluate the shadow potential at (R, n_hist[0]) without moving anything.
+ * It computes the shadow charges q[n] (Eq. diag_linear_qeq, closed form,
+ * one Coulomb apply), the forces F = q o E[n] + n o E[q - n] (+ short range),
+ * and the rank-m Krylov approximation Kf of J^{-1} (q[n] - n) for
+ * Eq. Jnddot (m - 1 further potential-only applies).
+ * Rebuilds the neighbour list first if none exists.  Synchronises once.
+ */
+int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, void *stream);
+
+/*
+ * One shadow XL-BOMD step.  First a velocity-Verlet half kick and drift of R.
+ * Then the dissipative Verlet update of n,
+ *   n(t+dt) = 2 n(t) - n(t-dt) - kappa Kf(t) + a sum_k c_k n(t - k dt),
+ * with the history shifted.  Then a neighbour rebuild if an atom moved more
+ * than skin / 2, a full evaluation (as qeq_shadow_init), and the second half
+ * kick.  The integrator constants are those of Niklasson et al., J. Chem.
+ * Phys. 130, 214109 (2009); the paper does not print them.
+ * Synchronises once (the skin check).
+ */
+int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, void *stream);
+
+/* Same as qeq_shadow_step repeated n_steps times. */
+int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int32_t n_steps,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QEQ_GB300_H */

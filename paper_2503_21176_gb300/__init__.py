@@ -1,0 +1,144 @@
+"""GB300-native shadow charge-equilibration Coulomb library (Python side).
+
+The compute path is ``libqeq.so`` (hand-written sm_103a CUDA behind the C ABI in
+``include/qeq.h``).  This package only marshals torch tensors into that ABI:
+
+* ``_lib``     -- one function per C entry point, same names (qeq_create,
+                  qeq_neighbor_build, qeq_coulomb_apply, qeq_shadow_step, ...)
+* ``System``   -- owns one context plus the output tensors of an apply
+* ``ShadowMD`` -- owns the caller-side state arrays of the shadow XL-BOMD step
+* ``autograd`` -- ``CoulombEnergy``, a torch.autograd.Function over the apply
+"""
+
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    QEQ_FP32_MIXED,
+    QEQ_FP64,
+    QEQ_SHORT_NONE,
+    QEQ_SHORT_WATER,
+    QeqError,
+    load,
+    md_params,
+    md_state,
+    qeq_coulomb_apply,
+    qeq_create,
+    qeq_destroy,
+    qeq_get_sizes,
+    qeq_last_error,
+    qeq_neighbor_build,
+    qeq_neighbor_displacement,
+    qeq_neighbor_export,
+    qeq_params,
+    qeq_params_default,
+    qeq_shadow_init,
+    qeq_shadow_run,
+    qeq_shadow_step,
+)
+
+PRECISIONS = {"fp64": QEQ_FP64, "fp32_mixed": QEQ_FP32_MIXED}
+
+
+def make_params(n_atoms, box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(32, 32, 32), order=4,
+                precision="fp64", gaussian_self=True, k_e=14.3996454784, max_neighbors=0,
+                krylov_rank=2, q_tot=0.0, dissipation_k=5, dt=0.5, short_range=QEQ_SHORT_NONE,
+                mass_unit=103.6427) -> qeq_params:
+    p = qeq_params_default()
+    p.n_atoms = int(n_atoms)
+    for d in range(3):
+        p.box[d] = float(box[d])
+        p.mesh[d] = int(mesh[d])
+    p.alpha = float(alpha)
+    p.r_cut = float(r_cut)
+    p.skin = float(skin)
+    p.order = int(order)
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.gaussian_self = int(bool(gaussian_self))
+    p.k_e = float(k_e)
+    p.max_neighbors = int(max_neighbors)
+    p.krylov_rank = int(krylov_rank)
+    p.q_tot = float(q_tot)
+    p.dissipation_k = int(dissipation_k)
+    p.dt = float(dt)
+    p.short_range = int(short_range)
+    p.mass_unit = float(mass_unit)
+    return p
+
+
+class System:
+    """One periodic system on the current CUDA device, with apply outputs preallocated."""
+
+    def __init__(self, params: qeq_params, device=None):
+        self.params = params
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.n = int(params.n_atoms)
+        with torch.cuda.device(self.device):
+            self.ctx = qeq_create(params)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.v = torch.empty(self.n, **f64)
+        self.E = torch.empty(self.n, 3, **f64)
+        self.F = torch.empty(self.n, 3, **f64)
+        self.energy = torch.zeros(4, **f64)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            qeq_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def neighbor_build(self, R, stream=None):
+        qeq_neighbor_build(self.ctx, R, stream)
+
+    def neighbor_export(self):
+        return qeq_neighbor_export(self.ctx)
+
+    def displacement2(self, R, stream=None) -> float:
+        return qeq_neighbor_displacement(self.ctx, R, stream)
+
+    def apply(self, R, q, sigma, field=True, stream=None):
+        """v = Phi q; returns (v, E, F, energy[4]) views of the preallocated outputs."""
+        qeq_coulomb_apply(self.ctx, R, q, sigma, self.v, self.E if field else None,
+                          self.F if field else None, self.energy, stream)
+        return self.v, self.E, self.F, self.energy
+
+
+class ShadowMD:
+    """Caller-side state of the shadow XL-BOMD step (all tensors on the device)."""
+
+    def __init__(self, system: System, chi, eta, sigma, mass, R, V, n0):
+        self.sys = system
+        p = system.params
+        n = system.n
+        f64 = dict(dtype=torch.float64, device=system.device)
+        self.chi, self.eta, self.sigma, self.mass = (t.contiguous() for t in (chi, eta, sigma, mass))
+        self.R = R.clone().contiguous()
+        self.V = V.clone().contiguous()
+        self.F = torch.zeros(n, 3, **f64)
+        self.Kf = torch.zeros(n, **f64)
+        self.n_hist = n0.reshape(1, n).repeat(p.dissipation_k + 1, 1).contiguous()
+        self.q = torch.zeros(n, **f64)
+        self.energies = torch.zeros(8, **f64)
+        self._prm = md_params(self.chi, self.eta, self.sigma, self.mass)
+        self._st = md_state(self.R, self.V, self.F, self.Kf, self.n_hist, self.q, self.energies)
+
+    def init(self, stream=None):
+        qeq_shadow_init(self.sys.ctx, self._prm, self._st, stream)
+
+    def step(self, n_steps: int = 1, stream=None):
+        if n_steps == 1:
+            qeq_shadow_step(self.sys.ctx, self._prm, self._st, stream)
+        else:
+            qeq_shadow_run(self.sys.ctx, self._prm, self._st, n_steps, stream)
+
+    def energy_dict(self):
+        e = self.energies.cpu().tolist()
+        return {"kinetic": e[0], "shadow_potential": e[1], "total": e[2], "short": e[3],
+                "lambda": e[4], "sum_q": e[5], "residual_norm": e[6], "applies": e[7]}

@@ -1,0 +1,236 @@
+"""ctypes binding of ``libqeq.so`` (include/qeq.h): argument marshalling only.
+
+Each function keeps the C name and forwards device pointers taken from torch
+tensors (CUDA, float64, contiguous).  Every step of the computation runs in
+the CUDA library.  If the library is missing the import fails with an error,
+and there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+QEQ_OK = 0
+QEQ_FP64 = 0
+QEQ_FP32_MIXED = 1
+QEQ_SHORT_NONE = 0
+QEQ_SHORT_WATER = 1
+
+_ERRORS = {
+    -1: "QEQ_ERR_INVALID",
+    -2: "QEQ_ERR_UNSUPPORTED",
+    -3: "QEQ_ERR_CUDA",
+    -4: "QEQ_ERR_CUFFT",
+    -5: "QEQ_ERR_NOMEM",
+    -6: "QEQ_ERR_NOLIST",
+    -7: "QEQ_ERR_NONFINITE",
+    -8: "QEQ_ERR_CAPACITY",
+}
+
+
+class QeqError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qeq_params(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int64),
+        ("box", ctypes.c_double * 3),
+        ("alpha", ctypes.c_double),
+        ("r_cut", ctypes.c_double),
+        ("skin", ctypes.c_double),
+        ("mesh", ctypes.c_int32 * 3),
+        ("order", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("gaussian_self", ctypes.c_int32),
+        ("k_e", ctypes.c_double),
+        ("max_neighbors", ctypes.c_int32),
+        ("krylov_rank", ctypes.c_int32),
+        ("q_tot", ctypes.c_double),
+        ("dissipation_k", ctypes.c_int32),
+        ("short_range", ctypes.c_int32),
+        ("dt", ctypes.c_double),
+        ("mass_unit", ctypes.c_double),
+    ]
+
+
+class qeq_md_state(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in ("R", "V", "F", "Kf", "n_hist", "q", "energies")]
+
+
+class qeq_md_params(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in ("chi", "eta", "sigma", "mass")]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libqeq.so (building it first if it is absent and nvcc is available)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} is missing; run __graft_entry__.build() first")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.qeq_params_default.argtypes = [ctypes.POINTER(qeq_params)]
+    L.qeq_params_default.restype = None
+    L.qeq_create.argtypes = [ctypes.POINTER(qeq_params), ctypes.POINTER(P)]
+    L.qeq_destroy.argtypes = [P]
+    L.qeq_destroy.restype = None
+    L.qeq_last_error.argtypes = [P]
+    L.qeq_last_error.restype = ctypes.c_char_p
+    L.qeq_get_sizes.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+    L.qeq_neighbor_build.argtypes = [P, P, P]
+    L.qeq_neighbor_export.argtypes = [P, P, P, P]
+    L.qeq_neighbor_displacement.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), P]
+    L.qeq_coulomb_apply.argtypes = [P, P, P, P, P, P, P, P, P]
+    L.qeq_shadow_init.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state), P]
+    L.qeq_shadow_step.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state), P]
+    L.qeq_shadow_run.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state),
+                                 ctypes.c_int32, P]
+    for name in ("qeq_create", "qeq_get_sizes", "qeq_neighbor_build", "qeq_neighbor_export",
+                 "qeq_neighbor_displacement", "qeq_coulomb_apply", "qeq_shadow_init",
+                 "qeq_shadow_step", "qeq_shadow_run"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _dev(t, name, shape=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(ctx, rc):
+    if rc != QEQ_OK:
+        msg = load().qeq_last_error(ctx)
+        raise QeqError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# the C entry points
+# ---------------------------------------------------------------------------
+
+def qeq_params_default() -> qeq_params:
+    p = qeq_params()
+    load().qeq_params_default(ctypes.byref(p))
+    return p
+
+
+def qeq_create(params: qeq_params):
+    h = ctypes.c_void_p()
+    rc = load().qeq_create(ctypes.byref(params), ctypes.byref(h))
+    _check(None, rc)
+    return h
+
+
+def qeq_destroy(ctx) -> None:
+    if ctx:
+        load().qeq_destroy(ctx)
+
+
+def qeq_last_error(ctx) -> str:
+    m = load().qeq_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def qeq_get_sizes(ctx):
+    n = ctypes.c_int64()
+    w = ctypes.c_int32()
+    _check(ctx, load().qeq_get_sizes(ctx, ctypes.byref(n), ctypes.byref(w)))
+    return int(n.value), int(w.value)
+
+
+def qeq_neighbor_build(ctx, R, stream=None) -> None:
+    _check(ctx, load().qeq_neighbor_build(ctx, _dev(R, "R"), _stream(stream)))
+
+
+def qeq_neighbor_export(ctx):
+    """Host copies (counts [N], nbr [N, width], shift [N, width, 3]) in original numbering."""
+    import numpy as np
+
+    n, w = qeq_get_sizes(ctx)
+    counts = np.zeros(n, dtype=np.int32)
+    nbr = np.full((n, w), -1, dtype=np.int32)
+    shift = np.zeros((n, w, 3), dtype=np.int8)
+    _check(ctx, load().qeq_neighbor_export(ctx, counts.ctypes.data_as(ctypes.c_void_p),
+                                           nbr.ctypes.data_as(ctypes.c_void_p),
+                                           shift.ctypes.data_as(ctypes.c_void_p)))
+    return counts, nbr, shift
+
+
+def qeq_neighbor_displacement(ctx, R, stream=None) -> float:
+    d2 = ctypes.c_double()
+    _check(ctx, load().qeq_neighbor_displacement(ctx, _dev(R, "R"), ctypes.byref(d2),
+                                                 _stream(stream)))
+    return float(d2.value)
+
+
+def qeq_coulomb_apply(ctx, R, q, sigma, v, E=None, F=None, energy=None, stream=None) -> None:
+    _check(ctx, load().qeq_coulomb_apply(ctx, _dev(R, "R"), _dev(q, "q"), _dev(sigma, "sigma"),
+                                         _dev(v, "v"), _dev(E, "E", allow_none=True),
+                                         _dev(F, "F", allow_none=True),
+                                         _dev(energy, "energy", allow_none=True),
+                                         _stream(stream)))
+
+
+def md_params(chi, eta, sigma, mass) -> qeq_md_params:
+    return qeq_md_params(_dev(chi, "chi"), _dev(eta, "eta"), _dev(sigma, "sigma"), _dev(mass, "mass"))
+
+
+def md_state(R, V, F, Kf, n_hist, q, energies) -> qeq_md_state:
+    return qeq_md_state(_dev(R, "R"), _dev(V, "V"), _dev(F, "F"), _dev(Kf, "Kf"),
+                        _dev(n_hist, "n_hist"), _dev(q, "q"), _dev(energies, "energies"))
+
+
+def qeq_shadow_init(ctx, prm: qeq_md_params, st: qeq_md_state, stream=None) -> None:
+    _check(ctx, load().qeq_shadow_init(ctx, ctypes.byref(prm), ctypes.byref(st), _stream(stream)))
+
+
+def qeq_shadow_step(ctx, prm: qeq_md_params, st: qeq_md_state, stream=None) -> None:
+    _check(ctx, load().qeq_shadow_step(ctx, ctypes.byref(prm), ctypes.byref(st), _stream(stream)))
+
+
+def qeq_shadow_run(ctx, prm: qeq_md_params, st: qeq_md_state, n_steps: int, stream=None) -> None:
+    _check(ctx, load().qeq_shadow_run(ctx, ctypes.byref(prm), ctypes.byref(st), int(n_steps),
+                                      _stream(stream)))

@@ -1,0 +1,215 @@
+// Exported C entry points of include/qeq.h: parameter checks, context lifetime,
+// error reporting, and the thin wrappers around the neighbour, Coulomb and
+// shadow-step code.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+namespace qeq {
+
+int set_error(qeq_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+int cuda_check(qeq_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return QEQ_OK;
+    cudaGetLastError();
+    return set_error(ctx, QEQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int validate(const qeq_params *p) {
+    if (!p) return set_error(nullptr, QEQ_ERR_INVALID, "params is NULL");
+    if (p->n_atoms < 1 || p->n_atoms > kIndexMask)
+        return set_error(nullptr, QEQ_ERR_INVALID, "n_atoms must be in [1, %d]", kIndexMask);
+    for (int d = 0; d < 3; ++d) {
+        if (!(p->box[d] > 0.0) || !std::isfinite(p->box[d]))
+            return set_error(nullptr, QEQ_ERR_INVALID, "box[%d] must be positive and finite", d);
+        if (p->mesh[d] < 4 || p->mesh[d] > 4096)
+            return set_error(nullptr, QEQ_ERR_INVALID, "mesh[%d] must be in [4, 4096]", d);
+        if (p->mesh[d] < p->order)
+            return set_error(nullptr, QEQ_ERR_INVALID, "mesh[%d] is smaller than the spline order", d);
+    }
+    if (!(p->alpha > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "alpha must be positive");
+    if (!(p->r_cut > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "r_cut must be positive");
+    if (!(p->skin >= 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "skin must be >= 0");
+    if (p->order < 4 || p->order > 8)
+        return set_error(nullptr, QEQ_ERR_UNSUPPORTED, "B-spline order must be in [4, 8]");
+    if (p->precision != QEQ_FP64 && p->precision != QEQ_FP32_MIXED)
+        return set_error(nullptr, QEQ_ERR_INVALID, "unknown precision %d", p->precision);
+    if (!(p->k_e > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "k_e must be positive");
+    if (p->krylov_rank < 1 || p->krylov_rank > kMaxRank)
+        return set_error(nullptr, QEQ_ERR_INVALID, "krylov_rank must be in [1, %d]", kMaxRank);
+    if (p->dissipation_k < 3 || p->dissipation_k > 7)
+        return set_error(nullptr, QEQ_ERR_INVALID, "dissipation_k must be in [3, 7]");
+    if (p->short_range != QEQ_SHORT_NONE && p->short_range != QEQ_SHORT_WATER)
+        return set_error(nullptr, QEQ_ERR_INVALID, "unknown short_range model %d", p->short_range);
+    if (!(p->dt > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "dt must be positive");
+    if (!(p->mass_unit > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "mass_unit must be positive");
+    if (p->max_neighbors < 0) return set_error(nullptr, QEQ_ERR_INVALID, "max_neighbors must be >= 0");
+    return QEQ_OK;
+}
+
+static void destroy(qeq_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    shadow_free(ctx);
+    coulomb_free(ctx);
+    nl_free(ctx);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // namespace qeq
+
+using namespace qeq;
+
+QEQ_API void qeq_params_default(qeq_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_atoms = 0;
+    p->alpha = 0.34;
+    p->r_cut = 8.0;
+    p->skin = 1.0;
+    p->mesh[0] = p->mesh[1] = p->mesh[2] = 32;
+    p->order = 4;
+    p->precision = QEQ_FP64;
+    p->gaussian_self = 1;
+    p->k_e = 14.3996454784;
+    p->max_neighbors = 0;
+    p->krylov_rank = 2;
+    p->q_tot = 0.0;
+    p->dissipation_k = 5;
+    p->short_range = QEQ_SHORT_NONE;
+    p->dt = 0.5;
+    p->mass_unit = 103.6427;
+}
+
+QEQ_API int qeq_create(const qeq_params *p, qeq_ctx **out) {
+    if (!out) return set_error(nullptr, QEQ_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    qeq_ctx *ctx = new (std::nothrow) qeq_ctx();
+    if (!ctx) return set_error(nullptr, QEQ_ERR_NOMEM, "host allocation failed");
+    ctx->p = *p;
+    ctx->n = p->n_atoms;
+    ctx->fp32 = p->precision == QEQ_FP32_MIXED;
+    cudaGetDevice(&ctx->device);
+    rc = nl_configure(ctx);
+    if (!rc) rc = nl_alloc(ctx);
+    if (!rc) rc = coulomb_alloc(ctx);
+    if (!rc) rc = shadow_alloc(ctx);
+    if (!rc) rc = cuda_check(ctx, cudaDeviceSynchronize(), "create");
+    if (rc) {
+        g_create_error = ctx->err;
+        destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return QEQ_OK;
+}
+
+QEQ_API void qeq_destroy(qeq_ctx *ctx) { destroy(ctx); }
+
+QEQ_API const char *qeq_last_error(const qeq_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+QEQ_API int qeq_get_sizes(const qeq_ctx *ctx, int64_t *n_atoms, int32_t *width) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (n_atoms) *n_atoms = ctx->n;
+    if (width) *width = ctx->width;
+    return QEQ_OK;
+}
+
+QEQ_API int qeq_neighbor_build(qeq_ctx *ctx, const double *R, void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!R) return set_error(ctx, QEQ_ERR_INVALID, "R is NULL");
+    ctx->err.clear();
+    return nl_build(ctx, R, (cudaStream_t)stream);
+}
+
+QEQ_API int qeq_neighbor_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int8_t *shift) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "no neighbour list built yet");
+    return nl_export(ctx, counts, nbr, shift);
+}
+
+QEQ_API int qeq_neighbor_displacement(qeq_ctx *ctx, const double *R, double *max_disp2,
+                                      void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!R || !max_disp2) return set_error(ctx, QEQ_ERR_INVALID, "NULL argument");
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "no neighbour list built yet");
+    return nl_displacement(ctx, R, (cudaStream_t)stream, max_disp2);
+}
+
+QEQ_API int qeq_coulomb_apply(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
+                              double *v, double *E, double *F, double *energy, void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!R || !q || !sigma || !v) return set_error(ctx, QEQ_ERR_INVALID, "NULL input or output");
+    const bool field = E || F;
+    return coulomb_apply_impl(ctx, R, q, sigma, v, E, F, energy, field, (cudaStream_t)stream);
+}
+
+static int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *st) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!prm || !st) return set_error(ctx, QEQ_ERR_INVALID, "NULL md params or state");
+    if (!prm->chi || !prm->eta || !prm->sigma || !prm->mass)
+        return set_error(ctx, QEQ_ERR_INVALID, "NULL parameter array");
+    if (!st->R || !st->V || !st->F || !st->Kf || !st->n_hist || !st->q || !st->energies)
+        return set_error(ctx, QEQ_ERR_INVALID, "NULL state array");
+    ctx->err.clear();
+    return QEQ_OK;
+}
+
+QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
+                            void *stream) {
+    int rc = check_md(ctx, prm, st);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->list_valid) {
+        rc = nl_build(ctx, st->R, s);
+        if (rc) return rc;
+    }
+    rc = shadow_evaluate(ctx, prm, st, s);
+    if (rc) return rc;
+    return shadow_finish(ctx, prm, st, false, s);
+}
+
+QEQ_API int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
+                            void *stream) {
+    int rc = check_md(ctx, prm, st);
+    if (rc) return rc;
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "call qeq_shadow_init first");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = shadow_advance(ctx, prm, st, s);
+    if (rc) return rc;
+    rc = shadow_evaluate(ctx, prm, st, s);
+    if (rc) return rc;
+    return shadow_finish(ctx, prm, st, true, s);
+}
+
+QEQ_API int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
+                           int32_t n_steps, void *stream) {
+    for (int32_t k = 0; k < n_steps; ++k) {
+        int rc = qeq_shadow_step(ctx, prm, st, stream);
+        if (rc) return rc;
+    }
+    return QEQ_OK;
+}

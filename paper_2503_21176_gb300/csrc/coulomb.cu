@@ -1,0 +1,629 @@
+// Periodic Coulomb apply v = Phi q and its field on one GB300.
+//
+// Phi = real space (Eq. ewald_real over the ELLPACK list, with the
+// Gaussian-charge correction) + smooth PME (Alg. 2) + self term (Eq. ewald_self).
+// Launch sequence per apply, all on the caller's stream:
+//   gather_in   sorted copies (x, y, z, q), sigma and B-spline base/fraction
+//   real        one thread per sorted atom over its ELLPACK row (no atomics)
+//   spread      one thread per sorted atom, p^3 atomic adds onto the K^3 mesh
+//   cuFFT R2C   (library call)
+//   influence   Q^ *= G on the half spectrum, plus the mesh energy partial sums
+//   cuFFT C2R   (library call; unnormalised, so phi = dE_rec/dQ directly)
+//   gather_out  potential and field from the mesh, plus the self term, added to
+//               the real-space part and written in original atom order, with
+//               energy partial sums
+//   finalize    one block per energy component (fixed-order, deterministic)
+// FP64 mode runs all of it in double.  FP32_MIXED runs the pair math, the
+// spreading, the FFT and the gather in float.  It accumulates rows in float
+// chunks of 32 flushed into double, and keeps the energies and outputs in double.
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qeq {
+
+namespace {
+
+template <typename T> struct V4;
+template <> struct V4<double> { using type = double4_32a; };
+template <> struct V4<float> { using type = float4; };
+template <typename T> struct C2;
+template <> struct C2<double> { using type = double2; };
+template <> struct C2<float> { using type = float2; };
+
+// ---------------------------------------------------------------------------
+// gather_in: sorted copies of the inputs
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const double *__restrict__ R,
+                            const double *__restrict__ w, const double *__restrict__ q,
+                            const double *__restrict__ sigma, double sK0, double sK1, double sK2,
+                            typename V4<T>::type *__restrict__ xq, T *__restrict__ sg,
+                            int4 *__restrict__ sbase, typename V4<T>::type *__restrict__ sfrac) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = perm[i];
+    const double x = R[3 * (size_t)a] + w[3 * (size_t)a];
+    const double y = R[3 * (size_t)a + 1] + w[3 * (size_t)a + 1];
+    const double z = R[3 * (size_t)a + 2] + w[3 * (size_t)a + 2];
+    const double qa = q[a];
+    xq[i] = {(T)x, (T)y, (T)z, (T)qa};
+    sg[i] = (T)sigma[a];
+    // scaled fractional coordinates u = K x / L, split into floor and fraction in FP64
+    const double ux = x * sK0, uy = y * sK1, uz = z * sK2;
+    const double fx = floor(ux), fy = floor(uy), fz = floor(uz);
+    sbase[i] = make_int4((int)fx, (int)fy, (int)fz, 0);
+    sfrac[i] = {(T)(ux - fx), (T)(uy - fy), (T)(uz - fz), (T)qa};
+}
+
+// ---------------------------------------------------------------------------
+// real space (Eq. ewald_real, Gaussian-charge correction)
+// ---------------------------------------------------------------------------
+
+struct RealArgs {
+    int n;
+    double Lx, Ly, Lz;
+    double alpha;
+    double rc2;
+    double ke;
+};
+
+__device__ __forceinline__ void decode_image(int32_t e, int &j, int &sx, int &sy, int &sz) {
+    j = e & kIndexMask;
+    const int code = (int)((uint32_t)e >> kIndexBits);
+    sx = code / 25 - 2;
+    sy = (code / 5) % 5 - 2;
+    sz = code % 5 - 2;
+}
+
+template <bool FIELD>
+__global__ void __launch_bounds__(kThreads)
+k_real64(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+         const double4_32a *__restrict__ xq, const double *__restrict__ sg, double *__restrict__ v_s,
+         double *__restrict__ E_s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double4_32a xi = xq[i];
+    const double si2 = sg[i] * sg[i];
+    const int c = cnt[i];
+    const double al = a.alpha, al2 = a.alpha * a.alpha;
+    double v = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    for (int k = 0; k < c; ++k) {
+        int j, sx, sy, sz;
+        decode_image(nbr[(size_t)k * a.n + i], j, sx, sy, sz);
+        const double4_32a xj = xq[j];
+        const double dx = (xj.x - xi.x) + sx * a.Lx;
+        const double dy = (xj.y - xi.y) + sy * a.Ly;
+        const double dz = (xj.z - xi.z) + sz * a.Lz;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < a.rc2)) continue;
+        const double r = sqrt(r2);
+        const double ir = 1.0 / r;
+        double f = erfc(al * r) * ir;
+        double dfr = -(f + kTwoOverSqrtPi * al * exp(-al2 * r2)) * ir;  // f'(r)
+        const double g2 = si2 + sg[j] * sg[j];
+        if (g2 > 0.0) {
+            const double ig = 1.0 / sqrt(g2);
+            const double fg = erfc(r * ig) * ir;
+            f -= fg;
+            dfr += (fg + kTwoOverSqrtPi * ig * exp(-r2 * ig * ig)) * ir;
+        }
+        v += xj.w * f;
+        if (FIELD) {
+            const double gq = xj.w * dfr * ir;
+            ex += gq * dx;
+            ey += gq * dy;
+            ez += gq * dz;
+        }
+    }
+    v_s[i] = a.ke * v;
+    if (FIELD) {
+        E_s[3 * (size_t)i] = a.ke * ex;
+        E_s[3 * (size_t)i + 1] = a.ke * ey;
+        E_s[3 * (size_t)i + 2] = a.ke * ez;
+    }
+}
+
+template <bool FIELD>
+__global__ void __launch_bounds__(kThreads)
+k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+         const float4 *__restrict__ xq, const float *__restrict__ sg, double *__restrict__ v_s,
+         double *__restrict__ E_s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float4 xi = xq[i];
+    const float si2 = sg[i] * sg[i];
+    const int c = cnt[i];
+    const float Lx = (float)a.Lx, Ly = (float)a.Ly, Lz = (float)a.Lz;
+    const float al = (float)a.alpha, al2 = al * al, rc2 = (float)a.rc2;
+    const float tsp = (float)kTwoOverSqrtPi;
+    double v = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    float vf = 0.f, exf = 0.f, eyf = 0.f, ezf = 0.f;
+    for (int k = 0; k < c; ++k) {
+        int j, sx, sy, sz;
+        decode_image(nbr[(size_t)k * a.n + i], j, sx, sy, sz);
+        const float4 xj = xq[j];
+        const float dx = (xj.x - xi.x) + sx * Lx;
+        const float dy = (xj.y - xi.y) + sy * Ly;
+        const float dz = (xj.z - xi.z) + sz * Lz;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < rc2) {
+            const float ir = rsqrtf(r2);
+            const float r = r2 * ir;
+            float f = erfcf(al * r) * ir;
+            float dfr = -(f + tsp * al * __expf(-al2 * r2)) * ir;
+            const float g2 = si2 + sg[j] * sg[j];
+            if (g2 > 0.f) {
+                const float ig = rsqrtf(g2);
+                const float fg = erfcf(r * ig) * ir;
+                f -= fg;
+                dfr += (fg + tsp * ig * __expf(-r2 * ig * ig)) * ir;
+            }
+            vf += xj.w * f;
+            if (FIELD) {
+                const float gq = xj.w * dfr * ir;
+                exf += gq * dx;
+                eyf += gq * dy;
+                ezf += gq * dz;
+            }
+        }
+        if ((k & 31) == 31) {  // flush the float chunk into the double accumulators
+            v += vf; vf = 0.f;
+            if (FIELD) {
+                ex += exf; ey += eyf; ez += ezf;
+                exf = eyf = ezf = 0.f;
+            }
+        }
+    }
+    v += vf;
+    v_s[i] = a.ke * v;
+    if (FIELD) {
+        E_s[3 * (size_t)i] = a.ke * (ex + exf);
+        E_s[3 * (size_t)i + 1] = a.ke * (ey + eyf);
+        E_s[3 * (size_t)i + 2] = a.ke * (ez + ezf);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PME (Alg. 2)
+// ---------------------------------------------------------------------------
+
+// Cardinal B-spline weights M_P(w + j), j = 0..P-1, by the order recursion
+// M_n(u) = [u M_{n-1}(u) + (n - u) M_{n-1}(u - 1)] / (n - 1) from M_2, and the
+// derivative M_P'(u) = M_{P-1}(u) - M_{P-1}(u - 1).
+template <typename T, int P, bool DERIV>
+__device__ __forceinline__ void bspline(T w, T (&M)[P], T (&dM)[P]) {
+    M[0] = w;
+    M[1] = T(1) - w;
+#pragma unroll
+    for (int j = 2; j < P; ++j) M[j] = T(0);
+#pragma unroll
+    for (int n = 3; n <= P; ++n) {
+        if (DERIV && n == P) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const T left = (j < P - 1) ? M[j] : T(0);
+                const T right = (j >= 1) ? M[j - 1] : T(0);
+                dM[j] = left - right;
+            }
+        }
+        const T inv = T(1) / T(n - 1);
+#pragma unroll
+        for (int j = n - 1; j >= 0; --j) {
+            const T left = (j < n - 1) ? M[j] : T(0);
+            const T right = (j >= 1) ? M[j - 1] : T(0);
+            M[j] = ((w + T(j)) * left + (T(n) - w - T(j)) * right) * inv;
+        }
+    }
+}
+
+__device__ __forceinline__ int wrap_index(int b, int K) {
+    int r = b % K;
+    return r < 0 ? r + K : r;
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__restrict__ sfrac,
+         int K0, int K1, int K2, T *__restrict__ mesh) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 b = sbase[i];
+    const auto f = sfrac[i];
+    T Mx[P], My[P], Mz[P], dummy[P];
+    bspline<T, P, false>(f.x, Mx, dummy);
+    bspline<T, P, false>(f.y, My, dummy);
+    bspline<T, P, false>(f.z, Mz, dummy);
+    int iz[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) iz[c] = wrap_index(b.z - c, K2);
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        const int ix = wrap_index(b.x - a, K0);
+        const T qa = f.w * Mx[a];
+#pragma unroll
+        for (int bb = 0; bb < P; ++bb) {
+            const int iy = wrap_index(b.y - bb, K1);
+            const T qab = qa * My[bb];
+            T *row = mesh + ((size_t)ix * K1 + iy) * K2;
+#pragma unroll
+            for (int c = 0; c < P; ++c) atomicAdd(row + iz[c], qab * Mz[c]);
+        }
+    }
+}
+
+// Q^ *= G on the half spectrum; partial sums of the mesh energy 1/2 sum_full G |Q^|^2,
+// where every half-spectrum point stands for itself and its mirror except on the
+// planes m3 = 0 and (K3 even) m3 = K3/2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_influence(int64_t nc, int K2h, int K2, typename C2<T>::type *__restrict__ meshc,
+            const T *__restrict__ G, double *__restrict__ part) {
+    double e = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int m3 = (int)(t % K2h);
+        const double wgt = (m3 == 0 || (2 * m3 == K2)) ? 0.5 : 1.0;
+        auto z = meshc[t];
+        const T g = G[t];
+        e += wgt * (double)g * ((double)z.x * (double)z.x + (double)z.y * (double)z.y);
+        z.x *= g;
+        z.y *= g;
+        meshc[t] = z;
+    }
+    double vals[1] = {e};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+}
+
+struct GatherArgs {
+    int n;
+    int K0, K1, K2;
+    double sx, sy, sz;  // K / L per axis
+    double self_coef;   // k_e * (-2 alpha / sqrt(pi))
+    double gauss_coef;  // k_e * sqrt(2 / pi) when the Gaussian self-energy is on, else 0
+};
+
+template <typename T, int P, bool FIELD>
+__global__ void __launch_bounds__(kThreads)
+k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restrict__ sbase,
+             const typename V4<T>::type *__restrict__ sfrac, const T *__restrict__ phi,
+             const double *__restrict__ v_s, const double *__restrict__ E_s,
+             const double *__restrict__ q, const double *__restrict__ sigma,
+             double *__restrict__ v_out, double *__restrict__ E_out, double *__restrict__ F_out,
+             double *__restrict__ part) {
+    double e_tot = 0.0, e_real = 0.0, e_self = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const int4 b = sbase[i];
+        const auto f = sfrac[i];
+        T Mx[P], My[P], Mz[P], dMx[P], dMy[P], dMz[P];
+        bspline<T, P, FIELD>(f.x, Mx, dMx);
+        bspline<T, P, FIELD>(f.y, My, dMy);
+        bspline<T, P, FIELD>(f.z, Mz, dMz);
+        int iz[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) iz[c] = wrap_index(b.z - c, a.K2);
+        T vr = T(0), gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+        for (int aa = 0; aa < P; ++aa) {
+            const int ix = wrap_index(b.x - aa, a.K0);
+#pragma unroll
+            for (int bb = 0; bb < P; ++bb) {
+                const int iy = wrap_index(b.y - bb, a.K1);
+                const T *row = phi + ((size_t)ix * a.K1 + iy) * a.K2;
+                T sv = T(0), sd = T(0);
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    const T ph = row[iz[c]];
+                    sv += Mz[c] * ph;
+                    if (FIELD) sd += dMz[c] * ph;
+                }
+                vr += Mx[aa] * My[bb] * sv;
+                if (FIELD) {
+                    gx += dMx[aa] * My[bb] * sv;
+                    gy += Mx[aa] * dMy[bb] * sv;
+                    gz += Mx[aa] * My[bb] * sd;
+                }
+            }
+        }
+        const int atom = perm[i];
+        const double qa = q[atom];
+        double sc = a.self_coef;
+        if (a.gauss_coef != 0.0) sc += a.gauss_coef / sigma[atom];
+        const double vs = v_s[i];
+        const double vself = sc * qa;
+        const double v = vs + (double)vr + vself;
+        v_out[atom] = v;
+        if (FIELD) {
+            const double Ex = E_s[3 * (size_t)i] - a.sx * (double)gx;
+            const double Ey = E_s[3 * (size_t)i + 1] - a.sy * (double)gy;
+            const double Ez = E_s[3 * (size_t)i + 2] - a.sz * (double)gz;
+            if (E_out) {
+                E_out[3 * (size_t)atom] = Ex;
+                E_out[3 * (size_t)atom + 1] = Ey;
+                E_out[3 * (size_t)atom + 2] = Ez;
+            }
+            if (F_out) {
+                F_out[3 * (size_t)atom] = qa * Ex;
+                F_out[3 * (size_t)atom + 1] = qa * Ey;
+                F_out[3 * (size_t)atom + 2] = qa * Ez;
+            }
+        }
+        e_tot += 0.5 * qa * v;
+        e_real += 0.5 * qa * vs;
+        e_self += 0.5 * qa * vself;
+    }
+    double vals[3] = {e_tot, e_real, e_self};
+    block_sum<3>(vals);
+    if (threadIdx.x == 0) {
+        part[0 * kRedBlocks + blockIdx.x] = vals[0];
+        part[1 * kRedBlocks + blockIdx.x] = vals[1];
+        part[3 * kRedBlocks + blockIdx.x] = vals[2];
+    }
+}
+
+__global__ void k_finalize(const double *__restrict__ part, double *__restrict__ out) {
+    double s = 0.0;
+    const double *p = part + (size_t)blockIdx.x * kRedBlocks;
+    for (int k = threadIdx.x; k < kRedBlocks; k += blockDim.x) s += p[k];
+    double vals[1] = {s};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) out[blockIdx.x] = vals[0];
+}
+
+// ---------------------------------------------------------------------------
+// host-side tables
+// ---------------------------------------------------------------------------
+
+// |b(m)|^2 of smooth PME: b(m) = e^{2 pi i (p-1) m / K} / sum_{k=0}^{p-2} M_p(k+1) e^{2 pi i m k / K}.
+// A vanishing denominator (odd p at m = K/2) gives 0.
+std::vector<double> bspline_mod2(int K, int p) {
+    // M_p at the integers 0..p-1 by the same order recursion, evaluated at w = 0
+    std::vector<double> M(p, 0.0);
+    M[0] = 0.0;
+    M[1] = 1.0;
+    for (int n = 3; n <= p; ++n) {
+        for (int j = n - 1; j >= 0; --j) {
+            const double left = (j < n - 1) ? M[j] : 0.0;
+            const double right = (j >= 1) ? M[j - 1] : 0.0;
+            M[j] = (j * left + (n - j) * right) / (n - 1);
+        }
+    }
+    std::vector<double> out(K);
+    for (int m = 0; m < K; ++m) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k <= p - 2; ++k) {
+            const double ang = 2.0 * kPi * m * k / K;
+            re += M[k + 1] * std::cos(ang);
+            im += M[k + 1] * std::sin(ang);
+        }
+        const double d2 = re * re + im * im;
+        out[m] = d2 > 1e-10 ? 1.0 / d2 : 0.0;
+    }
+    return out;
+}
+
+template <typename T, int P>
+void launch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s) {
+    k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
+        (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
+        (T *)ctx->mesh);
+}
+
+template <typename T, int P, bool FIELD>
+void launch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const void *sf,
+                   const double *q, const double *sigma, double *v, double *E, double *F,
+                   cudaStream_t s) {
+    k_gather_out<T, P, FIELD><<<kRedBlocks, kThreads, 0, s>>>(
+        ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
+        ctx->E_s, q, sigma, v, E, F, ctx->part);
+}
+
+template <typename T>
+void dispatch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s) {
+    switch (ctx->p.order) {
+        case 4: launch_spread<T, 4>(ctx, sb, sf, s); break;
+        case 5: launch_spread<T, 5>(ctx, sb, sf, s); break;
+        case 6: launch_spread<T, 6>(ctx, sb, sf, s); break;
+        case 7: launch_spread<T, 7>(ctx, sb, sf, s); break;
+        default: launch_spread<T, 8>(ctx, sb, sf, s); break;
+    }
+}
+
+template <typename T, bool FIELD>
+void dispatch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const void *sf,
+                     const double *q, const double *sigma, double *v, double *E, double *F,
+                     cudaStream_t s) {
+    switch (ctx->p.order) {
+        case 4: launch_gather<T, 4, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
+        case 5: launch_gather<T, 5, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
+        case 6: launch_gather<T, 6, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
+        case 7: launch_gather<T, 7, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
+        default: launch_gather<T, 8, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
+    }
+}
+
+template <typename T>
+int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma, double *v,
+            double *E, double *F, double *energy4, bool need_field, cudaStream_t s) {
+    const int n = (int)ctx->n;
+    using T4 = typename V4<T>::type;
+    constexpr bool f64 = std::is_same<T, double>::value;
+    T4 *xq = f64 ? (T4 *)ctx->xq64 : (T4 *)ctx->xq32;
+    T *sg = f64 ? (T *)ctx->sg64 : (T *)ctx->sg32;
+    const qeq_params &p = ctx->p;
+    k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
+        n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
+        ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac);
+
+    RealArgs ra;
+    ra.n = n;
+    ra.Lx = p.box[0]; ra.Ly = p.box[1]; ra.Lz = p.box[2];
+    ra.alpha = p.alpha;
+    ra.rc2 = p.r_cut * p.r_cut;
+    ra.ke = p.k_e;
+    if (f64) {
+        if (need_field)
+            k_real64<true><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
+                                                            (double *)sg, ctx->v_s, ctx->E_s);
+        else
+            k_real64<false><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
+                                                             (double *)sg, ctx->v_s, ctx->E_s);
+    } else {
+        if (need_field)
+            k_real32<true><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
+                                                            (float *)sg, ctx->v_s, ctx->E_s);
+        else
+            k_real32<false><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
+                                                             (float *)sg, ctx->v_s, ctx->E_s);
+    }
+
+    cudaMemsetAsync(ctx->mesh, 0, sizeof(T) * ctx->mesh_n, s);
+    dispatch_spread<T>(ctx, ctx->sbase, ctx->sfrac, s);
+    cufftResult cr;
+    cr = cufftSetStream(ctx->plan_r2c, s);
+    if (cr == CUFFT_SUCCESS) cr = cufftSetStream(ctx->plan_c2r, s);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftSetStream failed (%d)", (int)cr);
+    if (f64)
+        cr = cufftExecD2Z(ctx->plan_r2c, (cufftDoubleReal *)ctx->mesh, (cufftDoubleComplex *)ctx->meshc);
+    else
+        cr = cufftExecR2C(ctx->plan_r2c, (cufftReal *)ctx->mesh, (cufftComplex *)ctx->meshc);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "forward FFT failed (%d)", (int)cr);
+    k_influence<T><<<kRedBlocks, kThreads, 0, s>>>(
+        ctx->meshc_n, ctx->K[2] / 2 + 1, ctx->K[2], (typename C2<T>::type *)ctx->meshc,
+        (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+    if (f64)
+        cr = cufftExecZ2D(ctx->plan_c2r, (cufftDoubleComplex *)ctx->meshc, (cufftDoubleReal *)ctx->mesh);
+    else
+        cr = cufftExecC2R(ctx->plan_c2r, (cufftComplex *)ctx->meshc, (cufftReal *)ctx->mesh);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "inverse FFT failed (%d)", (int)cr);
+
+    GatherArgs ga;
+    ga.n = n;
+    ga.K0 = ctx->K[0]; ga.K1 = ctx->K[1]; ga.K2 = ctx->K[2];
+    ga.sx = ctx->K[0] / p.box[0];
+    ga.sy = ctx->K[1] / p.box[1];
+    ga.sz = ctx->K[2] / p.box[2];
+    ga.self_coef = p.k_e * (-kTwoOverSqrtPi * p.alpha);
+    ga.gauss_coef = p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0;
+    if (need_field)
+        dispatch_gather<T, true>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, E, F, s);
+    else
+        dispatch_gather<T, false>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, nullptr, nullptr, s);
+    if (energy4) k_finalize<<<4, kThreads, 0, s>>>(ctx->part, energy4);
+    return cuda_check(ctx, cudaGetLastError(), "coulomb apply launch");
+}
+
+}  // namespace
+
+void launch_finalize(const double *part, int nslots, double *out, cudaStream_t s) {
+    k_finalize<<<nslots, kThreads, 0, s>>>(part, out);
+}
+
+int coulomb_alloc(qeq_ctx *ctx) {
+    const qeq_params &p = ctx->p;
+    const int64_t n = ctx->n;
+    for (int d = 0; d < 3; ++d) ctx->K[d] = p.mesh[d];
+    const int K2h = ctx->K[2] / 2 + 1;
+    ctx->mesh_n = (int64_t)ctx->K[0] * ctx->K[1] * ctx->K[2];
+    ctx->meshc_n = (int64_t)ctx->K[0] * ctx->K[1] * K2h;
+    const size_t rs = ctx->fp32 ? sizeof(float) : sizeof(double);
+    struct {
+        void **ptr;
+        size_t bytes;
+    } bufs[] = {
+        {(void **)&ctx->v_s, sizeof(double) * n},
+        {(void **)&ctx->E_s, sizeof(double) * 3 * n},
+        {(void **)&ctx->sbase, sizeof(int4) * n},
+        {(void **)&ctx->sfrac, 4 * rs * n},
+        {ctx->fp32 ? (void **)&ctx->xq32 : (void **)&ctx->xq64, 4 * rs * n},
+        {ctx->fp32 ? (void **)&ctx->sg32 : (void **)&ctx->sg64, rs * n},
+        {&ctx->mesh, rs * ctx->mesh_n},
+        {&ctx->meshc, 2 * rs * ctx->meshc_n},
+        {&ctx->G, rs * ctx->meshc_n},
+        {(void **)&ctx->part, sizeof(double) * kMaxRedSlots * kRedBlocks},
+        {(void **)&ctx->scal, sizeof(double) * kNumScal},
+        {(void **)&ctx->energy4, sizeof(double) * 4},
+    };
+    for (auto &b : bufs) {
+        cudaError_t e = cudaMalloc(b.ptr, b.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed", b.bytes);
+        }
+    }
+    if (cudaMallocHost(&ctx->h_scal, sizeof(double) * kNumScal) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, QEQ_ERR_NOMEM, "pinned host allocation failed");
+    }
+    cudaMemset(ctx->scal, 0, sizeof(double) * kNumScal);
+    cudaMemset(ctx->part, 0, sizeof(double) * kMaxRedSlots * kRedBlocks);
+
+    // influence function G(m) = k_e (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2 * B(m) on the
+    // half spectrum [K0][K1][K2/2+1], G(0) = 0 (Eq. ewald_rec with the smooth-PME B factor)
+    std::vector<double> b0 = bspline_mod2(ctx->K[0], p.order);
+    std::vector<double> b1 = bspline_mod2(ctx->K[1], p.order);
+    std::vector<double> b2 = bspline_mod2(ctx->K[2], p.order);
+    const double V = p.box[0] * p.box[1] * p.box[2];
+    const double pref = p.k_e * 4.0 * kPi / V;
+    const double inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
+    std::vector<double> G((size_t)ctx->meshc_n);
+    for (int m0 = 0; m0 < ctx->K[0]; ++m0) {
+        const int c0 = m0 <= ctx->K[0] / 2 ? m0 : m0 - ctx->K[0];
+        const double kx = 2.0 * kPi * c0 / p.box[0];
+        for (int m1 = 0; m1 < ctx->K[1]; ++m1) {
+            const int c1 = m1 <= ctx->K[1] / 2 ? m1 : m1 - ctx->K[1];
+            const double ky = 2.0 * kPi * c1 / p.box[1];
+            for (int m2 = 0; m2 < K2h; ++m2) {
+                const double kz = 2.0 * kPi * m2 / p.box[2];
+                const double k2 = kx * kx + ky * ky + kz * kz;
+                const size_t t = ((size_t)m0 * ctx->K[1] + m1) * K2h + m2;
+                G[t] = k2 > 0.0 ? pref * std::exp(-k2 * inv4a2) / k2 * b0[m0] * b1[m1] * b2[m2] : 0.0;
+            }
+        }
+    }
+    cudaError_t e;
+    if (ctx->fp32) {
+        std::vector<float> Gf(G.begin(), G.end());
+        e = cudaMemcpy(ctx->G, Gf.data(), sizeof(float) * Gf.size(), cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(ctx->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice);
+    }
+    int rc = cuda_check(ctx, e, "influence upload");
+    if (rc) return rc;
+
+    cufftResult cr = cufftPlan3d(&ctx->plan_r2c, ctx->K[0], ctx->K[1], ctx->K[2],
+                                 ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z);
+    if (cr == CUFFT_SUCCESS)
+        cr = cufftPlan3d(&ctx->plan_c2r, ctx->K[0], ctx->K[1], ctx->K[2],
+                         ctx->fp32 ? CUFFT_C2R : CUFFT_Z2D);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftPlan3d failed (%d)", (int)cr);
+    ctx->have_plans = true;
+    return QEQ_OK;
+}
+
+void coulomb_free(qeq_ctx *ctx) {
+    void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
+                    ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
+                    ctx->scal, ctx->energy4};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->have_plans) {
+        cufftDestroy(ctx->plan_r2c);
+        cufftDestroy(ctx->plan_c2r);
+    }
+}
+
+int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
+                       double *v, double *E, double *F, double *energy4, bool need_field,
+                       cudaStream_t s) {
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "coulomb_apply before neighbor_build");
+    if (ctx->fp32) return apply_t<float>(ctx, R, q, sigma, v, E, F, energy4, need_field, s);
+    return apply_t<double>(ctx, R, q, sigma, v, E, F, energy4, need_field, s);
+}
+
+}  // namespace qeq

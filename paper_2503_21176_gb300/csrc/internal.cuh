@@ -1,0 +1,188 @@
+// Internal declarations of the GB300 Coulomb / shadow-QEq library.
+// Only qeq_* entry points (include/qeq.h) are exported from the shared object.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "qeq.h"
+
+#define QEQ_API extern "C" __attribute__((visibility("default")))
+
+namespace qeq {
+
+constexpr int kThreads = 256;
+// Fixed reduction grid: 8 blocks per SM on a 152-SM GB300.  Grid-stride kernels
+// that reduce write one partial per block into a [slot][kRedBlocks] table, and a
+// one-block finalize sums each slot in a fixed order (deterministic results).
+constexpr int kRedBlocks = 1216;
+constexpr int kMaxRedSlots = 32;
+constexpr int kMaxRank = 8;
+constexpr int kMaxHist = 8;
+// A neighbour entry packs the sorted atom index (low 24 bits) and the image
+// code (high 8 bits): code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2), |s| <= 2.
+constexpr int kIndexBits = 24;
+constexpr int32_t kIndexMask = (1 << kIndexBits) - 1;
+constexpr int kMaxWidthLimit = 1 << 16;
+
+constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
+constexpr double kSqrtTwoOverPi = 0.79788456080286535588;
+constexpr double kPi = 3.14159265358979323846;
+
+// Device-side status words (int32).
+enum Flag { kFlagMaxRow = 0, kFlagNonFinite = 1, kNumFlags = 4 };
+
+// Device scalar table (double).  Slot 4 holds the last max displacement^2;
+// shadow.cu uses slots 32..127 for its reductions.
+enum Scal { kScMaxDisp2 = 4, kNumScal = 128 };
+
+}  // namespace qeq
+
+struct qeq_ctx {
+    qeq_params p{};
+    std::string err;
+    int device = 0;
+    int64_t n = 0;
+    bool fp32 = false;
+
+    // ---- cell grid (Sec. 3.1) ----
+    int nc[3] = {1, 1, 1};
+    int reach[3] = {1, 1, 1};
+    int64_t ncell = 1;
+    double cw[3] = {0, 0, 0};
+    double rl = 0, rl2 = 0;
+    float rl2f_lo = 0, rl2f_hi = 0;
+
+    // ---- neighbour list buffers (sorted numbering) ----
+    int32_t *cell_of = nullptr;     // [N] cell of atom (original numbering)
+    int32_t *cell_count = nullptr;  // [ncell]
+    int32_t *cell_start = nullptr;  // [ncell + 1]
+    int32_t *cell_fill = nullptr;   // [ncell]
+    int32_t *tmp_list = nullptr;    // [N]
+    int32_t *perm = nullptr;        // [N] sorted slot -> original atom
+    int32_t *cell_s = nullptr;      // [N] cell of sorted slot
+    double *wrap_off = nullptr;     // [N][3] wrap offsets w (original numbering)
+    double *R_build = nullptr;      // [N][3] positions at the last build
+    double4_32a *xs64 = nullptr;        // [N] wrapped positions at build (sorted)
+    float4 *xs32 = nullptr;         // [N] FP32 copy
+    int32_t *nbr = nullptr;         // [width][N] packed entries, column-major
+    int32_t *cnt = nullptr;         // [N] entries per sorted row
+    int width = 0;
+    int32_t *d_flags = nullptr;     // [kNumFlags]
+    int32_t *h_flags = nullptr;     // pinned host mirror
+    bool list_valid = false;
+    int64_t n_builds = 0;
+
+    // ---- apply buffers (sorted numbering) ----
+    double4_32a *xq64 = nullptr;   // [N] (x, y, z, q) FP64
+    double *sg64 = nullptr;    // [N] sigma
+    float4 *xq32 = nullptr;    // [N] FP32 copies
+    float *sg32 = nullptr;
+    double *v_s = nullptr;     // [N] real-space potential (sorted)
+    double *E_s = nullptr;     // [N][3] real-space field (sorted)
+    int4 *sbase = nullptr;     // [N] B-spline base mesh index floor(K x / L) (sorted)
+    void *sfrac = nullptr;     // [N] (fraction x, y, z, q) in the compute precision (sorted)
+
+    // ---- PME (Alg. 2) ----
+    int K[3] = {0, 0, 0};
+    int64_t mesh_n = 0, meshc_n = 0;
+    void *mesh = nullptr;      // [K1][K2][K3] real (double or float)
+    void *meshc = nullptr;     // [K1][K2][K3/2+1] complex
+    void *G = nullptr;         // influence function on the half spectrum (double or float)
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
+    bool have_plans = false;
+
+    // ---- reductions ----
+    double *part = nullptr;    // [kMaxRedSlots][kRedBlocks]
+    double *scal = nullptr;    // [kNumScal]
+    double *h_scal = nullptr;  // pinned host mirror
+
+    // ---- shadow-step scratch (original numbering) ----
+    double *v_n = nullptr, *E_n = nullptr, *phi = nullptr, *E_f = nullptr, *fvec = nullptr;
+    double *Wb = nullptr;      // [m][N] Krylov basis
+    double *Rb = nullptr;      // [m][N] J applied to the basis
+    double *F_short = nullptr; // [N][3]
+    double *energy4 = nullptr; // [4] energy parts of the last apply
+};
+
+namespace qeq {
+
+// ---- error helpers (api.cu) ----
+int set_error(qeq_ctx *ctx, int code, const char *fmt, ...);
+int cuda_check(qeq_ctx *ctx, cudaError_t e, const char *what);
+
+// ---- neighbour list (nlist.cu) ----
+int nl_configure(qeq_ctx *ctx);  // cell grid from params
+int nl_alloc(qeq_ctx *ctx);
+int nl_alloc_list(qeq_ctx *ctx, int width);
+int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s);
+int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int8_t *shift);
+int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_disp2);
+void nl_free(qeq_ctx *ctx);
+
+// ---- Coulomb operator (coulomb.cu) ----
+int coulomb_alloc(qeq_ctx *ctx);
+void coulomb_free(qeq_ctx *ctx);
+// v, E, F in original numbering; E / F / energy4 may be null; need_field=false
+// skips every field computation (potential-only apply).
+int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
+                       double *v, double *E, double *F, double *energy4, bool need_field,
+                       cudaStream_t s);
+
+// ---- reductions (coulomb.cu) ----
+// Sum nslots partial tables of kRedBlocks entries each, starting at part, into out[0..nslots).
+void launch_finalize(const double *part, int nslots, double *out, cudaStream_t s);
+
+// ---- shadow step (shadow.cu) ----
+int shadow_alloc(qeq_ctx *ctx);
+void shadow_free(qeq_ctx *ctx);
+int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
+int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
+int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
+                  cudaStream_t s);
+
+// ---- device helpers ----
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of NV values (blockDim.x == kThreads); result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sh[NV][kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double t = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = t;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < kThreads / 32 ? sh[k][lane] : 0.0;
+            v[k] = warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+inline int grid_for(int64_t n, int threads = kThreads) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace qeq

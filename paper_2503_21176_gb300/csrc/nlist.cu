@@ -1,0 +1,437 @@
+// Cell-list neighbour build (Sec. 3.1, Alg. 1) for one GB300.
+//
+// The paper gathers a [N, 27, C_max] candidate tensor and filters it (Alg. 1).
+// Its Triton variant instead loops over neighbouring cells per atom, writing a
+// buffer sized by a neighbour-count estimate.  Here:
+//   1. wrap + bin            one thread per atom: wrap offsets, cell index, cell histogram
+//   2. scan                  one block, exclusive scan of the cell histogram
+//   3. scatter               one thread per atom: slot in its cell (atomic)
+//   4. cell sort             one warp per cell: rank by atom id, so the order in a cell
+//                            is ascending atom id whatever order step 3 gave
+//   5. pair emit             one thread per sorted atom sweeps the (2r+1)^3 cell images;
+//                            FP32 distance prefilter, FP64 decision inside a band
+//                            around the list radius; ELLPACK rows, column-major
+// The FP64 decision is d = (xw_j - xw_i) + s * L per axis, then
+// d2 = (dx*dx + dy*dy) + dz*dz < r_list^2, every operation explicitly rounded
+// (no fused multiply-add), so the emitted set is exactly the geometric one.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qeq {
+
+namespace {
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+__global__ void k_wrap_bin(int n, const double *__restrict__ R, double Lx, double Ly, double Lz,
+                           double cwx, double cwy, double cwz, int ncx, int ncy, int ncz,
+                           int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_count,
+                           double *__restrict__ wrap_off, double *__restrict__ R_build,
+                           int32_t *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double L[3] = {Lx, Ly, Lz};
+    const double cw[3] = {cwx, cwy, cwz};
+    const int nc[3] = {ncx, ncy, ncz};
+    int c[3];
+    bool finite = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double x = R[3 * (size_t)i + d];
+        finite = finite && isfinite(x);
+        // w = -(L * floor(x / L)), xw = x + w: one IEEE rounding per operation
+        const double fl = floor(__ddiv_rn(x, L[d]));
+        const double w = -__dmul_rn(L[d], fl);
+        const double xw = __dadd_rn(x, w);
+        wrap_off[3 * (size_t)i + d] = w;
+        R_build[3 * (size_t)i + d] = x;
+        int cc = isfinite(xw) ? (int)floor(xw / cw[d]) : 0;
+        c[d] = min(max(cc, 0), nc[d] - 1);
+    }
+    if (!finite) atomicExch(&flags[kFlagNonFinite], 1);
+    const int cell = (c[0] * ncy + c[1]) * ncz + c[2];
+    cell_of[i] = cell;
+    atomicAdd(&cell_count[cell], 1);
+}
+
+// Single-block exclusive scan of ncell ints (any size: each thread scans a chunk).
+__global__ void k_scan(int64_t ncell, const int32_t *__restrict__ count, int32_t *__restrict__ start,
+                       int32_t *__restrict__ fill) {
+    __shared__ int32_t sh[1024];
+    const int t = threadIdx.x;
+    const int64_t chunk = (ncell + blockDim.x - 1) / blockDim.x;
+    const int64_t b = t * chunk, e = min(ncell, b + chunk);
+    int32_t s = 0;
+    for (int64_t k = b; k < e; ++k) s += count[k];
+    sh[t] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the per-thread sums
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        int32_t add = t >= off ? sh[t - off] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int32_t run = sh[t] - s;
+    for (int64_t k = b; k < e; ++k) {
+        start[k] = run;
+        fill[k] = 0;
+        run += count[k];
+    }
+    if (t == blockDim.x - 1) start[ncell] = sh[t];
+}
+
+__global__ void k_scatter(int n, const int32_t *__restrict__ cell_of,
+                          const int32_t *__restrict__ start, int32_t *__restrict__ fill,
+                          int32_t *__restrict__ tmp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell_of[i];
+    const int slot = atomicAdd(&fill[c], 1);
+    tmp[start[c] + slot] = i;
+}
+
+// One warp per cell: the rank of an atom inside its cell is the number of atoms
+// of that cell with a smaller id.  Writes the permutation, the sorted cell id and
+// the wrapped positions (recomputed from R and w with the same roundings).
+__global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start,
+                            const int32_t *__restrict__ tmp, const double *__restrict__ R,
+                            const double *__restrict__ wrap_off, int32_t *__restrict__ perm,
+                            int32_t *__restrict__ cell_s, double4_32a *__restrict__ xs64,
+                            float4 *__restrict__ xs32) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= ncell) return;
+    const int b = start[warp], e = start[warp + 1];
+    for (int k = b + lane; k < e; k += 32) {
+        const int id = tmp[k];
+        int rank = 0;
+        for (int t = b; t < e; ++t) rank += tmp[t] < id;
+        const int slot = b + rank;
+        perm[slot] = id;
+        cell_s[slot] = (int)warp;
+        const double x = __dadd_rn(R[3 * (size_t)id], wrap_off[3 * (size_t)id]);
+        const double y = __dadd_rn(R[3 * (size_t)id + 1], wrap_off[3 * (size_t)id + 1]);
+        const double z = __dadd_rn(R[3 * (size_t)id + 2], wrap_off[3 * (size_t)id + 2]);
+        xs64[slot] = make_double4_32a(x, y, z, 0.0);
+        xs32[slot] = make_float4((float)x, (float)y, (float)z, 0.f);
+    }
+}
+
+struct EmitArgs {
+    int n;
+    int ncx, ncy, ncz;
+    int rx, ry, rz;
+    double Lx, Ly, Lz;
+    float Lfx, Lfy, Lfz;
+    double rl2;
+    float lo, hi;
+    int width;
+};
+
+__global__ void __launch_bounds__(kThreads)
+k_emit(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
+       const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
+       int32_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int c = cell_s[i];
+    const int cx = c / (a.ncy * a.ncz), cy = (c / a.ncz) % a.ncy, cz = c % a.ncz;
+    const double4_32a xi = xs64[i];
+    const float4 xf = xs32[i];
+    int count = 0;
+    for (int ox = -a.rx; ox <= a.rx; ++ox) {
+        const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
+        const double shx = __dmul_rn((double)sx, a.Lx);
+        const float shxf = (float)sx * a.Lfx;
+        for (int oy = -a.ry; oy <= a.ry; ++oy) {
+            const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
+            const double shy = __dmul_rn((double)sy, a.Ly);
+            const float shyf = (float)sy * a.Lfy;
+            for (int oz = -a.rz; oz <= a.rz; ++oz) {
+                const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
+                const double shz = __dmul_rn((double)sz, a.Lz);
+                const float shzf = (float)sz * a.Lfz;
+                const int cn = (wx * a.ncy + wy) * a.ncz + wz;
+                const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
+                const int32_t code = ((sx + 2) * 25 + (sy + 2) * 5 + (sz + 2)) << kIndexBits;
+                const int jb = cell_start[cn], je = cell_start[cn + 1];
+                for (int j = jb; j < je; ++j) {
+                    if (self_img && j == i) continue;
+                    const float4 xj = xs32[j];
+                    const float dxf = (xj.x - xf.x) + shxf;
+                    const float dyf = (xj.y - xf.y) + shyf;
+                    const float dzf = (xj.z - xf.z) + shzf;
+                    const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                    bool keep;
+                    if (d2f < a.lo) {
+                        keep = true;
+                    } else if (d2f > a.hi) {
+                        keep = false;
+                    } else {
+                        const double4_32a xj64 = xs64[j];
+                        const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), shx);
+                        const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), shy);
+                        const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), shz);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                    __dmul_rn(dz, dz));
+                        keep = d2 < a.rl2;
+                    }
+                    if (keep) {
+                        if (count < a.width) nbr[(size_t)count * a.n + i] = j | code;
+                        ++count;
+                    }
+                }
+            }
+        }
+    }
+    cnt[i] = min(count, a.width);
+    if (count > a.width) atomicMax(&flags[kFlagMaxRow], count);
+}
+
+__global__ void k_max_disp2(int n, const double *__restrict__ R, const double *__restrict__ R0,
+                            double *__restrict__ part) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double dx = R[3 * (size_t)i] - R0[3 * (size_t)i];
+        const double dy = R[3 * (size_t)i + 1] - R0[3 * (size_t)i + 1];
+        const double dz = R[3 * (size_t)i + 2] - R0[3 * (size_t)i + 2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (!(d2 == d2)) d2 = INFINITY;
+        m = fmax(m, d2);
+    }
+    __shared__ double sh[kThreads / 32];
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_max_final(int nb, const double *__restrict__ part, double *__restrict__ out) {
+    double m = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) m = fmax(m, part[k]);
+    __shared__ double sh[kThreads / 32];
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) *out = t;
+    }
+}
+
+}  // namespace
+
+int nl_configure(qeq_ctx *ctx) {
+    const qeq_params &p = ctx->p;
+    ctx->rl = p.r_cut + p.skin;
+    ctx->rl2 = ctx->rl * ctx->rl;
+    double lmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double L = p.box[d];
+        lmax = std::max(lmax, L);
+        // cells at least r_list wide (with a relative margin so that rounding in
+        // the cell index cannot move an atom by more than one cell)
+        int nc = (int)std::floor(L / (ctx->rl * (1.0 + 1e-9)));
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        ctx->nc[d] = nc;
+        ctx->cw[d] = L / nc;
+        ctx->reach[d] = (int)std::ceil(ctx->rl * (1.0 + 1e-9) / ctx->cw[d]);
+        // image index |s| <= ceil(reach / nc) must fit the 8-bit image code (|s| <= 2)
+        const int smax = (ctx->reach[d] + nc - 1) / nc;
+        if (smax > 2)
+            return set_error(ctx, QEQ_ERR_UNSUPPORTED,
+                             "box edge %d (%.6g) is shorter than half the list radius %.6g", d, L,
+                             ctx->rl);
+    }
+    ctx->ncell = (int64_t)ctx->nc[0] * ctx->nc[1] * ctx->nc[2];
+    // FP32 prefilter band: |d2_fp32 - d2_exact| is bounded by a few ulp of the
+    // coordinates times the list radius; 4e-5 * rl * (Lmax + rl) is >10x that bound.
+    const double margin = 4e-5 * ctx->rl * (lmax + ctx->rl) + 1e-6;
+    ctx->rl2f_lo = (float)(ctx->rl2 - margin);
+    ctx->rl2f_hi = (float)(ctx->rl2 + margin);
+    return QEQ_OK;
+}
+
+int nl_alloc_list(qeq_ctx *ctx, int width) {
+    if (width > kMaxWidthLimit)
+        return set_error(ctx, QEQ_ERR_CAPACITY, "neighbour row of %d entries exceeds the limit %d",
+                         width, kMaxWidthLimit);
+    if (ctx->nbr) cudaFree(ctx->nbr);
+    ctx->nbr = nullptr;
+    cudaError_t e = cudaMalloc(&ctx->nbr, sizeof(int32_t) * (size_t)width * ctx->n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, QEQ_ERR_NOMEM, "cannot allocate a %d-wide neighbour list (%s)", width,
+                         cudaGetErrorString(e));
+    }
+    ctx->width = width;
+    return QEQ_OK;
+}
+
+int nl_alloc(qeq_ctx *ctx) {
+    const int64_t n = ctx->n;
+    struct {
+        void **ptr;
+        size_t bytes;
+    } bufs[] = {
+        {(void **)&ctx->cell_of, sizeof(int32_t) * n},
+        {(void **)&ctx->cell_count, sizeof(int32_t) * ctx->ncell},
+        {(void **)&ctx->cell_start, sizeof(int32_t) * (ctx->ncell + 1)},
+        {(void **)&ctx->cell_fill, sizeof(int32_t) * ctx->ncell},
+        {(void **)&ctx->tmp_list, sizeof(int32_t) * n},
+        {(void **)&ctx->perm, sizeof(int32_t) * n},
+        {(void **)&ctx->cell_s, sizeof(int32_t) * n},
+        {(void **)&ctx->wrap_off, sizeof(double) * 3 * n},
+        {(void **)&ctx->R_build, sizeof(double) * 3 * n},
+        {(void **)&ctx->xs64, sizeof(double4_32a) * n},
+        {(void **)&ctx->xs32, sizeof(float4) * n},
+        {(void **)&ctx->cnt, sizeof(int32_t) * n},
+        {(void **)&ctx->d_flags, sizeof(int32_t) * kNumFlags},
+    };
+    for (auto &b : bufs) {
+        cudaError_t e = cudaMalloc(b.ptr, b.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed", b.bytes);
+        }
+    }
+    if (cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * kNumFlags) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, QEQ_ERR_NOMEM, "pinned host allocation failed");
+    }
+    int width = ctx->p.max_neighbors;
+    if (width <= 0) {
+        const double V = ctx->p.box[0] * ctx->p.box[1] * ctx->p.box[2];
+        const double mean = 4.0 / 3.0 * kPi * ctx->rl2 * ctx->rl * (double)n / V;
+        width = (int)std::ceil(1.2 * mean + 32.0);
+    }
+    width = std::max(8, (width + 7) / 8 * 8);
+    return nl_alloc_list(ctx, width);
+}
+
+void nl_free(qeq_ctx *ctx) {
+    void *ptrs[] = {ctx->cell_of, ctx->cell_count, ctx->cell_start, ctx->cell_fill, ctx->tmp_list,
+                    ctx->perm,    ctx->cell_s,     ctx->wrap_off,   ctx->R_build,   ctx->xs64,
+                    ctx->xs32,    ctx->nbr,        ctx->cnt,        ctx->d_flags};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+}
+
+static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
+    EmitArgs a;
+    a.n = (int)ctx->n;
+    a.ncx = ctx->nc[0]; a.ncy = ctx->nc[1]; a.ncz = ctx->nc[2];
+    a.rx = ctx->reach[0]; a.ry = ctx->reach[1]; a.rz = ctx->reach[2];
+    a.Lx = ctx->p.box[0]; a.Ly = ctx->p.box[1]; a.Lz = ctx->p.box[2];
+    a.Lfx = (float)a.Lx; a.Lfy = (float)a.Ly; a.Lfz = (float)a.Lz;
+    a.rl2 = ctx->rl2;
+    a.lo = ctx->rl2f_lo;
+    a.hi = ctx->rl2f_hi;
+    a.width = ctx->width;
+    k_emit<<<grid_for(ctx->n), kThreads, 0, s>>>(a, ctx->xs64, ctx->xs32, ctx->cell_s,
+                                                 ctx->cell_start, ctx->nbr, ctx->cnt, ctx->d_flags);
+}
+
+int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
+    const int n = (int)ctx->n;
+    cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s);
+    cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
+    k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(
+        n, R, ctx->p.box[0], ctx->p.box[1], ctx->p.box[2], ctx->cw[0], ctx->cw[1], ctx->cw[2],
+        ctx->nc[0], ctx->nc[1], ctx->nc[2], ctx->cell_of, ctx->cell_count, ctx->wrap_off,
+        ctx->R_build, ctx->d_flags);
+    k_scan<<<1, 1024, 0, s>>>(ctx->ncell, ctx->cell_count, ctx->cell_start, ctx->cell_fill);
+    k_scatter<<<grid_for(n), kThreads, 0, s>>>(n, ctx->cell_of, ctx->cell_start, ctx->cell_fill,
+                                               ctx->tmp_list);
+    k_cell_sort<<<grid_for(ctx->ncell * 32), kThreads, 0, s>>>(
+        ctx->ncell, ctx->cell_start, ctx->tmp_list, R, ctx->wrap_off, ctx->perm, ctx->cell_s,
+        ctx->xs64, ctx->xs32);
+    launch_emit(ctx, s);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int32_t) * kNumFlags,
+                        cudaMemcpyDeviceToHost, s);
+        int rc = cuda_check(ctx, cudaStreamSynchronize(s), "neighbour build");
+        if (rc) return rc;
+        if (ctx->h_flags[kFlagNonFinite]) {
+            ctx->list_valid = false;
+            return set_error(ctx, QEQ_ERR_NONFINITE, "non-finite position in neighbor_build");
+        }
+        const int need = ctx->h_flags[kFlagMaxRow];
+        if (need <= ctx->width) break;
+        // grow (the paper's estimate-plus-buffer, Sec. 3.1) and emit again
+        rc = nl_alloc_list(ctx, (int)std::ceil(need * 1.1 / 8.0) * 8 + 8);
+        if (rc) {
+            ctx->list_valid = false;
+            return rc;
+        }
+        cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
+        launch_emit(ctx, s);
+    }
+    ctx->list_valid = true;
+    ctx->n_builds++;
+    return cuda_check(ctx, cudaGetLastError(), "neighbour build launch");
+}
+
+int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_disp2) {
+    k_max_disp2<<<kRedBlocks, kThreads, 0, s>>>((int)ctx->n, R, ctx->R_build, ctx->part);
+    k_max_final<<<1, kThreads, 0, s>>>(kRedBlocks, ctx->part, ctx->scal + kScMaxDisp2);
+    if (max_disp2) {
+        cudaMemcpyAsync(ctx->h_scal + kScMaxDisp2, ctx->scal + kScMaxDisp2, sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
+        int rc = cuda_check(ctx, cudaStreamSynchronize(s), "displacement check");
+        if (rc) return rc;
+        *max_disp2 = ctx->h_scal[kScMaxDisp2];
+    }
+    return QEQ_OK;
+}
+
+int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr_out, int8_t *shift_out) {
+    const int64_t n = ctx->n;
+    const int w = ctx->width;
+    std::vector<int32_t> perm(n), cnt(n), nbr((size_t)w * n);
+    int rc = cuda_check(ctx, cudaDeviceSynchronize(), "export sync");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpy(perm.data(), ctx->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost),
+                    "export perm");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpy(cnt.data(), ctx->cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost),
+                    "export counts");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpy(nbr.data(), ctx->nbr, sizeof(int32_t) * (size_t)w * n,
+                                    cudaMemcpyDeviceToHost),
+                    "export list");
+    if (rc) return rc;
+    for (int64_t si = 0; si < n; ++si) {
+        const int64_t atom = perm[si];
+        if (counts) counts[atom] = cnt[si];
+        for (int k = 0; k < cnt[si]; ++k) {
+            const int32_t e = nbr[(size_t)k * n + si];
+            const int32_t j = e & kIndexMask;
+            const int code = (int)((uint32_t)e >> kIndexBits);
+            if (nbr_out) nbr_out[atom * w + k] = perm[j];
+            if (shift_out) {
+                shift_out[(atom * w + k) * 3 + 0] = (int8_t)(code / 25 - 2);
+                shift_out[(atom * w + k) * 3 + 1] = (int8_t)((code / 5) % 5 - 2);
+                shift_out[(atom * w + k) * 3 + 2] = (int8_t)(code % 5 - 2);
+            }
+        }
+    }
+    return QEQ_OK;
+}
+
+}  // namespace qeq

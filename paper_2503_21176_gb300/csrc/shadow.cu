@@ -1,0 +1,481 @@
+// Shadow XL-BOMD step for the charge-equilibration model (Sec. 3.5), FP64 on the GPU.
+//
+// evaluate(R, n):
+//   v[n], E[n]    = apply(n)                              (one Coulomb apply)
+//   lambda, q[n]  from Eq. diag_linear_qeq in closed form:
+//                 lambda = -(Q_tot + sum (chi + v) / u) / sum 1 / u,
+//                 q = -(chi + v + lambda) / u
+//   f = q - n;    Phi f, E[f] = apply(f)                  (second apply)
+//   F = q o E[n] + n o E[f] (+ short range)
+//   Krylov:       w_1 = f / |f|, r_k = J w_k with
+//                 J x = -(Phi x + mu) / u - x, mu = -(sum Phi x / u) / sum 1 / u;
+//                 w_{k+1} = r_k Gram-Schmidt-orthonormalised against w_1..w_k
+//                 (one potential-only apply per extra vector);
+//                 O = R^T R, c = O^{-1} R^T f, Kf = W c
+//   energies      shadow energy (Eq. qeq_energy at q[n]), lambda, sum q, |f|
+// advance: velocity-Verlet half kick + drift, dissipative Verlet update of the
+//   n history (constants of Niklasson et al., J. Chem. Phys. 130, 214109 (2009)),
+//   neighbour rebuild when an atom moved more than skin / 2.
+// finish: second half kick and kinetic energy.
+// Every reduction writes one partial per block of a fixed grid, and a
+// one-block finalize sums them in fixed order, so a step is deterministic apart
+// from the floating-point atomics of the PME spread.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace qeq {
+
+namespace {
+
+// scalar slots (ctx->scal)
+constexpr int S_LAM = 32;   // S1 = sum (chi + v) / u, S2 = sum 1 / u
+constexpr int S_CHG = 34;   // sum f^2, sum q chi, sum u q^2 / 2, sum q v, sum n v, sum q
+constexpr int S_MU = 40;    // sum (Phi w) / u
+constexpr int S_DOT = 41;   // Gram-Schmidt dot
+constexpr int S_OM = 48;    // O (kMaxRank^2, row-major) then g = R^T f (kMaxRank)
+constexpr int S_KE = 120;   // kinetic energy
+constexpr int S_SHORT = 121;
+
+__global__ void k_lambda_part(int n, const double *__restrict__ chi, const double *__restrict__ u,
+                              const double *__restrict__ v, double *__restrict__ part) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double iu = 1.0 / u[i];
+        s1 += (chi[i] + v[i]) * iu;
+        s2 += iu;
+    }
+    double vals[2] = {s1, s2};
+    block_sum<2>(vals);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = vals[0];
+        part[kRedBlocks + blockIdx.x] = vals[1];
+    }
+}
+
+__global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
+                          const double *__restrict__ u, const double *__restrict__ v,
+                          const double *__restrict__ nn, const double *__restrict__ scal,
+                          double *__restrict__ q, double *__restrict__ f, double *__restrict__ part) {
+    const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double qi = -(chi[i] + v[i] + lam) / u[i];
+        const double fi = qi - nn[i];
+        q[i] = qi;
+        f[i] = fi;
+        a[0] += fi * fi;
+        a[1] += qi * chi[i];
+        a[2] += 0.5 * u[i] * qi * qi;
+        a[3] += qi * v[i];
+        a[4] += nn[i] * v[i];
+        a[5] += qi;
+    }
+    block_sum<6>(a);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) part[k * kRedBlocks + blockIdx.x] = a[k];
+}
+
+// energies: 1 shadow potential, 3 short range, 4 lambda, 5 sum q, 6 |f|, 7 applies
+__global__ void k_charge_energies(double q_tot, int applies, const double *__restrict__ scal,
+                                  double *__restrict__ energies) {
+    const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
+    const double e_short = scal[S_SHORT];
+    energies[1] = scal[S_CHG + 1] + scal[S_CHG + 2] + scal[S_CHG + 3] - 0.5 * scal[S_CHG + 4] + e_short;
+    energies[3] = e_short;
+    energies[4] = lam;
+    energies[5] = scal[S_CHG + 5];
+    energies[6] = sqrt(scal[S_CHG]);
+    energies[7] = (double)applies;
+}
+
+// F = q E[n] + n E[f] (+ F_short); w_1 = f / |f|; Phi w_1 = Phi f / |f| (in place);
+// partial sum of (Phi w_1) / u for mu.
+__global__ void k_forces_w1(int n, const double *__restrict__ q, const double *__restrict__ nn,
+                            const double *__restrict__ En, const double *__restrict__ Ef,
+                            const double *__restrict__ Fs, const double *__restrict__ f,
+                            const double *__restrict__ u, const double *__restrict__ scal,
+                            double *__restrict__ F, double *__restrict__ w1,
+                            double *__restrict__ phi, double *__restrict__ part) {
+    const double nf = sqrt(scal[S_CHG]);
+    const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double Fi = q[i] * En[3 * (size_t)i + d] + nn[i] * Ef[3 * (size_t)i + d];
+            if (Fs) Fi += Fs[3 * (size_t)i + d];
+            F[3 * (size_t)i + d] = Fi;
+        }
+        w1[i] = f[i] * inv;
+        const double pw = phi[i] * inv;
+        phi[i] = pw;
+        s += pw / u[i];
+    }
+    double vals[1] = {s};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+}
+
+__global__ void k_mu_part(int n, const double *__restrict__ phi, const double *__restrict__ u,
+                          double *__restrict__ part) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s += phi[i] / u[i];
+    double vals[1] = {s};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+}
+
+// r = J w = -(Phi w + mu) / u - w with mu = -(sum Phi w / u) / sum 1 / u
+__global__ void k_jacobian(int n, const double *__restrict__ phi, const double *__restrict__ w,
+                           const double *__restrict__ u, const double *__restrict__ scal,
+                           double *__restrict__ r) {
+    const double mu = -scal[S_MU] / scal[S_LAM + 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        r[i] = -(phi[i] + mu) / u[i] - w[i];
+}
+
+// partial of <a, b>
+__global__ void k_dot_part(int n, const double *__restrict__ a, const double *__restrict__ b,
+                           double *__restrict__ part) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    double vals[1] = {s};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+}
+
+// x -= scal[S_DOT] * y, then partial of <z, x> (z may alias x for the norm)
+__global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double *__restrict__ y,
+                           double *x, const double *z, double *__restrict__ part) {
+    const double a = scal[S_DOT];
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double xi = x[i] - a * y[i];
+        x[i] = xi;
+        s += z[i] * xi;
+    }
+    double vals[1] = {s};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+}
+
+__global__ void k_copy(int n, const double *__restrict__ src, double *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+__global__ void k_normalize(int n, const double *__restrict__ scal, double *__restrict__ x) {
+    const double nv = sqrt(scal[S_DOT]);
+    const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] *= inv;
+}
+
+// partials of O_ab = <R_a, R_b> (a <= b) and g_a = <R_a, f>
+__global__ void k_normal_part(int n, int m, const double *__restrict__ Rb,
+                              const double *__restrict__ f, double *__restrict__ part) {
+    double acc[kMaxRank * (kMaxRank + 1) / 2 + kMaxRank];
+    const int nO = m * (m + 1) / 2;
+    for (int k = 0; k < nO + m; ++k) acc[k] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double r[kMaxRank];
+        for (int a = 0; a < m; ++a) r[a] = Rb[(size_t)a * n + i];
+        int k = 0;
+        for (int a = 0; a < m; ++a)
+            for (int b = a; b < m; ++b) acc[k++] += r[a] * r[b];
+        for (int a = 0; a < m; ++a) acc[nO + a] += r[a] * f[i];
+    }
+    for (int k = 0; k < nO + m; ++k) {
+        double vals[1] = {acc[k]};
+        block_sum<1>(vals);
+        if (threadIdx.x == 0) part[k * kRedBlocks + blockIdx.x] = vals[0];
+    }
+}
+
+// Solve O c = g (m x m, symmetric) by Gaussian elimination with partial pivoting.
+// Singular directions (pivot 0, e.g. f = 0) get c = 0.
+__global__ void k_solve_small(int m, double *__restrict__ scal) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double A[kMaxRank][kMaxRank + 1];
+    const int nO = m * (m + 1) / 2;
+    int k = 0;
+    for (int a = 0; a < m; ++a)
+        for (int b = a; b < m; ++b) {
+            A[a][b] = scal[S_OM + k];
+            A[b][a] = scal[S_OM + k];
+            ++k;
+        }
+    for (int a = 0; a < m; ++a) A[a][m] = scal[S_OM + nO + a];
+    double scale = 0.0;
+    for (int a = 0; a < m; ++a) scale = fmax(scale, fabs(A[a][a]));
+    const double tiny = scale * 1e-300;
+    int piv_ok[kMaxRank];
+    for (int c = 0; c < m; ++c) {
+        int best = c;
+        for (int r = c + 1; r < m; ++r)
+            if (fabs(A[r][c]) > fabs(A[best][c])) best = r;
+        if (best != c)
+            for (int j = 0; j <= m; ++j) {
+                const double t = A[c][j];
+                A[c][j] = A[best][j];
+                A[best][j] = t;
+            }
+        piv_ok[c] = fabs(A[c][c]) > tiny && A[c][c] != 0.0;
+        if (!piv_ok[c]) continue;
+        for (int r = c + 1; r < m; ++r) {
+            const double fct = A[r][c] / A[c][c];
+            for (int j = c; j <= m; ++j) A[r][j] -= fct * A[c][j];
+        }
+    }
+    double x[kMaxRank];
+    for (int c = m - 1; c >= 0; --c) {
+        if (!piv_ok[c]) {
+            x[c] = 0.0;
+            continue;
+        }
+        double s = A[c][m];
+        for (int j = c + 1; j < m; ++j) s -= A[c][j] * x[j];
+        x[c] = s / A[c][c];
+    }
+    for (int a = 0; a < m; ++a) scal[S_OM + kMaxRank * kMaxRank + a] = x[a];
+}
+
+__global__ void k_kf(int n, int m, const double *__restrict__ Wb, const double *__restrict__ scal,
+                     double *__restrict__ Kf) {
+    const double *c = scal + S_OM + kMaxRank * kMaxRank;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int a = 0; a < m; ++a) s += c[a] * Wb[(size_t)a * n + i];
+        Kf[i] = s;
+    }
+}
+
+struct Dissipation {
+    double kappa, alpha;
+    double c[kMaxHist];
+    int kd;
+};
+
+Dissipation dissipation(int kd) {
+    // Niklasson et al., J. Chem. Phys. 130, 214109 (2009), Table I
+    Dissipation d{};
+    d.kd = kd;
+    static const double c3[] = {-2, 3, 0, -1};
+    static const double c4[] = {-3, 6, -2, -2, 1};
+    static const double c5[] = {-6, 14, -8, -3, 4, -1};
+    static const double c6[] = {-14, 36, -27, -2, 12, -6, 1};
+    static const double c7[] = {-36, 99, -88, 11, 32, -25, 8, -1};
+    const double *c = nullptr;
+    switch (kd) {
+        case 3: d.kappa = 1.69; d.alpha = 150e-3; c = c3; break;
+        case 4: d.kappa = 1.75; d.alpha = 57e-3; c = c4; break;
+        case 5: d.kappa = 1.82; d.alpha = 18e-3; c = c5; break;
+        case 6: d.kappa = 1.84; d.alpha = 5.5e-3; c = c6; break;
+        default: d.kappa = 1.86; d.alpha = 1.6e-3; c = c7; break;
+    }
+    for (int k = 0; k <= kd; ++k) d.c[k] = c[k];
+    return d;
+}
+
+// Half kick + drift of R; n_{t+1} = 2 n_t - n_{t-1} - kappa Kf + alpha sum_k c_k n_{t-k};
+// history shifted in place (each thread owns one atom's column).
+__global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
+                          const double *__restrict__ mass, const double *__restrict__ F,
+                          const double *__restrict__ Kf, double *__restrict__ R,
+                          double *__restrict__ V, double *__restrict__ hist) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double inv_m = 1.0 / (mass[i] * mass_unit);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double vi = V[3 * (size_t)i + d] + 0.5 * dt * F[3 * (size_t)i + d] * inv_m;
+            V[3 * (size_t)i + d] = vi;
+            R[3 * (size_t)i + d] += dt * vi;
+        }
+        double h[kMaxHist];
+        for (int k = 0; k <= dis.kd; ++k) h[k] = hist[(size_t)k * n + i];
+        double acc = 0.0;
+        for (int k = 0; k <= dis.kd; ++k) acc += dis.c[k] * h[k];
+        const double nn = 2.0 * h[0] - h[1] - dis.kappa * Kf[i] + dis.alpha * acc;
+        for (int k = dis.kd; k >= 1; --k) hist[(size_t)k * n + i] = h[k - 1];
+        hist[i] = nn;
+    }
+}
+
+// optional second half kick, then partial of the kinetic energy
+__global__ void k_finish(int n, double dt, double mass_unit, bool kick,
+                         const double *__restrict__ mass, const double *__restrict__ F,
+                         double *__restrict__ V, double *__restrict__ part) {
+    double ke = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double mi = mass[i] * mass_unit;
+        double v2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double vi = V[3 * (size_t)i + d];
+            if (kick) {
+                vi += 0.5 * dt * F[3 * (size_t)i + d] / mi;
+                V[3 * (size_t)i + d] = vi;
+            }
+            v2 += vi * vi;
+        }
+        ke += 0.5 * mi * v2;
+    }
+    double vals[1] = {ke};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+}
+
+__global__ void k_total_energy(const double *__restrict__ scal, double *__restrict__ energies) {
+    energies[0] = scal[S_KE];
+    energies[2] = scal[S_KE] + energies[1];
+}
+
+}  // namespace
+
+int shadow_alloc(qeq_ctx *ctx) {
+    const int64_t n = ctx->n;
+    const int m = ctx->p.krylov_rank;
+    struct {
+        void **ptr;
+        size_t bytes;
+    } bufs[] = {
+        {(void **)&ctx->v_n, sizeof(double) * n},
+        {(void **)&ctx->E_n, sizeof(double) * 3 * n},
+        {(void **)&ctx->phi, sizeof(double) * n},
+        {(void **)&ctx->E_f, sizeof(double) * 3 * n},
+        {(void **)&ctx->fvec, sizeof(double) * n},
+        {(void **)&ctx->Wb, sizeof(double) * (size_t)m * n},
+        {(void **)&ctx->Rb, sizeof(double) * (size_t)m * n},
+    };
+    for (auto &b : bufs) {
+        cudaError_t e = cudaMalloc(b.ptr, b.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed", b.bytes);
+        }
+    }
+    if (ctx->p.short_range == QEQ_SHORT_WATER) {
+        if (cudaMalloc(&ctx->F_short, sizeof(double) * 3 * n) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation failed");
+        }
+    }
+    return QEQ_OK;
+}
+
+void shadow_free(qeq_ctx *ctx) {
+    void *ptrs[] = {ctx->v_n, ctx->E_n, ctx->phi, ctx->E_f, ctx->fvec, ctx->Wb, ctx->Rb, ctx->F_short};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int short_range_forces(qeq_ctx *ctx, const double *R, const double *mass, double *F_short,
+                       double *e_short_slot, cudaStream_t s);
+
+int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
+    const int n = (int)ctx->n;
+    const int m = ctx->p.krylov_rank;
+    const double *u = prm->eta;
+    double *nn = st->n_hist;  // n(t) is history slot 0
+    double *part = ctx->part;
+    double *scal = ctx->scal;
+    const int G = kRedBlocks;
+
+    // short-range stand-in (or zero)
+    if (ctx->p.short_range == QEQ_SHORT_WATER) {
+        int rc = short_range_forces(ctx, st->R, prm->mass, ctx->F_short, scal + S_SHORT, s);
+        if (rc) return rc;
+    } else {
+        cudaMemsetAsync(scal + S_SHORT, 0, sizeof(double), s);
+    }
+
+    // 1. v[n], E[n]
+    int rc = coulomb_apply_impl(ctx, st->R, nn, prm->sigma, ctx->v_n, ctx->E_n, nullptr, nullptr,
+                                true, s);
+    if (rc) return rc;
+    // 2. lambda and q[n] (Eq. diag_linear_qeq)
+    k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, part);
+    launch_finalize(part, 2, scal + S_LAM, s);
+    k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->v_n, nn, scal, st->q,
+                                     ctx->fvec, part);
+    launch_finalize(part, 6, scal + S_CHG, s);
+    // 3. Phi f, E[f]
+    rc = coulomb_apply_impl(ctx, st->R, ctx->fvec, prm->sigma, ctx->phi, ctx->E_f, nullptr, nullptr,
+                            true, s);
+    if (rc) return rc;
+    // 4. forces, w_1, r_1
+    double *W0 = ctx->Wb, *R0 = ctx->Rb;
+    k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
+                                       ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr,
+                                       ctx->fvec, u, scal, st->F, W0, ctx->phi, part);
+    launch_finalize(part, 1, scal + S_MU, s);
+    k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, W0, u, scal, R0);
+    // 5. further Krylov vectors
+    for (int k = 1; k < m; ++k) {
+        double *Wk = ctx->Wb + (size_t)k * n;
+        const double *Rprev = ctx->Rb + (size_t)(k - 1) * n;
+        k_copy<<<G, kThreads, 0, s>>>(n, Rprev, Wk);
+        // modified Gram-Schmidt: Wk -= <w_j, Wk> w_j for j = 0..k-1, then normalise
+        k_dot_part<<<G, kThreads, 0, s>>>(n, ctx->Wb, Wk, part);
+        launch_finalize(part, 1, scal + S_DOT, s);
+        for (int j = 0; j < k; ++j) {
+            const double *wj = ctx->Wb + (size_t)j * n;
+            const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
+            k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, part);
+            launch_finalize(part, 1, scal + S_DOT, s);
+        }
+        k_normalize<<<G, kThreads, 0, s>>>(n, scal, Wk);
+        rc = coulomb_apply_impl(ctx, st->R, Wk, prm->sigma, ctx->phi, nullptr, nullptr, nullptr,
+                                false, s);
+        if (rc) return rc;
+        k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, u, part);
+        launch_finalize(part, 1, scal + S_MU, s);
+        k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, Wk, u, scal, ctx->Rb + (size_t)k * n);
+    }
+    // 6. normal equations and Kf = W c
+    const int nO = m * (m + 1) / 2;
+    k_normal_part<<<G, kThreads, 0, s>>>(n, m, ctx->Rb, ctx->fvec, part);
+    launch_finalize(part, nO + m, scal + S_OM, s);
+    k_solve_small<<<1, 32, 0, s>>>(m, scal);
+    k_kf<<<G, kThreads, 0, s>>>(n, m, ctx->Wb, scal, st->Kf);
+    k_charge_energies<<<1, 1, 0, s>>>(ctx->p.q_tot, m + 1, scal, st->energies);
+    return cuda_check(ctx, cudaGetLastError(), "shadow evaluate launch");
+}
+
+int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
+    const int n = (int)ctx->n;
+    k_advance<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
+                                              dissipation(ctx->p.dissipation_k), prm->mass, st->F,
+                                              st->Kf, st->R, st->V, st->n_hist);
+    double d2 = 0.0;
+    int rc = nl_displacement(ctx, st->R, s, &d2);
+    if (rc) return rc;
+    const double half = 0.5 * ctx->p.skin;
+    if (!(d2 <= half * half)) {
+        rc = nl_build(ctx, st->R, s);
+        if (rc) return rc;
+    }
+    return QEQ_OK;
+}
+
+int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
+                  cudaStream_t s) {
+    const int n = (int)ctx->n;
+    k_finish<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass, st->F,
+                                             st->V, ctx->part);
+    launch_finalize(ctx->part, 1, ctx->scal + S_KE, s);
+    k_total_energy<<<1, 1, 0, s>>>(ctx->scal, st->energies);
+    return cuda_check(ctx, cudaGetLastError(), "shadow finish launch");
+}
+
+// Built-in short-range stand-in is added in a later translation unit; until then the
+// model reports that it is unavailable.
+int short_range_forces(qeq_ctx *ctx, const double *, const double *, double *, double *,
+                       cudaStream_t) {
+    return set_error(ctx, QEQ_ERR_UNSUPPORTED, "short-range water model not built in");
+}
+
+}  // namespace qeq
