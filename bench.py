@@ -1,0 +1,513 @@
+#!/usr/bin/env python
+"""Benchmark of the shadow-QEq Coulomb hot path on GB300.
+
+Workload: water box of 100,000 molecules (300,000 atoms, L = 144.13 A, seeded
+synthetic recipe), alpha 0.34 1/A, r_c 8 A, skin 1 A, smooth PME 144^3 of
+order 4, Krylov rank 2, dissipation window K_d 5, dt 0.5 fs.
+
+A step is one shadow XL-BOMD step.  It covers the integrator, the skin check,
+m + 1 = 3 Coulomb applies (neighbour list, real space, PME spread / FFT /
+influence / FFT / gather, self term), shadow charges, forces, and the Krylov
+kernel.  The headline value is FP32-mixed steps/s.  The same line also
+reports the FP64 steps/s, applies/s for both modes, neighbour-build time and
+p50 / p99 step times.
+
+Runs: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+N > 1 is launched by torchrun: each rank runs an independent replica on its own
+GPU (weak scaling, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Coulomb applies/s & shadow-MD steps/s at 300k atoms, FP32-mixed vs FP64; p50/p99 ms"
+UNIT = "steps/s"
+N_MOL = 100_000
+SEED = 2504
+ALPHA, R_CUT, SKIN, MESH, ORDER, RANK, KD, DT = 0.34, 8.0, 1.0, 144, 4, 2, 5, 0.5
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+# algorithmic work per directed real-space pair inside r_c (FMA-pipe operations)
+PAIR_OPS = 40
+SM_COUNT, FP32_LANES, FP64_LANES = 152, 128, 2
+T_EV = 0.025852  # k_B * 300 K in eV
+
+
+def workload_config(n_mol=N_MOL):
+    from workloads import water_box_length
+
+    L = water_box_length(n_mol)
+    return {
+        "workload": f"water box {n_mol:,} molecules ({3 * n_mol:,} atoms), L {L:.2f} A, "
+                    f"alpha {ALPHA}, r_c {R_CUT} A, skin {SKIN} A, PME {MESH}^3 order {ORDER}, "
+                    f"Krylov rank {RANK}, K_d {KD}, dt {DT} fs, shadow XL-BOMD step",
+        "n_atoms": 3 * n_mol,
+        "box_A": round(L, 4),
+        "seed": SEED,
+        "l2": "flushed between timed steps (256 MiB write, not timed)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * p / 100.0
+    lo, hi = math.floor(k), math.ceil(k)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+def make_system(qg, w, precision, device):
+    import torch
+
+    p = qg.make_params(w.n_atoms, w.box, alpha=ALPHA, r_cut=R_CUT, skin=SKIN,
+                       mesh=(MESH, MESH, MESH), order=ORDER, precision=precision,
+                       krylov_rank=RANK, dissipation_k=KD, dt=DT)
+    with torch.cuda.device(device):
+        return qg.System(p, device=device.index)
+
+
+def initial_state(w, seed):
+    """Maxwell-Boltzmann velocities at 300 K (zero total momentum)."""
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal(w.R.shape) * np.sqrt(T_EV / (w.mass[:, None] * 103.6427))
+    V -= (w.mass[:, None] * V).sum(0) / w.mass.sum()
+    return V
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
+    import torch
+
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    sysm = make_system(qg, w, precision, device)
+    R, sigma = t(w.R), t(w.sigma)
+    res = {}
+    with torch.cuda.stream(stream):
+        # neighbour build time (one sync per build is part of the call)
+        nl_ms = []
+        for k in range(3):
+            flush.zero_()
+            t0 = time.perf_counter()
+            sysm.neighbor_build(R, stream)
+            nl_ms.append((time.perf_counter() - t0) * 1e3)
+        res["neighbor_build_ms"] = round(min(nl_ms), 3)
+        # Coulomb applies (full potential + field)
+        q = t(np.random.default_rng(1).standard_normal(w.n_atoms) * 0.3)
+        for _ in range(warmup):
+            sysm.apply(R, q, sigma, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sysm.apply(R, q, sigma, stream=stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(device)
+        ams = [a.elapsed_time(b) for a, b in ev]
+        res["apply_ms_p50"] = round(pct(ams, 50), 4)
+        res["apply_ms_p99"] = round(pct(ams, 99), 4)
+        res["applies_per_s"] = round(1e3 / statistics.mean(ams), 2)
+
+        # shadow MD: initial n from the shadow charges of n = 0
+        V0 = t(initial_state(w, SEED + 1))
+        md = qg.ShadowMD(sysm, t(w.chi), t(w.eta), sigma, t(w.mass), R, V0,
+                         torch.zeros(w.n_atoms, dtype=torch.float64, device=device))
+        md.init(stream)
+        md.n_hist.copy_(md.q.reshape(1, -1).expand_as(md.n_hist))
+        md.init(stream)
+        for _ in range(warmup):
+            md.step(1, stream)
+        torch.cuda.synchronize(device)
+        c0 = qg.qeq_get_counters(sysm.ctx)
+        if profile:
+            qg.qeq_profile_enable(sysm.ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        e_tot = []
+        sampler = ClockSampler(device.index)
+        with sampler:
+            torch.cuda.synchronize(device)
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                md.step(1, stream)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize(device)
+        sms = [a.elapsed_time(b) for a, b in ev]
+        prof = qg.qeq_profile_read(sysm.ctx) if profile else None
+        if profile:
+            qg.qeq_profile_enable(sysm.ctx, False)
+        c1 = qg.qeq_get_counters(sysm.ctx)
+        e = md.energy_dict()
+        res.update({
+            "steps_per_s": round(1e3 / statistics.mean(sms), 3),
+            "ms_per_step": round(statistics.mean(sms), 4),
+            "step_ms_p50": round(pct(sms, 50), 4),
+            "step_ms_p99": round(pct(sms, 99), 4),
+            "gpu_launches": c1[0] - c0[0],
+            "neighbor_rebuilds": c1[1] - c0[1],
+            "applies_in_timed_steps": c1[2] - c0[2],
+            "clocks": sampler.summary(),
+            "final_energy_eV": {k: round(v, 6) for k, v in e.items()},
+        })
+        res["_step_ms_sum"] = float(sum(sms))
+        res["_profile"] = prof
+        res["_md"] = md
+        res["_sys"] = sysm
+    return res
+
+
+def e2e_steps(qg, md, steps, stream, device):
+    """Same step through the C ABI with HOST buffers: pinned H2D of the state and
+    parameters, the step, and D2H of the results, all inside the timed region."""
+    import torch
+
+    names_in = ["R", "V", "F", "Kf", "n_hist", "chi", "eta", "sigma", "mass"]
+    dev_in = {k: getattr(md, k) for k in names_in}
+    host_in = {k: v.cpu().pin_memory() for k, v in dev_in.items()}
+    names_out = ["R", "V", "F", "q", "energies"]
+    host_out = {k: torch.empty_like(getattr(md, k), device="cpu").pin_memory() for k in names_out}
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize(device)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            for k in names_in:
+                dev_in[k].copy_(host_in[k], non_blocking=True)
+            md.step(1, stream)
+            for k in names_out:
+                host_out[k].copy_(getattr(md, k), non_blocking=True)
+            stream.synchronize()
+            for k in ("R", "V", "F"):  # the caller keeps the advanced state on the host
+                host_in[k].copy_(host_out[k])
+        t1.record(stream)
+        torch.cuda.synchronize(device)
+    ms = t0.elapsed_time(t1) / steps
+    return {"value": round(1e3 / ms, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4)}
+
+
+def roofline(res, precision, n_pairs_rc, peaks):
+    """Roofline of the dominant phase of the timed steps (CUDA events on the launch stream)."""
+    prof = res.get("_profile") or {}
+    if not prof:
+        return None
+    name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    share = ms / max(1e-9, sum(v[0] for v in prof.values()))
+    avg_ms = ms / max(1, cnt)
+    clock = 2.07e9
+    if name == "real_space":
+        lanes = FP32_LANES if precision == "fp32_mixed" else FP64_LANES
+        peak = SM_COUNT * lanes * clock / 1e12  # FMA-pipe Tops/s at the maximum SM clock
+        achieved = n_pairs_rc * PAIR_OPS / (avg_ms * 1e-3) / 1e12
+        out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
+               "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+               "traffic": None, "peak_source": f"{SM_COUNT} SMs x {lanes} lanes x 2.07 GHz",
+               "pairs_per_s": round(n_pairs_rc / (avg_ms * 1e-3), 1)}
+    else:
+        gbs = peaks.get("hbm_gbs", 6800.0)
+        out = {"kernel": name, "bound": "hbm", "achieved": None, "peak": gbs, "unit": "GB/s",
+               "frac": None, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    out.update({"avg_launch_ms": round(avg_ms, 4), "launches": cnt, "share_of_profiled": round(share, 4),
+                "phases_ms": {k: round(v[0], 3) for k, v in prof.items()}})
+    return out
+
+
+def count_pairs_within_rc(sysm, w):
+    """Directed real-space pairs inside r_c at the positions of the last neighbour build.
+
+    The exported images refer to positions wrapped as x - L floor(x / L).
+    """
+    counts, nbr, shift = sysm.neighbor_export()
+    box = np.asarray(w.box, dtype=np.float64)
+    xw = w.R - box * np.floor(w.R / box)
+    mask = np.arange(nbr.shape[1])[None, :] < counts[:, None]
+    rows = np.nonzero(mask)[0]
+    cols = nbr[mask]
+    d = xw[cols] - xw[rows] + shift[mask].astype(np.float64) * box
+    return int(np.count_nonzero(np.einsum("ij,ij->i", d, d) < R_CUT * R_CUT))
+
+
+def cpu_baseline(w):
+    """The oracle's shadow-step evaluation at full size, timed on the host cores."""
+    from oracle import ewald, native, qeq
+
+    def coul(R, x, need_field=True):
+        o = ewald.coulomb_apply(R, x, w.sigma, w.box, ALPHA, R_CUT, recip="pme",
+                                mesh=(MESH, MESH, MESH), order=ORDER, gaussian_self=True)
+        return o["v"], o["E"]
+
+    osys = qeq.ShadowSystem(coul, w.chi, w.eta, w.mass, rank=RANK, dt=DT, k_d=KD)
+    n0 = np.zeros(w.n_atoms)
+    t0 = time.perf_counter()
+    osys.evaluate(w.R, n0)
+    dt_s = time.perf_counter() - t0
+    return {"value": round(1.0 / dt_s, 5), "unit": UNIT, "cores": native.num_threads(),
+            "kind": "oracle",
+            "sample": f"one full shadow-step evaluation of the {w.n_atoms:,}-atom box "
+                      f"({RANK + 1} Coulomb applies: cell-list real space in C/OpenMP + numpy "
+                      f"PME {MESH}^3 + Krylov), {dt_s:.1f} s wall"}
+
+
+def ours(args):
+    import torch
+
+    import paper_2503_21176_gb300 as qg
+    from workloads import water_box
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE {world}")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+    qg.load()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        peaks = {"hbm_gbs": 6800.0, "source": "fallback"}
+
+    w = water_box(args.n_mol, seed=SEED + rank)
+    stream = torch.cuda.Stream(device)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    modes = ["fp32_mixed"] if args.no_fp64 else ["fp32_mixed", "fp64"]
+    results = {}
+    for m in modes:
+        if dist is not None:
+            dist.barrier()
+        results[m] = run_mode(qg, w, m, device, args.steps, args.warmup, stream, flush,
+                              profile=True)
+
+    head = results["fp32_mixed"]
+    sysm, md = head["_sys"], head["_md"]
+    # directed pairs inside r_c at the initial positions (fresh list) for the roofline
+    sysm.neighbor_build(torch.as_tensor(w.R, dtype=torch.float64, device=device), stream)
+    n_pairs = count_pairs_within_rc(sysm, w)
+
+    e2e = e2e_steps(qg, md, max(3, args.steps // 2), stream, device)
+
+    # max over ranks of the timed region
+    total_ms = head["_step_ms_sum"]
+    if dist is not None:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        dist.barrier()
+    value = world * args.steps / (total_ms * 1e-3)
+
+    line = None
+    if rank == 0:
+        roof = roofline(head, "fp32_mixed", n_pairs, peaks)
+        fp64 = None
+        if "fp64" in results:
+            r64 = results["fp64"]
+            fp64 = {k: v for k, v in r64.items() if not k.startswith("_")}
+            fp64["roofline"] = roofline(r64, "fp64", n_pairs, peaks)
+        cfg = workload_config(args.n_mol)
+        cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+        line = {
+            "metric": METRIC,
+            "value": round(value, 3),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 (FP32-mixed: f32 pair/PME math, f64 sums, Krylov, integrator)",
+            "data": "synthetic",
+            "config": cfg,
+            "fp32_mixed": {k: v for k, v in head.items() if not k.startswith("_")},
+            "fp64": fp64,
+            "directed_pairs_within_rc": n_pairs,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": head["gpu_launches"],
+            "clocks": head["clocks"],
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+    for m in list(results):
+        results[m]["_sys"].close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import ewald, native, qeq
+    from workloads import water_box
+
+    w = water_box(args.n_mol, seed=SEED)
+
+    def coul(R, x, need_field=True):
+        o = ewald.coulomb_apply(R, x, w.sigma, w.box, ALPHA, R_CUT, recip="pme",
+                                mesh=(MESH, MESH, MESH), order=ORDER, gaussian_self=True)
+        return o["v"], o["E"]
+
+    osys = qeq.ShadowSystem(coul, w.chi, w.eta, w.mass, rank=RANK, dt=DT, k_d=KD)
+    st = osys.init_state(w.R, initial_state(w, SEED + 1), np.zeros(w.n_atoms))
+    budget_s = args.reference_budget
+    t_start = time.perf_counter()
+    times = []
+    planned = args.warmup + args.steps
+    for k in range(planned):
+        t0 = time.perf_counter()
+        st = osys.step(st)
+        times.append(time.perf_counter() - t0)
+        spent = time.perf_counter() - t_start
+        if spent + times[-1] > budget_s and k + 1 >= 2:
+            break
+    timed = times[min(args.warmup, len(times) - 1):] if len(times) > 1 else times
+    ms = 1e3 * statistics.mean(timed)
+    value = 1e3 / ms
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 5),
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": len(timed),
+        "warmup": len(times) - len(timed),
+        "ms_per_step": round(ms, 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args.n_mol),
+        "cpu_baseline": {
+            "value": round(value, 5), "unit": UNIT, "cores": native.num_threads(), "kind": "oracle",
+            "sample": f"{len(timed)} full shadow XL-BOMD steps of the {w.n_atoms:,}-atom box "
+                      f"(FP64 oracle: C/OpenMP cell-list real space + numpy PME), "
+                      f"capped at {budget_s:.0f} s total",
+        },
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-mol", type=int, default=N_MOL)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-budget", type=float, default=200.0,
+                    help="seconds of oracle work the reference arm may spend")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -239,6 +239,32 @@ int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, vo
 int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int32_t n_steps,
                    void *stream);
 
+/*
+ * Tracing.  The paper reports a per-component time breakdown of its MD runs
+ * (Sec. 4.2.3, Fig. MD_simulation).  These calls give the same breakdown per
+ * library phase, measured with CUDA events on the caller's stream.
+ * Phase ids 0..9: neighbor_build, gather_in, real_space, pme_spread,
+ * fft_forward, pme_influence, fft_inverse, pme_gather, shadow_reductions,
+ * integrate (qeq_profile_phase_name gives the strings).
+ */
+#define QEQ_NUM_PHASES 10
+
+/* on = 1 starts recording event pairs around every phase (pool of 4096
+ * pairs; pairs beyond the pool are dropped).  on = 0 stops.  Resets the pool. */
+int qeq_profile_enable(qeq_ctx *ctx, int on);
+
+/* Synchronise the device, then return the accumulated milliseconds and launch
+ * counts per phase since the last read.  The host arrays ms[n_phases] and
+ * counts[n_phases] are both nullable.  The totals are reset afterwards. */
+int qeq_profile_read(qeq_ctx *ctx, double *ms, int64_t *counts, int n_phases);
+
+/* Name of a phase id, or "" when out of range. */
+const char *qeq_profile_phase_name(int phase);
+
+/* Host int64 out4[4]: this library's kernel launches (cuFFT excluded),
+ * neighbour builds, Coulomb applies and cuFFT executions since creation. */
+int qeq_get_counters(const qeq_ctx *ctx, int64_t *out4);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ from ._lib import (  # noqa: F401
     qeq_coulomb_apply,
     qeq_create,
     qeq_destroy,
+    qeq_get_counters,
     qeq_get_sizes,
     qeq_last_error,
     qeq_neighbor_build,
@@ -34,10 +35,15 @@ from ._lib import (  # noqa: F401
     qeq_neighbor_export,
     qeq_params,
     qeq_params_default,
+    qeq_profile_enable,
+    qeq_profile_phase_name,
+    qeq_profile_read,
     qeq_shadow_init,
     qeq_shadow_run,
     qeq_shadow_step,
 )
+
+from .autograd import CoulombEnergy, coulomb_energy  # noqa: E402,F401
 
 PRECISIONS = {"fp64": QEQ_FP64, "fp32_mixed": QEQ_FP32_MIXED}
 

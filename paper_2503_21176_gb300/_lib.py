@@ -104,6 +104,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_shadow_step.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state), P]
     L.qeq_shadow_run.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state),
                                  ctypes.c_int32, P]
+    L.qeq_profile_enable.argtypes = [P, ctypes.c_int]
+    L.qeq_profile_read.argtypes = [P, P, P, ctypes.c_int]
+    L.qeq_profile_phase_name.argtypes = [ctypes.c_int]
+    L.qeq_profile_phase_name.restype = ctypes.c_char_p
+    L.qeq_get_counters.argtypes = [P, P]
+    for name in ("qeq_profile_enable", "qeq_profile_read", "qeq_get_counters"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("qeq_create", "qeq_get_sizes", "qeq_neighbor_build", "qeq_neighbor_export",
                  "qeq_neighbor_displacement", "qeq_coulomb_apply", "qeq_shadow_init",
                  "qeq_shadow_step", "qeq_shadow_run"):
@@ -234,3 +241,34 @@ def qeq_shadow_step(ctx, prm: qeq_md_params, st: qeq_md_state, stream=None) -> N
 def qeq_shadow_run(ctx, prm: qeq_md_params, st: qeq_md_state, n_steps: int, stream=None) -> None:
     _check(ctx, load().qeq_shadow_run(ctx, ctypes.byref(prm), ctypes.byref(st), int(n_steps),
                                       _stream(stream)))
+
+
+QEQ_NUM_PHASES = 10
+
+
+def qeq_profile_enable(ctx, on: bool) -> None:
+    _check(ctx, load().qeq_profile_enable(ctx, int(bool(on))))
+
+
+def qeq_profile_read(ctx):
+    """{phase name: (milliseconds, launches)} accumulated since the last read (synchronises)."""
+    import numpy as np
+
+    ms = np.zeros(QEQ_NUM_PHASES, dtype=np.float64)
+    cnt = np.zeros(QEQ_NUM_PHASES, dtype=np.int64)
+    _check(ctx, load().qeq_profile_read(ctx, ms.ctypes.data_as(ctypes.c_void_p),
+                                        cnt.ctypes.data_as(ctypes.c_void_p), QEQ_NUM_PHASES))
+    return {qeq_profile_phase_name(k): (float(ms[k]), int(cnt[k])) for k in range(QEQ_NUM_PHASES)}
+
+
+def qeq_profile_phase_name(phase: int) -> str:
+    return load().qeq_profile_phase_name(int(phase)).decode()
+
+
+def qeq_get_counters(ctx):
+    """(kernel launches, neighbour builds, Coulomb applies, cuFFT executions)."""
+    import numpy as np
+
+    out = np.zeros(4, dtype=np.int64)
+    _check(ctx, load().qeq_get_counters(ctx, out.ctypes.data_as(ctypes.c_void_p)))
+    return tuple(int(x) for x in out)

@@ -68,6 +68,7 @@ static int validate(const qeq_params *p) {
 static void destroy(qeq_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
     shadow_free(ctx);
     coulomb_free(ctx);
     nl_free(ctx);
@@ -211,5 +212,67 @@ QEQ_API int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state 
         int rc = qeq_shadow_step(ctx, prm, st, stream);
         if (rc) return rc;
     }
+    return QEQ_OK;
+}
+
+static const char *kPhaseNames[kNumPhases] = {
+    "neighbor_build", "gather_in", "real_space", "pme_spread", "fft_forward",
+    "pme_influence",  "fft_inverse", "pme_gather", "shadow_reductions", "integrate"};
+
+QEQ_API int qeq_profile_enable(qeq_ctx *ctx, int on) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    Profiler &P = ctx->prof;
+    if (on && P.ev.empty()) {
+        const int pool = 8192;
+        P.ev.resize(pool);
+        P.phase.resize(pool / 2);
+        for (int k = 0; k < pool; ++k) {
+            cudaError_t e = cudaEventCreate(&P.ev[k]);
+            if (e != cudaSuccess) {
+                P.ev.resize(k);
+                return cuda_check(ctx, e, "profiler event pool");
+            }
+        }
+    }
+    P.on = on != 0;
+    P.used = 0;
+    P.open = false;
+    return QEQ_OK;
+}
+
+QEQ_API int qeq_profile_read(qeq_ctx *ctx, double *ms, int64_t *counts, int n_phases) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    Profiler &P = ctx->prof;
+    int rc = cuda_check(ctx, cudaDeviceSynchronize(), "profile read");
+    if (rc) return rc;
+    for (int k = 0; k < P.used / 2; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, P.ev[2 * k], P.ev[2 * k + 1]) == cudaSuccess) {
+            P.ms[P.phase[k]] += t;
+            P.count[P.phase[k]] += 1;
+        }
+    }
+    cudaGetLastError();
+    P.used = 0;
+    P.open = false;
+    for (int k = 0; k < n_phases && k < kNumPhases; ++k) {
+        if (ms) ms[k] = P.ms[k];
+        if (counts) counts[k] = P.count[k];
+        P.ms[k] = 0.0;
+        P.count[k] = 0;
+    }
+    return QEQ_OK;
+}
+
+QEQ_API const char *qeq_profile_phase_name(int phase) {
+    return (phase >= 0 && phase < kNumPhases) ? kPhaseNames[phase] : "";
+}
+
+QEQ_API int qeq_get_counters(const qeq_ctx *ctx, int64_t *out4) {
+    if (!ctx || !out4) return QEQ_ERR_INVALID;
+    out4[0] = ctx->launches;
+    out4[1] = ctx->n_builds;
+    out4[2] = ctx->applies;
+    out4[3] = ctx->fft_execs;
     return QEQ_OK;
 }

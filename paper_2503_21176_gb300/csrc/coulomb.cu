@@ -455,9 +455,13 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     T4 *xq = f64 ? (T4 *)ctx->xq64 : (T4 *)ctx->xq32;
     T *sg = f64 ? (T *)ctx->sg64 : (T *)ctx->sg32;
     const qeq_params &p = ctx->p;
+    ctx->applies++;
+    prof_begin(ctx, kPhGatherIn, s);
     k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
         n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
         ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac);
+    prof_end(ctx, s);
+    ctx->launches++;
 
     RealArgs ra;
     ra.n = n;
@@ -465,6 +469,7 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.alpha = p.alpha;
     ra.rc2 = p.r_cut * p.r_cut;
     ra.ke = p.k_e;
+    prof_begin(ctx, kPhReal, s);
     if (f64) {
         if (need_field)
             k_real64<true><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
@@ -481,24 +486,38 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                                                              (float *)sg, ctx->v_s, ctx->E_s);
     }
 
+    prof_end(ctx, s);
+    ctx->launches++;
+    prof_begin(ctx, kPhSpread, s);
     cudaMemsetAsync(ctx->mesh, 0, sizeof(T) * ctx->mesh_n, s);
     dispatch_spread<T>(ctx, ctx->sbase, ctx->sfrac, s);
+    prof_end(ctx, s);
+    ctx->launches++;
     cufftResult cr;
     cr = cufftSetStream(ctx->plan_r2c, s);
     if (cr == CUFFT_SUCCESS) cr = cufftSetStream(ctx->plan_c2r, s);
     if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftSetStream failed (%d)", (int)cr);
+    prof_begin(ctx, kPhFftFwd, s);
     if (f64)
         cr = cufftExecD2Z(ctx->plan_r2c, (cufftDoubleReal *)ctx->mesh, (cufftDoubleComplex *)ctx->meshc);
     else
         cr = cufftExecR2C(ctx->plan_r2c, (cufftReal *)ctx->mesh, (cufftComplex *)ctx->meshc);
+    prof_end(ctx, s);
+    ctx->fft_execs++;
     if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "forward FFT failed (%d)", (int)cr);
+    prof_begin(ctx, kPhInfluence, s);
     k_influence<T><<<kRedBlocks, kThreads, 0, s>>>(
         ctx->meshc_n, ctx->K[2] / 2 + 1, ctx->K[2], (typename C2<T>::type *)ctx->meshc,
         (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+    prof_end(ctx, s);
+    ctx->launches++;
+    prof_begin(ctx, kPhFftInv, s);
     if (f64)
         cr = cufftExecZ2D(ctx->plan_c2r, (cufftDoubleComplex *)ctx->meshc, (cufftDoubleReal *)ctx->mesh);
     else
         cr = cufftExecC2R(ctx->plan_c2r, (cufftComplex *)ctx->meshc, (cufftReal *)ctx->mesh);
+    prof_end(ctx, s);
+    ctx->fft_execs++;
     if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "inverse FFT failed (%d)", (int)cr);
 
     GatherArgs ga;
@@ -509,11 +528,17 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ga.sz = ctx->K[2] / p.box[2];
     ga.self_coef = p.k_e * (-kTwoOverSqrtPi * p.alpha);
     ga.gauss_coef = p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0;
+    prof_begin(ctx, kPhGatherOut, s);
     if (need_field)
         dispatch_gather<T, true>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, E, F, s);
     else
         dispatch_gather<T, false>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, nullptr, nullptr, s);
-    if (energy4) k_finalize<<<4, kThreads, 0, s>>>(ctx->part, energy4);
+    prof_end(ctx, s);
+    ctx->launches++;
+    if (energy4) {
+        k_finalize<<<4, kThreads, 0, s>>>(ctx->part, energy4);
+        ctx->launches++;
+    }
     return cuda_check(ctx, cudaGetLastError(), "coulomb apply launch");
 }
 

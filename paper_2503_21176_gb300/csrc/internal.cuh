@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "qeq.h"
 
@@ -39,6 +40,32 @@ enum Flag { kFlagMaxRow = 0, kFlagNonFinite = 1, kNumFlags = 4 };
 // Device scalar table (double).  Slot 4 holds the last max displacement^2;
 // shadow.cu uses slots 32..127 for its reductions.
 enum Scal { kScMaxDisp2 = 4, kNumScal = 128 };
+
+// Phases timed by the optional CUDA-event profiler (qeq_profile_*).
+enum Phase {
+    kPhNeighbor = 0,
+    kPhGatherIn,
+    kPhReal,
+    kPhSpread,
+    kPhFftFwd,
+    kPhInfluence,
+    kPhFftInv,
+    kPhGatherOut,
+    kPhShadow,
+    kPhIntegrate,
+    kNumPhases
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // pool of event pairs, recorded in order
+    std::vector<int> phase;       // phase of pair k
+    int used = 0;                 // events used since the last read
+    bool open = false;
+    double ms[kNumPhases] = {};
+    int64_t count[kNumPhases] = {};
+    int64_t dropped = 0;
+};
 
 }  // namespace qeq
 
@@ -107,6 +134,12 @@ struct qeq_ctx {
     double *Rb = nullptr;      // [m][N] J applied to the basis
     double *F_short = nullptr; // [N][3]
     double *energy4 = nullptr; // [4] energy parts of the last apply
+
+    // ---- tracing ----
+    qeq::Profiler prof;
+    int64_t launches = 0;     // kernels of this library launched (cuFFT excluded)
+    int64_t applies = 0;      // Coulomb applies
+    int64_t fft_execs = 0;    // cuFFT executions
 };
 
 namespace qeq {
@@ -177,6 +210,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
         }
     }
     __syncthreads();
+}
+
+// Record the start / end event of a profiled phase on stream s (no-op when off).
+inline void prof_begin(qeq_ctx *c, int ph, cudaStream_t s) {
+    Profiler &P = c->prof;
+    if (!P.on || P.open) return;
+    if (P.used + 2 > (int)P.ev.size()) {
+        ++P.dropped;
+        return;
+    }
+    cudaEventRecord(P.ev[P.used], s);
+    P.phase[P.used / 2] = ph;
+    P.open = true;
+}
+
+inline void prof_end(qeq_ctx *c, cudaStream_t s) {
+    Profiler &P = c->prof;
+    if (!P.on || !P.open) return;
+    cudaEventRecord(P.ev[P.used + 1], s);
+    P.used += 2;
+    P.open = false;
 }
 
 inline int grid_for(int64_t n, int threads = kThreads) {

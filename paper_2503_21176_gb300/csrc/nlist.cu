@@ -349,6 +349,8 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
 
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
     const int n = (int)ctx->n;
+    prof_begin(ctx, kPhNeighbor, s);
+    ctx->launches += 5;
     cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s);
     cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
     k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(
@@ -362,6 +364,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
         ctx->ncell, ctx->cell_start, ctx->tmp_list, R, ctx->wrap_off, ctx->perm, ctx->cell_s,
         ctx->xs64, ctx->xs32);
     launch_emit(ctx, s);
+    prof_end(ctx, s);
     for (int attempt = 0; attempt < 4; ++attempt) {
         cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int32_t) * kNumFlags,
                         cudaMemcpyDeviceToHost, s);
@@ -380,7 +383,10 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
             return rc;
         }
         cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
+        prof_begin(ctx, kPhNeighbor, s);
         launch_emit(ctx, s);
+        prof_end(ctx, s);
+        ctx->launches++;
     }
     ctx->list_valid = true;
     ctx->n_builds++;
@@ -388,8 +394,11 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
 }
 
 int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_disp2) {
+    prof_begin(ctx, kPhIntegrate, s);
     k_max_disp2<<<kRedBlocks, kThreads, 0, s>>>((int)ctx->n, R, ctx->R_build, ctx->part);
     k_max_final<<<1, kThreads, 0, s>>>(kRedBlocks, ctx->part, ctx->scal + kScMaxDisp2);
+    prof_end(ctx, s);
+    ctx->launches += 2;
     if (max_disp2) {
         cudaMemcpyAsync(ctx->h_scal + kScMaxDisp2, ctx->scal + kScMaxDisp2, sizeof(double),
                         cudaMemcpyDeviceToHost, s);

@@ -383,73 +383,97 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     double *part = ctx->part;
     double *scal = ctx->scal;
     const int G = kRedBlocks;
+    auto fin = [&](int nslots, int slot0) {
+        launch_finalize(part, nslots, scal + slot0, s);
+        ctx->launches += 2;  // the partial kernel before it, and the finalize
+    };
 
     // short-range stand-in (or zero)
+    prof_begin(ctx, kPhShadow, s);
     if (ctx->p.short_range == QEQ_SHORT_WATER) {
         int rc = short_range_forces(ctx, st->R, prm->mass, ctx->F_short, scal + S_SHORT, s);
         if (rc) return rc;
     } else {
         cudaMemsetAsync(scal + S_SHORT, 0, sizeof(double), s);
     }
+    prof_end(ctx, s);
 
     // 1. v[n], E[n]
     int rc = coulomb_apply_impl(ctx, st->R, nn, prm->sigma, ctx->v_n, ctx->E_n, nullptr, nullptr,
                                 true, s);
     if (rc) return rc;
     // 2. lambda and q[n] (Eq. diag_linear_qeq)
+    prof_begin(ctx, kPhShadow, s);
     k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, part);
-    launch_finalize(part, 2, scal + S_LAM, s);
+    fin(2, S_LAM);
     k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->v_n, nn, scal, st->q,
                                      ctx->fvec, part);
-    launch_finalize(part, 6, scal + S_CHG, s);
+    fin(6, S_CHG);
+    prof_end(ctx, s);
     // 3. Phi f, E[f]
     rc = coulomb_apply_impl(ctx, st->R, ctx->fvec, prm->sigma, ctx->phi, ctx->E_f, nullptr, nullptr,
                             true, s);
     if (rc) return rc;
     // 4. forces, w_1, r_1
+    prof_begin(ctx, kPhShadow, s);
     double *W0 = ctx->Wb, *R0 = ctx->Rb;
     k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
                                        ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr,
                                        ctx->fvec, u, scal, st->F, W0, ctx->phi, part);
-    launch_finalize(part, 1, scal + S_MU, s);
+    fin(1, S_MU);
     k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, W0, u, scal, R0);
+    ctx->launches++;
+    prof_end(ctx, s);
     // 5. further Krylov vectors
     for (int k = 1; k < m; ++k) {
         double *Wk = ctx->Wb + (size_t)k * n;
         const double *Rprev = ctx->Rb + (size_t)(k - 1) * n;
+        prof_begin(ctx, kPhShadow, s);
         k_copy<<<G, kThreads, 0, s>>>(n, Rprev, Wk);
+        ctx->launches++;
         // modified Gram-Schmidt: Wk -= <w_j, Wk> w_j for j = 0..k-1, then normalise
         k_dot_part<<<G, kThreads, 0, s>>>(n, ctx->Wb, Wk, part);
-        launch_finalize(part, 1, scal + S_DOT, s);
+        fin(1, S_DOT);
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
             k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, part);
-            launch_finalize(part, 1, scal + S_DOT, s);
+            fin(1, S_DOT);
         }
         k_normalize<<<G, kThreads, 0, s>>>(n, scal, Wk);
+        ctx->launches++;
+        prof_end(ctx, s);
         rc = coulomb_apply_impl(ctx, st->R, Wk, prm->sigma, ctx->phi, nullptr, nullptr, nullptr,
                                 false, s);
         if (rc) return rc;
+        prof_begin(ctx, kPhShadow, s);
         k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, u, part);
-        launch_finalize(part, 1, scal + S_MU, s);
+        fin(1, S_MU);
         k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, Wk, u, scal, ctx->Rb + (size_t)k * n);
+        ctx->launches++;
+        prof_end(ctx, s);
     }
     // 6. normal equations and Kf = W c
+    prof_begin(ctx, kPhShadow, s);
     const int nO = m * (m + 1) / 2;
     k_normal_part<<<G, kThreads, 0, s>>>(n, m, ctx->Rb, ctx->fvec, part);
-    launch_finalize(part, nO + m, scal + S_OM, s);
+    fin(nO + m, S_OM);
     k_solve_small<<<1, 32, 0, s>>>(m, scal);
     k_kf<<<G, kThreads, 0, s>>>(n, m, ctx->Wb, scal, st->Kf);
     k_charge_energies<<<1, 1, 0, s>>>(ctx->p.q_tot, m + 1, scal, st->energies);
+    ctx->launches += 3;
+    prof_end(ctx, s);
     return cuda_check(ctx, cudaGetLastError(), "shadow evaluate launch");
 }
 
 int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
+    prof_begin(ctx, kPhIntegrate, s);
     k_advance<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
                                               dissipation(ctx->p.dissipation_k), prm->mass, st->F,
                                               st->Kf, st->R, st->V, st->n_hist);
+    prof_end(ctx, s);
+    ctx->launches++;
     double d2 = 0.0;
     int rc = nl_displacement(ctx, st->R, s, &d2);
     if (rc) return rc;
@@ -464,10 +488,13 @@ int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cud
 int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
                   cudaStream_t s) {
     const int n = (int)ctx->n;
+    prof_begin(ctx, kPhIntegrate, s);
     k_finish<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass, st->F,
                                              st->V, ctx->part);
     launch_finalize(ctx->part, 1, ctx->scal + S_KE, s);
     k_total_energy<<<1, 1, 0, s>>>(ctx->scal, st->energies);
+    prof_end(ctx, s);
+    ctx->launches += 3;
     return cuda_check(ctx, cudaGetLastError(), "shadow finish launch");
 }
 
