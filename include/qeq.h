@@ -163,6 +163,44 @@ int qeq_neighbor_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int8_t *shi
 int qeq_neighbor_displacement(qeq_ctx *ctx, const double *R, double *max_disp2, void *stream);
 
 /*
+ * Allocation-free neighbour build.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc / cudaFree.  Examples
+ * are an engine plugin whose host owns all device memory through its own
+ * arena, a latency-critical loop that cannot take the device-wide
+ * synchronisation of cudaFree, and a process under a hard memory budget.
+ * It builds the same pair set as qeq_neighbor_build (same wrap, cells, FP64
+ * decision and strict r_list comparison) without a qeq_ctx.  The scratch is
+ * one file-scope device array of about 3.5 MB per device, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * Limits: n_atoms <= 32768, each box edge >= r_list / 2, and at most 32768
+ * cells (larger cells are used when the grid would not fit).  Larger inputs
+ * are rejected with QEQ_ERR_CAPACITY before any GPU work.
+ * R:       device [N][3] positions.     box: HOST double[3] orthorhombic edges.
+ * r_list:  list radius (pairs at exactly r_list excluded).
+ * width:   row capacity of nbr.
+ * counts:  device [N] int32 output, entries per row.
+ * nbr:     device [N][width] int32 output, row-major in original numbering.
+ *          Entry = j | (code << 24), where j is the neighbour atom id and
+ *          code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2) encodes the image,
+ *          so that the displacement is x_j - x_i + s * box.
+ * max_row: HOST int32 output (nullable).  When a row needs more than width
+ *          entries, the call returns QEQ_ERR_CAPACITY, writes the needed
+ *          width here, and leaves the rows truncated.
+ * Errors are reported through qeq_last_error(NULL).
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current.  Make that first
+ * call before any stream capture.  The call calls no cudaMalloc, cudaFree or
+ * allocating library routine.  It synchronises `stream` once to read the
+ * overflow and non-finite flags.  Every call reuses the same array and
+ * clears what must start at zero.  Calls whose GPU work overlaps (other
+ * streams, other host threads) race on the array and must be serialised.
+ */
+int qeq_neighbor_build_noalloc(const double *R, int64_t n_atoms, const double *box, double r_list,
+                               int32_t width, int32_t *counts, int32_t *nbr, int32_t *max_row,
+                               void *stream);
+
+/*
  * Coulomb apply: v = Phi q with its field (Sec. 3.4, matrix-free form of
  * C v = u o v + dE_Coul/dv).  Phi is Eq. ewald_real (over the current list,
  * plain truncation at r_cut, Gaussian-charge correction

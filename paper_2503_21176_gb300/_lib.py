@@ -104,6 +104,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_shadow_step.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state), P]
     L.qeq_shadow_run.argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state),
                                  ctypes.c_int32, P]
+    L.qeq_neighbor_build_noalloc.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int32,
+                                             P, P, ctypes.POINTER(ctypes.c_int32), P]
+    L.qeq_neighbor_build_noalloc.restype = ctypes.c_int
     L.qeq_profile_enable.argtypes = [P, ctypes.c_int]
     L.qeq_profile_read.argtypes = [P, P, P, ctypes.c_int]
     L.qeq_profile_phase_name.argtypes = [ctypes.c_int]
@@ -272,3 +275,31 @@ def qeq_get_counters(ctx):
     out = np.zeros(4, dtype=np.int64)
     _check(ctx, load().qeq_get_counters(ctx, out.ctypes.data_as(ctypes.c_void_p)))
     return tuple(int(x) for x in out)
+
+
+def qeq_neighbor_build_noalloc(R, box, r_list, counts, nbr, stream=None) -> None:
+    """Allocation-free neighbour build into caller buffers (see include/qeq.h).
+
+    R: CUDA float64 [N, 3]; counts: CUDA int32 [N]; nbr: CUDA int32 [N, width].
+    Raises QeqError (code -8 with the needed width in ``.needed_width``) when a
+    row does not fit.
+    """
+    import numpy as np
+
+    n = int(R.shape[0])
+    for t, name, dt in ((counts, "counts", torch.int32), (nbr, "nbr", torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA int32 tensor")
+    if tuple(counts.shape) != (n,) or nbr.dim() != 2 or nbr.shape[0] != n:
+        raise ValueError("counts must be [N] and nbr [N, width]")
+    boxh = np.ascontiguousarray(np.asarray(box, dtype=np.float64))
+    need = ctypes.c_int32(0)
+    rc = load().qeq_neighbor_build_noalloc(_dev(R, "R"), n, boxh.ctypes.data_as(ctypes.c_void_p),
+                                           float(r_list), int(nbr.shape[1]),
+                                           ctypes.c_void_p(counts.data_ptr()),
+                                           ctypes.c_void_p(nbr.data_ptr()), ctypes.byref(need),
+                                           _stream(stream))
+    if rc != QEQ_OK:
+        err = QeqError(rc, qeq_last_error(None))
+        err.needed_width = int(need.value)
+        raise err

@@ -16,6 +16,7 @@
 // (no fused multiply-add), so the emitted set is exactly the geometric one.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -444,3 +445,230 @@ int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr_out, int8_t *shift_out
 }
 
 }  // namespace qeq
+
+// ---------------------------------------------------------------------------
+// Allocation-free neighbour build (qeq_neighbor_build_noalloc).
+//
+// Some callers cannot call cudaMalloc / cudaFree.  One example is a plugin
+// inside an MD or serving engine that owns every byte of device memory
+// through its own arena.  Another is a latency-critical loop that cannot
+// afford the device-wide synchronisation cudaFree implies.  A third runs
+// under a hard memory budget where an allocation failure mid-run is not
+// acceptable.  For them this entry point keeps its scratch in one file-scope
+// device array of fixed size, so it needs no qeq_ctx.  That scratch holds the
+// cell histogram and offsets, the permutation, the wrap offsets and the
+// sorted positions.  The caller passes the inputs and the outputs.
+//
+// The array lives in every device that loads the library until the process
+// exits, and every call shares it.  Each call clears what must start at zero
+// (cell counts, flags).  Calls whose work overlaps on the GPU, on different
+// streams or from different host threads, race on the array: serialise them.
+// ---------------------------------------------------------------------------
+
+namespace qeq {
+
+namespace {
+
+constexpr int kNoAllocMaxAtoms = 32768;
+constexpr int kNoAllocMaxCells = 32768;
+
+struct NoAllocScratch {
+    double4_32a xs64[kNoAllocMaxAtoms];
+    float4 xs32[kNoAllocMaxAtoms];
+    double wrap_off[3 * kNoAllocMaxAtoms];
+    double R_build[3 * kNoAllocMaxAtoms];
+    int32_t cell_of[kNoAllocMaxAtoms];
+    int32_t tmp_list[kNoAllocMaxAtoms];
+    int32_t perm[kNoAllocMaxAtoms];
+    int32_t cell_s[kNoAllocMaxAtoms];
+    int32_t cell_count[kNoAllocMaxCells];
+    int32_t cell_start[kNoAllocMaxCells + 1];
+    int32_t cell_fill[kNoAllocMaxCells];
+    int32_t flags[kNumFlags];
+};
+
+// About 3.5 MB per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+// In host code g_noalloc_scratch is only a host-side stand-in for the symbol.
+// The device address comes from cudaGetSymbolAddress, once per device, with
+// that device current.
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(NoAllocScratch **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(nullptr, QEQ_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(nullptr, QEQ_ERR_UNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return set_error(nullptr, QEQ_ERR_CUDA, "cudaGetSymbolAddress: %s",
+                             cudaGetErrorString(e));
+        }
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = static_cast<NoAllocScratch *>(g_noalloc_addr[dev]);
+    return QEQ_OK;
+}
+
+// The pair emission of k_emit, written for the caller: rows and neighbour
+// indices in original atom numbering, rows row-major [N][width].
+__global__ void __launch_bounds__(kThreads)
+k_emit_original(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
+                const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
+                const int32_t *__restrict__ perm, int32_t *__restrict__ nbr,
+                int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int c = cell_s[i];
+    const int cx = c / (a.ncy * a.ncz), cy = (c / a.ncz) % a.ncy, cz = c % a.ncz;
+    const double4_32a xi = xs64[i];
+    const float4 xf = xs32[i];
+    int32_t *row = nbr + (size_t)perm[i] * a.width;
+    int count = 0;
+    for (int ox = -a.rx; ox <= a.rx; ++ox) {
+        const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
+        const double shx = __dmul_rn((double)sx, a.Lx);
+        const float shxf = (float)sx * a.Lfx;
+        for (int oy = -a.ry; oy <= a.ry; ++oy) {
+            const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
+            const double shy = __dmul_rn((double)sy, a.Ly);
+            const float shyf = (float)sy * a.Lfy;
+            for (int oz = -a.rz; oz <= a.rz; ++oz) {
+                const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
+                const double shz = __dmul_rn((double)sz, a.Lz);
+                const float shzf = (float)sz * a.Lfz;
+                const int cn = (wx * a.ncy + wy) * a.ncz + wz;
+                const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
+                const int32_t code = ((sx + 2) * 25 + (sy + 2) * 5 + (sz + 2)) << kIndexBits;
+                const int jb = cell_start[cn], je = cell_start[cn + 1];
+                for (int j = jb; j < je; ++j) {
+                    if (self_img && j == i) continue;
+                    const float4 xj = xs32[j];
+                    const float dxf = (xj.x - xf.x) + shxf;
+                    const float dyf = (xj.y - xf.y) + shyf;
+                    const float dzf = (xj.z - xf.z) + shzf;
+                    const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                    bool keep;
+                    if (d2f < a.lo) {
+                        keep = true;
+                    } else if (d2f > a.hi) {
+                        keep = false;
+                    } else {
+                        const double4_32a xj64 = xs64[j];
+                        const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), shx);
+                        const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), shy);
+                        const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), shz);
+                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                                    __dmul_rn(dz, dz));
+                        keep = d2 < a.rl2;
+                    }
+                    if (keep) {
+                        if (count < a.width) row[count] = perm[j] | code;
+                        ++count;
+                    }
+                }
+            }
+        }
+    }
+    cnt[perm[i]] = min(count, a.width);
+    if (count > a.width) atomicMax(&flags[kFlagMaxRow], count);
+}
+
+}  // namespace
+
+}  // namespace qeq
+
+QEQ_API int qeq_neighbor_build_noalloc(const double *R, int64_t n_atoms, const double *box,
+                                       double r_list, int32_t width, int32_t *counts,
+                                       int32_t *nbr, int32_t *max_row, void *stream) {
+    using namespace qeq;
+    if (max_row) *max_row = 0;
+    if (!R || !box || !counts || !nbr)
+        return set_error(nullptr, QEQ_ERR_INVALID, "noalloc neighbour build: NULL argument");
+    if (n_atoms < 1 || n_atoms > kNoAllocMaxAtoms)
+        return set_error(nullptr, QEQ_ERR_CAPACITY,
+                         "noalloc neighbour build: n_atoms %lld outside [1, %d]",
+                         (long long)n_atoms, kNoAllocMaxAtoms);
+    if (width < 1 || width > kMaxWidthLimit)
+        return set_error(nullptr, QEQ_ERR_INVALID, "noalloc neighbour build: width %d outside [1, %d]",
+                         width, kMaxWidthLimit);
+    if (!(r_list > 0.0) || !std::isfinite(r_list))
+        return set_error(nullptr, QEQ_ERR_INVALID, "noalloc neighbour build: r_list must be positive");
+    int nc[3], reach[3];
+    double cw[3], lmax = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0.0) || !std::isfinite(box[d]))
+            return set_error(nullptr, QEQ_ERR_INVALID, "noalloc neighbour build: box[%d] invalid", d);
+        lmax = std::max(lmax, box[d]);
+        nc[d] = std::max(1, std::min(1024, (int)std::floor(box[d] / (r_list * (1.0 + 1e-9)))));
+    }
+    // fewer, larger cells when the grid would not fit the fixed cell table
+    while ((int64_t)nc[0] * nc[1] * nc[2] > kNoAllocMaxCells) {
+        int d = (nc[0] >= nc[1] && nc[0] >= nc[2]) ? 0 : (nc[1] >= nc[2] ? 1 : 2);
+        nc[d] = std::max(1, nc[d] / 2);
+    }
+    for (int d = 0; d < 3; ++d) {
+        cw[d] = box[d] / nc[d];
+        reach[d] = (int)std::ceil(r_list * (1.0 + 1e-9) / cw[d]);
+        if ((reach[d] + nc[d] - 1) / nc[d] > 2)
+            return set_error(nullptr, QEQ_ERR_UNSUPPORTED,
+                             "noalloc neighbour build: box edge %d shorter than r_list / 2", d);
+    }
+    const int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    NoAllocScratch *S = nullptr;
+    int rc = noalloc_scratch(&S);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)n_atoms;
+    cudaMemsetAsync(S->cell_count, 0, sizeof(int32_t) * ncell, s);
+    cudaMemsetAsync(S->flags, 0, sizeof(int32_t) * kNumFlags, s);
+    k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(n, R, box[0], box[1], box[2], cw[0], cw[1], cw[2],
+                                                nc[0], nc[1], nc[2], S->cell_of, S->cell_count,
+                                                S->wrap_off, S->R_build, S->flags);
+    k_scan<<<1, 1024, 0, s>>>(ncell, S->cell_count, S->cell_start, S->cell_fill);
+    k_scatter<<<grid_for(n), kThreads, 0, s>>>(n, S->cell_of, S->cell_start, S->cell_fill,
+                                               S->tmp_list);
+    k_cell_sort<<<grid_for(ncell * 32), kThreads, 0, s>>>(ncell, S->cell_start, S->tmp_list, R,
+                                                          S->wrap_off, S->perm, S->cell_s,
+                                                          S->xs64, S->xs32);
+    EmitArgs a;
+    a.n = n;
+    a.ncx = nc[0]; a.ncy = nc[1]; a.ncz = nc[2];
+    a.rx = reach[0]; a.ry = reach[1]; a.rz = reach[2];
+    a.Lx = box[0]; a.Ly = box[1]; a.Lz = box[2];
+    a.Lfx = (float)box[0]; a.Lfy = (float)box[1]; a.Lfz = (float)box[2];
+    a.rl2 = r_list * r_list;
+    const double margin = 4e-5 * r_list * (lmax + r_list) + 1e-6;
+    a.lo = (float)(a.rl2 - margin);
+    a.hi = (float)(a.rl2 + margin);
+    a.width = width;
+    k_emit_original<<<grid_for(n), kThreads, 0, s>>>(a, S->xs64, S->xs32, S->cell_s, S->cell_start,
+                                                     S->perm, nbr, counts, S->flags);
+    int32_t flags[kNumFlags] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(flags, S->flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(nullptr, QEQ_ERR_CUDA, "noalloc neighbour build: %s", cudaGetErrorString(e));
+    }
+    if (flags[kFlagNonFinite])
+        return set_error(nullptr, QEQ_ERR_NONFINITE, "noalloc neighbour build: non-finite position");
+    if (flags[kFlagMaxRow] > width) {
+        if (max_row) *max_row = flags[kFlagMaxRow];
+        return set_error(nullptr, QEQ_ERR_CAPACITY,
+                         "noalloc neighbour build: a row needs %d entries, width is %d",
+                         flags[kFlagMaxRow], width);
+    }
+    return QEQ_OK;
+}
