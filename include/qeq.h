@@ -278,6 +278,14 @@ int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int
                    void *stream);
 
 /*
+ * Diagnostic: evaluate the FP32 complementary error function used by the
+ * FP32-mixed real-space kernel (Abramowitz & Stegun eq. 7.1.26, absolute
+ * error <= 1.5e-7 for x >= 0) on n device inputs x, writing device out.
+ * Lets tests check the approximation against a reference erfc.
+ */
+int qeq_selftest_erfc32(const float *x, float *out, int64_t n, void *stream);
+
+/*
  * Tracing.  The paper reports a per-component time breakdown of its MD runs
  * (Sec. 4.2.3, Fig. MD_simulation).  These calls give the same breakdown per
  * library phase, measured with CUDA events on the caller's stream.

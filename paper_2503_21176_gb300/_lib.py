@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_neighbor_build_noalloc.argtypes = [P, ctypes.c_int64, P, ctypes.c_double, ctypes.c_int32,
                                              P, P, ctypes.POINTER(ctypes.c_int32), P]
     L.qeq_neighbor_build_noalloc.restype = ctypes.c_int
+    L.qeq_selftest_erfc32.argtypes = [P, P, ctypes.c_int64, P]
+    L.qeq_selftest_erfc32.restype = ctypes.c_int
     L.qeq_profile_enable.argtypes = [P, ctypes.c_int]
     L.qeq_profile_read.argtypes = [P, P, P, ctypes.c_int]
     L.qeq_profile_phase_name.argtypes = [ctypes.c_int]
@@ -303,3 +305,14 @@ def qeq_neighbor_build_noalloc(R, box, r_list, counts, nbr, stream=None) -> None
         err = QeqError(rc, qeq_last_error(None))
         err.needed_width = int(need.value)
         raise err
+
+
+def qeq_selftest_erfc32(x, out, stream=None) -> None:
+    """FP32 erfc of the real-space kernel on CUDA float32 tensors x -> out."""
+    for t, name in ((x, "x"), (out, "out")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA float32 tensor")
+    _check(None, load().qeq_selftest_erfc32(ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()), x.numel(),
+                                            _stream(stream)))

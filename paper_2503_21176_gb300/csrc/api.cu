@@ -276,3 +276,13 @@ QEQ_API int qeq_get_counters(const qeq_ctx *ctx, int64_t *out4) {
     out4[3] = ctx->fft_execs;
     return QEQ_OK;
 }
+
+namespace qeq {
+int erfc32_selftest(const float *x, float *out, int64_t n, cudaStream_t s);
+}
+
+QEQ_API int qeq_selftest_erfc32(const float *x, float *out, int64_t n, void *stream) {
+    if (!x || !out || n < 0) return set_error(nullptr, QEQ_ERR_INVALID, "selftest: bad argument");
+    if (n == 0) return QEQ_OK;
+    return erfc32_selftest(x, out, n, (cudaStream_t)stream);
+}

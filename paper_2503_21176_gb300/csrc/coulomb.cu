@@ -127,63 +127,119 @@ k_real64(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
     }
 }
 
+// erfc(x), x >= 0, in FP32 by Abramowitz & Stegun, Handbook of Mathematical
+// Functions, eq. 7.1.26 (Hastings' approximation):
+//   erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),  t = 1 / (1 + p x),
+// with an absolute error of at most 1.5e-7.  exp(-x^2) is an argument because the
+// field term needs the same exponential.
+__device__ __forceinline__ float erfc_as7126(float x, float ex2) {
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float p = fmaf(t, 1.061405429f, -1.453152027f);
+    p = fmaf(t, p, 1.421413741f);
+    p = fmaf(t, p, -0.284496736f);
+    p = fmaf(t, p, 0.254829592f);
+    return t * p * ex2;
+}
+
+// Kahan-compensated FP32 accumulation of a chunk sum.
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// FP32 pair math with one exp per erfc shared with the field term, image shifts
+// from a shared table, and FP32 chunk sums of 32 entries accumulated with
+// compensation (no FP64 arithmetic in the loop).
 template <bool FIELD>
 __global__ void __launch_bounds__(kThreads)
 k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const float4 *__restrict__ xq, const float *__restrict__ sg, double *__restrict__ v_s,
          double *__restrict__ E_s) {
+    __shared__ float4 shift_tab[128];
+    for (int t = threadIdx.x; t < 125; t += blockDim.x)
+        shift_tab[t] = make_float4((float)(t / 25 - 2) * (float)a.Lx,
+                                   (float)((t / 5) % 5 - 2) * (float)a.Ly,
+                                   (float)(t % 5 - 2) * (float)a.Lz, 0.f);
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const float4 xi = xq[i];
-    const float si2 = sg[i] * sg[i];
+    const float si = sg[i];
+    const float si2 = si * si;
     const int c = cnt[i];
-    const float Lx = (float)a.Lx, Ly = (float)a.Ly, Lz = (float)a.Lz;
-    const float al = (float)a.alpha, al2 = al * al, rc2 = (float)a.rc2;
+    const float al = (float)a.alpha, rc2 = (float)a.rc2;
+    const float tspa = (float)(kTwoOverSqrtPi * a.alpha);
     const float tsp = (float)kTwoOverSqrtPi;
-    double v = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    float sv = 0.f, cv = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
     float vf = 0.f, exf = 0.f, eyf = 0.f, ezf = 0.f;
+    const int32_t *col = nbr + i;
+#pragma unroll 2
     for (int k = 0; k < c; ++k) {
-        int j, sx, sy, sz;
-        decode_image(nbr[(size_t)k * a.n + i], j, sx, sy, sz);
-        const float4 xj = xq[j];
-        const float dx = (xj.x - xi.x) + sx * Lx;
-        const float dy = (xj.y - xi.y) + sy * Ly;
-        const float dz = (xj.z - xi.z) + sz * Lz;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const int32_t e = __ldg(col + (size_t)k * a.n);
+        const int j = e & kIndexMask;
+        const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
+        const float4 xj = __ldg(xq + j);
+        const float dx = (xj.x - xi.x) + sh.x;
+        const float dy = (xj.y - xi.y) + sh.y;
+        const float dz = (xj.z - xi.z) + sh.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (r2 < rc2) {
             const float ir = rsqrtf(r2);
             const float r = r2 * ir;
-            float f = erfcf(al * r) * ir;
-            float dfr = -(f + tsp * al * __expf(-al2 * r2)) * ir;
-            const float g2 = si2 + sg[j] * sg[j];
+            const float x1 = al * r;
+            const float e1 = __expf(-x1 * x1);
+            float f = erfc_as7126(x1, e1) * ir;
+            float dfr = 0.f;
+            if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
+            const float sj = __ldg(sg + j);
+            const float g2 = fmaf(sj, sj, si2);
             if (g2 > 0.f) {
                 const float ig = rsqrtf(g2);
-                const float fg = erfcf(r * ig) * ir;
+                const float x2 = r * ig;
+                const float e2 = __expf(-x2 * x2);
+                const float fg = erfc_as7126(x2, e2) * ir;
                 f -= fg;
-                dfr += (fg + tsp * ig * __expf(-r2 * ig * ig)) * ir;
+                if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
             }
-            vf += xj.w * f;
+            vf = fmaf(xj.w, f, vf);
             if (FIELD) {
                 const float gq = xj.w * dfr * ir;
-                exf += gq * dx;
-                eyf += gq * dy;
-                ezf += gq * dz;
+                exf = fmaf(gq, dx, exf);
+                eyf = fmaf(gq, dy, eyf);
+                ezf = fmaf(gq, dz, ezf);
             }
         }
-        if ((k & 31) == 31) {  // flush the float chunk into the double accumulators
-            v += vf; vf = 0.f;
+        if ((k & 31) == 31) {
+            kahan_add(sv, cv, vf);
+            vf = 0.f;
             if (FIELD) {
-                ex += exf; ey += eyf; ez += ezf;
+                kahan_add(sx, cx, exf);
+                kahan_add(sy, cy, eyf);
+                kahan_add(sz, cz, ezf);
                 exf = eyf = ezf = 0.f;
             }
         }
     }
-    v += vf;
-    v_s[i] = a.ke * v;
+    kahan_add(sv, cv, vf);
+    v_s[i] = a.ke * ((double)sv - (double)cv);
     if (FIELD) {
-        E_s[3 * (size_t)i] = a.ke * (ex + exf);
-        E_s[3 * (size_t)i + 1] = a.ke * (ey + eyf);
-        E_s[3 * (size_t)i + 2] = a.ke * (ez + ezf);
+        kahan_add(sx, cx, exf);
+        kahan_add(sy, cy, eyf);
+        kahan_add(sz, cz, ezf);
+        E_s[3 * (size_t)i] = a.ke * ((double)sx - (double)cx);
+        E_s[3 * (size_t)i + 1] = a.ke * ((double)sy - (double)cy);
+        E_s[3 * (size_t)i + 2] = a.ke * ((double)sz - (double)cz);
+    }
+}
+
+// Self-test hook: the FP32 erfc of the real-space kernel on n device inputs.
+__global__ void k_erfc32(int64_t n, const float *__restrict__ x, float *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const float xv = x[t];
+        out[t] = erfc_as7126(xv, __expf(-xv * xv));
     }
 }
 
@@ -252,6 +308,111 @@ k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__re
 #pragma unroll
             for (int c = 0; c < P; ++c) atomicAdd(row + iz[c], qab * Mz[c]);
         }
+    }
+}
+
+// Spread with a shared-memory brick.  Block b owns the atoms of cells
+// [b C, (b + 1) C), C consecutive cells along z of one cell column (C divides
+// the z cell count, so a block never straddles a column).  The block finds
+// the bounding box of its atoms' spline supports (base - (P-1) .. base per
+// axis).  It accumulates q M_x M_y M_z into that brick with shared-memory
+// atomics, then adds the nonzero brick points to the global mesh with one
+// atomic each.  A brick larger than `cap` points falls back to direct global
+// atomics for that block.
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_spread_cells(int cells_per_block, const int32_t *__restrict__ cell_start,
+               const int4 *__restrict__ sbase, const typename V4<T>::type *__restrict__ sfrac,
+               int K0, int K1, int K2, int cap, T *__restrict__ mesh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *brick = reinterpret_cast<T *>(smem_raw);
+    __shared__ int bmin[3], bmax[3];
+    const int c0 = blockIdx.x * cells_per_block;
+    const int a0 = cell_start[c0], a1 = cell_start[c0 + cells_per_block];
+    if (a1 == a0) return;  // uniform across the block
+    if (threadIdx.x < 3) {
+        bmin[threadIdx.x] = 0x7fffffff;
+        bmax[threadIdx.x] = -0x7fffffff;
+    }
+    __syncthreads();
+    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+        const int4 b = sbase[a];
+        lo[0] = min(lo[0], b.x); hi[0] = max(hi[0], b.x);
+        lo[1] = min(lo[1], b.y); hi[1] = max(hi[1], b.y);
+        lo[2] = min(lo[2], b.z); hi[2] = max(hi[2], b.z);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(&bmin[d], lo[d]);
+            atomicMax(&bmax[d], hi[d]);
+        }
+    }
+    __syncthreads();
+    const int ox = bmin[0] - (P - 1), oy = bmin[1] - (P - 1), oz = bmin[2] - (P - 1);
+    const int nx = bmax[0] - bmin[0] + P, ny = bmax[1] - bmin[1] + P, nz = bmax[2] - bmin[2] + P;
+    const int vol = nx * ny * nz;
+    const bool use_brick = vol <= cap;
+    if (use_brick) {
+        for (int t = threadIdx.x; t < vol; t += blockDim.x) brick[t] = T(0);
+        __syncthreads();
+    }
+    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+        const int4 b = sbase[a];
+        const auto f = sfrac[a];
+        T Mx[P], My[P], Mz[P], dummy[P];
+        bspline<T, P, false>(f.x, Mx, dummy);
+        bspline<T, P, false>(f.y, My, dummy);
+        bspline<T, P, false>(f.z, Mz, dummy);
+        if (use_brick) {
+#pragma unroll
+            for (int ax = 0; ax < P; ++ax) {
+                const T qa = f.w * Mx[ax];
+#pragma unroll
+                for (int ay = 0; ay < P; ++ay) {
+                    const T qab = qa * My[ay];
+                    T *row = brick + ((b.x - ax - ox) * ny + (b.y - ay - oy)) * nz + (b.z - oz);
+#pragma unroll
+                    for (int az = 0; az < P; ++az) atomicAdd(row - az, qab * Mz[az]);
+                }
+            }
+        } else {
+            int iz[P];
+#pragma unroll
+            for (int az = 0; az < P; ++az) iz[az] = wrap_index(b.z - az, K2);
+#pragma unroll
+            for (int ax = 0; ax < P; ++ax) {
+                const int ix = wrap_index(b.x - ax, K0);
+                const T qa = f.w * Mx[ax];
+#pragma unroll
+                for (int ay = 0; ay < P; ++ay) {
+                    const int iy = wrap_index(b.y - ay, K1);
+                    const T qab = qa * My[ay];
+                    T *row = mesh + ((size_t)ix * K1 + iy) * K2;
+#pragma unroll
+                    for (int az = 0; az < P; ++az) atomicAdd(row + iz[az], qab * Mz[az]);
+                }
+            }
+        }
+    }
+    if (!use_brick) return;
+    __syncthreads();
+    const int nyz = ny * nz;
+    for (int t = threadIdx.x; t < vol; t += blockDim.x) {
+        const T val = brick[t];
+        if (val == T(0)) continue;
+        const int lx = t / nyz, rem = t - lx * nyz, ly = rem / nz, lz = rem - ly * nz;
+        const int ix = wrap_index(ox + lx, K0), iy = wrap_index(oy + ly, K1), iz = wrap_index(oz + lz, K2);
+        atomicAdd(mesh + ((size_t)ix * K1 + iy) * K2 + iz, val);
     }
 }
 
@@ -406,11 +567,37 @@ std::vector<double> bspline_mod2(int K, int p) {
     return out;
 }
 
+// Shared memory for one spread brick (bytes); the kernels are opted in at create time.
+constexpr int kSpreadSmemBytes = 64 * 1024;
+
 template <typename T, int P>
 void launch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s) {
-    k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
-        (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
-        (T *)ctx->mesh);
+    if (ctx->spread_cells_per_block > 0) {
+        const int blocks = (int)(ctx->ncell / ctx->spread_cells_per_block);
+        k_spread_cells<T, P><<<blocks, kThreads, kSpreadSmemBytes, s>>>(
+            ctx->spread_cells_per_block, ctx->cell_start, sb, (const typename V4<T>::type *)sf,
+            ctx->K[0], ctx->K[1], ctx->K[2], kSpreadSmemBytes / (int)sizeof(T), (T *)ctx->mesh);
+    } else {
+        k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
+            (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
+            (T *)ctx->mesh);
+    }
+}
+
+template <typename T, int P>
+cudaError_t opt_in_spread() {
+    return cudaFuncSetAttribute(k_spread_cells<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kSpreadSmemBytes);
+}
+
+template <typename T>
+cudaError_t opt_in_spread_all() {
+    cudaError_t e = opt_in_spread<T, 4>();
+    if (e == cudaSuccess) e = opt_in_spread<T, 5>();
+    if (e == cudaSuccess) e = opt_in_spread<T, 6>();
+    if (e == cudaSuccess) e = opt_in_spread<T, 7>();
+    if (e == cudaSuccess) e = opt_in_spread<T, 8>();
+    return e;
 }
 
 template <typename T, int P, bool FIELD>
@@ -620,6 +807,21 @@ int coulomb_alloc(qeq_ctx *ctx) {
     int rc = cuda_check(ctx, e, "influence upload");
     if (rc) return rc;
 
+    // spread bricks: C consecutive z cells per block, C | nc_z, brick within ~40 mesh points in z
+    {
+        const int ncz = ctx->nc[2];
+        const double pts_per_cell = ctx->cw[2] * ctx->K[2] / p.box[2];
+        int best = 0;
+        for (int c = 1; c <= ncz; ++c)
+            if (ncz % c == 0 && c * pts_per_cell <= 40.0) best = c;
+        ctx->spread_cells_per_block = best;
+        cudaError_t ea = ctx->fp32 ? opt_in_spread_all<float>() : opt_in_spread_all<double>();
+        if (ea != cudaSuccess) {
+            cudaGetLastError();
+            ctx->spread_cells_per_block = 0;  // keep the direct-atomic spread
+        }
+    }
+
     cufftResult cr = cufftPlan3d(&ctx->plan_r2c, ctx->K[0], ctx->K[1], ctx->K[2],
                                  ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z);
     if (cr == CUFFT_SUCCESS)
@@ -641,6 +843,11 @@ void coulomb_free(qeq_ctx *ctx) {
         cufftDestroy(ctx->plan_r2c);
         cufftDestroy(ctx->plan_c2r);
     }
+}
+
+int erfc32_selftest(const float *x, float *out, int64_t n, cudaStream_t s) {
+    k_erfc32<<<grid_for(n), kThreads, 0, s>>>(n, x, out);
+    return cudaGetLastError() == cudaSuccess ? QEQ_OK : QEQ_ERR_CUDA;
 }
 
 int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,

@@ -122,6 +122,7 @@ struct qeq_ctx {
     void *G = nullptr;         // influence function on the half spectrum (double or float)
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     bool have_plans = false;
+    int spread_cells_per_block = 0;  // 0: direct-atomic spread
 
     // ---- reductions ----
     double *part = nullptr;    // [kMaxRedSlots][kRedBlocks]
@@ -133,6 +134,8 @@ struct qeq_ctx {
     double *Wb = nullptr;      // [m][N] Krylov basis
     double *Rb = nullptr;      // [m][N] J applied to the basis
     double *F_short = nullptr; // [N][3]
+    double *inv_u = nullptr;   // [N] 1 / u of the current evaluation
+    double *inv_m = nullptr;   // [N] 1 / (m * mass_unit) of the current step
     double *energy4 = nullptr; // [4] energy parts of the last apply
 
     // ---- tracing ----

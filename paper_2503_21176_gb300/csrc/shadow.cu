@@ -38,10 +38,12 @@ constexpr int S_KE = 120;   // kinetic energy
 constexpr int S_SHORT = 121;
 
 __global__ void k_lambda_part(int n, const double *__restrict__ chi, const double *__restrict__ u,
-                              const double *__restrict__ v, double *__restrict__ part) {
+                              const double *__restrict__ v, double *__restrict__ inv_u,
+                              double *__restrict__ part) {
     double s1 = 0.0, s2 = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double iu = 1.0 / u[i];
+        inv_u[i] = iu;
         s1 += (chi[i] + v[i]) * iu;
         s2 += iu;
     }
@@ -54,13 +56,14 @@ __global__ void k_lambda_part(int n, const double *__restrict__ chi, const doubl
 }
 
 __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
-                          const double *__restrict__ u, const double *__restrict__ v,
+                          const double *__restrict__ u, const double *__restrict__ inv_u,
+                          const double *__restrict__ v,
                           const double *__restrict__ nn, const double *__restrict__ scal,
                           double *__restrict__ q, double *__restrict__ f, double *__restrict__ part) {
     const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
     double a[6] = {0, 0, 0, 0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double qi = -(chi[i] + v[i] + lam) / u[i];
+        const double qi = -(chi[i] + v[i] + lam) * inv_u[i];
         const double fi = qi - nn[i];
         q[i] = qi;
         f[i] = fi;
@@ -76,25 +79,12 @@ __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
         for (int k = 0; k < 6; ++k) part[k * kRedBlocks + blockIdx.x] = a[k];
 }
 
-// energies: 1 shadow potential, 3 short range, 4 lambda, 5 sum q, 6 |f|, 7 applies
-__global__ void k_charge_energies(double q_tot, int applies, const double *__restrict__ scal,
-                                  double *__restrict__ energies) {
-    const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
-    const double e_short = scal[S_SHORT];
-    energies[1] = scal[S_CHG + 1] + scal[S_CHG + 2] + scal[S_CHG + 3] - 0.5 * scal[S_CHG + 4] + e_short;
-    energies[3] = e_short;
-    energies[4] = lam;
-    energies[5] = scal[S_CHG + 5];
-    energies[6] = sqrt(scal[S_CHG]);
-    energies[7] = (double)applies;
-}
-
 // F = q E[n] + n E[f] (+ F_short); w_1 = f / |f|; Phi w_1 = Phi f / |f| (in place);
 // partial sum of (Phi w_1) / u for mu.
 __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *__restrict__ nn,
                             const double *__restrict__ En, const double *__restrict__ Ef,
                             const double *__restrict__ Fs, const double *__restrict__ f,
-                            const double *__restrict__ u, const double *__restrict__ scal,
+                            const double *__restrict__ inv_u, const double *__restrict__ scal,
                             double *__restrict__ F, double *__restrict__ w1,
                             double *__restrict__ phi, double *__restrict__ part) {
     const double nf = sqrt(scal[S_CHG]);
@@ -110,41 +100,45 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
         w1[i] = f[i] * inv;
         const double pw = phi[i] * inv;
         phi[i] = pw;
-        s += pw / u[i];
+        s += pw * inv_u[i];
     }
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
 }
 
-__global__ void k_mu_part(int n, const double *__restrict__ phi, const double *__restrict__ u,
+__global__ void k_mu_part(int n, const double *__restrict__ phi, const double *__restrict__ inv_u,
                           double *__restrict__ part) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s += phi[i] / u[i];
+        s += phi[i] * inv_u[i];
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
 }
 
-// r = J w = -(Phi w + mu) / u - w with mu = -(sum Phi w / u) / sum 1 / u
+// r = J w = -(Phi w + mu) / u - w with mu = -(sum Phi w / u) / sum 1 / u.
+// When wnext is given, also start the next basis vector: wnext = r and the
+// partial of <w0, r>, the first modified Gram-Schmidt projection.
 __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *__restrict__ w,
-                           const double *__restrict__ u, const double *__restrict__ scal,
-                           double *__restrict__ r) {
+                           const double *__restrict__ inv_u, const double *__restrict__ scal,
+                           double *__restrict__ r, double *__restrict__ wnext,
+                           const double *__restrict__ w0, double *__restrict__ part) {
     const double mu = -scal[S_MU] / scal[S_LAM + 1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        r[i] = -(phi[i] + mu) / u[i] - w[i];
-}
-
-// partial of <a, b>
-__global__ void k_dot_part(int n, const double *__restrict__ a, const double *__restrict__ b,
-                           double *__restrict__ part) {
     double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s += a[i] * b[i];
-    double vals[1] = {s};
-    block_sum<1>(vals);
-    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double ri = -(phi[i] + mu) * inv_u[i] - w[i];
+        r[i] = ri;
+        if (wnext) {
+            wnext[i] = ri;
+            s += w0[i] * ri;
+        }
+    }
+    if (wnext) {
+        double vals[1] = {s};
+        block_sum<1>(vals);
+        if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    }
 }
 
 // x -= scal[S_DOT] * y, then partial of <z, x> (z may alias x for the norm)
@@ -160,11 +154,6 @@ __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double 
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
-}
-
-__global__ void k_copy(int n, const double *__restrict__ src, double *__restrict__ dst) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        dst[i] = src[i];
 }
 
 __global__ void k_normalize(int n, const double *__restrict__ scal, double *__restrict__ x) {
@@ -195,20 +184,33 @@ __global__ void k_normal_part(int n, int m, const double *__restrict__ Rb,
     }
 }
 
-// Solve O c = g (m x m, symmetric) by Gaussian elimination with partial pivoting.
-// Singular directions (pivot 0, e.g. f = 0) get c = 0.
-__global__ void k_solve_small(int m, double *__restrict__ scal) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double A[kMaxRank][kMaxRank + 1];
+// One block: sum the partials of O = R^T R and g = R^T f in fixed order, solve
+// O c = g (m x m) by Gaussian elimination with partial pivoting (singular
+// directions, e.g. f = 0, get c = 0), and write the evaluation's energies:
+// 1 shadow potential, 3 short range, 4 lambda, 5 sum q, 6 |f|, 7 applies.
+__global__ void k_normal_solve(int m, double q_tot, int applies, const double *__restrict__ part,
+                               double *__restrict__ scal, double *__restrict__ energies) {
+    __shared__ double sums[kMaxRank * (kMaxRank + 1) / 2 + kMaxRank];
     const int nO = m * (m + 1) / 2;
+    for (int k = 0; k < nO + m; ++k) {
+        double acc = 0.0;
+        const double *p = part + (size_t)k * kRedBlocks;
+        for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) acc += p[b];
+        double vals[1] = {acc};
+        block_sum<1>(vals);
+        if (threadIdx.x == 0) sums[k] = vals[0];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double A[kMaxRank][kMaxRank + 1];
     int k = 0;
     for (int a = 0; a < m; ++a)
         for (int b = a; b < m; ++b) {
-            A[a][b] = scal[S_OM + k];
-            A[b][a] = scal[S_OM + k];
+            A[a][b] = sums[k];
+            A[b][a] = sums[k];
             ++k;
         }
-    for (int a = 0; a < m; ++a) A[a][m] = scal[S_OM + nO + a];
+    for (int a = 0; a < m; ++a) A[a][m] = sums[nO + a];
     double scale = 0.0;
     for (int a = 0; a < m; ++a) scale = fmax(scale, fabs(A[a][a]));
     const double tiny = scale * 1e-300;
@@ -236,11 +238,19 @@ __global__ void k_solve_small(int m, double *__restrict__ scal) {
             x[c] = 0.0;
             continue;
         }
-        double s = A[c][m];
-        for (int j = c + 1; j < m; ++j) s -= A[c][j] * x[j];
-        x[c] = s / A[c][c];
+        double acc = A[c][m];
+        for (int j = c + 1; j < m; ++j) acc -= A[c][j] * x[j];
+        x[c] = acc / A[c][c];
     }
     for (int a = 0; a < m; ++a) scal[S_OM + kMaxRank * kMaxRank + a] = x[a];
+    const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
+    const double e_short = scal[S_SHORT];
+    energies[1] = scal[S_CHG + 1] + scal[S_CHG + 2] + scal[S_CHG + 3] - 0.5 * scal[S_CHG + 4] + e_short;
+    energies[3] = e_short;
+    energies[4] = lam;
+    energies[5] = scal[S_CHG + 5];
+    energies[6] = sqrt(scal[S_CHG]);
+    energies[7] = (double)applies;
 }
 
 __global__ void k_kf(int n, int m, const double *__restrict__ Wb, const double *__restrict__ scal,
@@ -285,9 +295,11 @@ Dissipation dissipation(int kd) {
 __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
                           const double *__restrict__ mass, const double *__restrict__ F,
                           const double *__restrict__ Kf, double *__restrict__ R,
-                          double *__restrict__ V, double *__restrict__ hist) {
+                          double *__restrict__ V, double *__restrict__ hist,
+                          double *__restrict__ inv_m_out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double inv_m = 1.0 / (mass[i] * mass_unit);
+        inv_m_out[i] = inv_m;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double vi = V[3 * (size_t)i + d] + 0.5 * dt * F[3 * (size_t)i + d] * inv_m;
@@ -306,8 +318,9 @@ __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
 
 // optional second half kick, then partial of the kinetic energy
 __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
-                         const double *__restrict__ mass, const double *__restrict__ F,
-                         double *__restrict__ V, double *__restrict__ part) {
+                         const double *__restrict__ mass, const double *__restrict__ inv_m,
+                         const double *__restrict__ F, double *__restrict__ V,
+                         double *__restrict__ part) {
     double ke = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double mi = mass[i] * mass_unit;
@@ -316,7 +329,7 @@ __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
         for (int d = 0; d < 3; ++d) {
             double vi = V[3 * (size_t)i + d];
             if (kick) {
-                vi += 0.5 * dt * F[3 * (size_t)i + d] / mi;
+                vi += 0.5 * dt * F[3 * (size_t)i + d] * inv_m[i];
                 V[3 * (size_t)i + d] = vi;
             }
             v2 += vi * vi;
@@ -349,6 +362,8 @@ int shadow_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->fvec, sizeof(double) * n},
         {(void **)&ctx->Wb, sizeof(double) * (size_t)m * n},
         {(void **)&ctx->Rb, sizeof(double) * (size_t)m * n},
+        {(void **)&ctx->inv_u, sizeof(double) * n},
+        {(void **)&ctx->inv_m, sizeof(double) * n},
     };
     for (auto &b : bufs) {
         cudaError_t e = cudaMalloc(b.ptr, b.bytes);
@@ -367,7 +382,8 @@ int shadow_alloc(qeq_ctx *ctx) {
 }
 
 void shadow_free(qeq_ctx *ctx) {
-    void *ptrs[] = {ctx->v_n, ctx->E_n, ctx->phi, ctx->E_f, ctx->fvec, ctx->Wb, ctx->Rb, ctx->F_short};
+    void *ptrs[] = {ctx->v_n, ctx->E_n, ctx->phi, ctx->E_f, ctx->fvec, ctx->Wb,
+                    ctx->Rb,  ctx->F_short, ctx->inv_u, ctx->inv_m};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -402,38 +418,37 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     int rc = coulomb_apply_impl(ctx, st->R, nn, prm->sigma, ctx->v_n, ctx->E_n, nullptr, nullptr,
                                 true, s);
     if (rc) return rc;
-    // 2. lambda and q[n] (Eq. diag_linear_qeq)
+    // 2. lambda and q[n] (Eq. diag_linear_qeq); 1/u kept for the rest of the evaluation
     prof_begin(ctx, kPhShadow, s);
-    k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, part);
+    k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, ctx->inv_u, part);
     fin(2, S_LAM);
-    k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->v_n, nn, scal, st->q,
-                                     ctx->fvec, part);
+    k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn, scal,
+                                     st->q, ctx->fvec, part);
     fin(6, S_CHG);
     prof_end(ctx, s);
     // 3. Phi f, E[f]
     rc = coulomb_apply_impl(ctx, st->R, ctx->fvec, prm->sigma, ctx->phi, ctx->E_f, nullptr, nullptr,
                             true, s);
     if (rc) return rc;
-    // 4. forces, w_1, r_1
+    // 4. forces, w_1, r_1 (and, when m > 1, the start of w_2)
     prof_begin(ctx, kPhShadow, s);
-    double *W0 = ctx->Wb, *R0 = ctx->Rb;
     k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
                                        ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr,
-                                       ctx->fvec, u, scal, st->F, W0, ctx->phi, part);
+                                       ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb, ctx->phi, part);
     fin(1, S_MU);
-    k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, W0, u, scal, R0);
+    k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
+                                      m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part);
     ctx->launches++;
+    if (m > 1) {
+        launch_finalize(part, 1, scal + S_DOT, s);
+        ctx->launches++;
+    }
     prof_end(ctx, s);
-    // 5. further Krylov vectors
+    // 5. further Krylov vectors: w_k starts as r_{k-1} with <w_0, w_k> already reduced
     for (int k = 1; k < m; ++k) {
         double *Wk = ctx->Wb + (size_t)k * n;
-        const double *Rprev = ctx->Rb + (size_t)(k - 1) * n;
         prof_begin(ctx, kPhShadow, s);
-        k_copy<<<G, kThreads, 0, s>>>(n, Rprev, Wk);
-        ctx->launches++;
         // modified Gram-Schmidt: Wk -= <w_j, Wk> w_j for j = 0..k-1, then normalise
-        k_dot_part<<<G, kThreads, 0, s>>>(n, ctx->Wb, Wk, part);
-        fin(1, S_DOT);
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
@@ -447,20 +462,24 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
                                 false, s);
         if (rc) return rc;
         prof_begin(ctx, kPhShadow, s);
-        k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, u, part);
+        k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->inv_u, part);
         fin(1, S_MU);
-        k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, Wk, u, scal, ctx->Rb + (size_t)k * n);
+        const bool more = k + 1 < m;
+        k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, Wk, ctx->inv_u, scal, ctx->Rb + (size_t)k * n,
+                                          more ? ctx->Wb + (size_t)(k + 1) * n : nullptr, ctx->Wb,
+                                          part);
         ctx->launches++;
+        if (more) {
+            launch_finalize(part, 1, scal + S_DOT, s);
+            ctx->launches++;
+        }
         prof_end(ctx, s);
     }
-    // 6. normal equations and Kf = W c
+    // 6. normal equations, m x m solve and energies in one block; Kf = W c
     prof_begin(ctx, kPhShadow, s);
-    const int nO = m * (m + 1) / 2;
     k_normal_part<<<G, kThreads, 0, s>>>(n, m, ctx->Rb, ctx->fvec, part);
-    fin(nO + m, S_OM);
-    k_solve_small<<<1, 32, 0, s>>>(m, scal);
+    k_normal_solve<<<1, kThreads, 0, s>>>(m, ctx->p.q_tot, m + 1, part, scal, st->energies);
     k_kf<<<G, kThreads, 0, s>>>(n, m, ctx->Wb, scal, st->Kf);
-    k_charge_energies<<<1, 1, 0, s>>>(ctx->p.q_tot, m + 1, scal, st->energies);
     ctx->launches += 3;
     prof_end(ctx, s);
     return cuda_check(ctx, cudaGetLastError(), "shadow evaluate launch");
@@ -471,7 +490,7 @@ int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cud
     prof_begin(ctx, kPhIntegrate, s);
     k_advance<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
                                               dissipation(ctx->p.dissipation_k), prm->mass, st->F,
-                                              st->Kf, st->R, st->V, st->n_hist);
+                                              st->Kf, st->R, st->V, st->n_hist, ctx->inv_m);
     prof_end(ctx, s);
     ctx->launches++;
     double d2 = 0.0;
@@ -489,8 +508,8 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
                   cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_finish<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass, st->F,
-                                             st->V, ctx->part);
+    k_finish<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
+                                             ctx->inv_m, st->F, st->V, ctx->part);
     launch_finalize(ctx->part, 1, ctx->scal + S_KE, s);
     k_total_energy<<<1, 1, 0, s>>>(ctx->scal, st->energies);
     prof_end(ctx, s);
