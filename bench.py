@@ -149,6 +149,21 @@ def initial_state(w, seed):
     return V
 
 
+def aggregate_over_ranks(local_ms, steps, world, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank ran `steps` steps in
+    `local_ms` ms; the job took the slowest rank's time (max over ranks), and the
+    units processed are world * steps.  Returns (value in steps/s, max ms)."""
+    total_ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+
+        t = torch.tensor([total_ms], dtype=torch.float64,
+                         device=device if device is not None else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms * 1e-3), total_ms
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -377,13 +392,9 @@ def ours(args):
     e2e = e2e_steps(qg, md, max(3, args.steps // 2), stream, device)
 
     # max over ranks of the timed region
-    total_ms = head["_step_ms_sum"]
+    value, total_ms = aggregate_over_ranks(head["_step_ms_sum"], args.steps, world, dist, device)
     if dist is not None:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
         dist.barrier()
-    value = world * args.steps / (total_ms * 1e-3)
 
     line = None
     if rank == 0:
@@ -489,6 +500,36 @@ def reference(args):
     print(json.dumps(line))
 
 
+def serve_bench(args):
+    """Serving workload: Poisson stream of mixed-size water boxes, half QEq evaluations and
+    half 20-step shadow-MD runs, FP32-mixed and FP64.  Prints one JSON line."""
+    import torch
+
+    import paper_2503_21176_gb300 as qg
+    from paper_2503_21176_gb300.serve import Server, request_from_box
+    from workloads import serving_stream
+
+    qg.load()
+    torch.cuda.set_device(0)
+    stream = serving_stream(n_requests=args.serve_requests, rate=args.serve_rate)
+    out = {"metric": "serving throughput and p50/p99 latency, mixed-size periodic QEq / shadow-MD "
+                     "requests", "unit": "requests/s", "data": "synthetic",
+           "config": {"requests": args.serve_requests, "arrival_rate_per_s": args.serve_rate,
+                      "atoms": "100-20,000 log-uniform", "kinds": "half 1 QEq evaluation, half 20 MD steps",
+                      "mesh": "smallest 2^k or 3*2^k with spacing <= 1.0 A", "r_c": 8.0,
+                      "max_inflight": args.serve_inflight}}
+    for prec in ("fp32_mixed", "fp64"):
+        reqs = [request_from_box(r["rid"], r["kind"], r["box"], r["mesh"], V=r["V"],
+                                 steps=r["steps"], arrival=r["arrival"], precision=prec)
+                for r in stream]
+        # warm the library, the memory pool and cuFFT on a few requests first
+        Server(max_inflight=args.serve_inflight).serve(reqs[:8], realtime=False)
+        res, stats = Server(max_inflight=args.serve_inflight).serve(reqs, realtime=True)
+        out[prec] = stats
+    out["value"] = out["fp32_mixed"]["throughput_req_per_s"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,7 +541,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reference-budget", type=float, default=200.0,
                     help="seconds of oracle work the reference arm may spend")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-inflight", type=int, default=8)
     args = ap.parse_args()
+    if args.serve:
+        serve_bench(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

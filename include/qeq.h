@@ -121,7 +121,20 @@ void qeq_params_default(qeq_params *p);
  * On failure *out is NULL and the return code says why.  Synchronises. */
 int qeq_create(const qeq_params *p, qeq_ctx **out);
 
-/* Free everything qeq_create allocated.  NULL is ignored.  Synchronises the device. */
+/* Same as qeq_create, but every device buffer, including the cuFFT work
+ * area, comes from the device's default stream-ordered memory pool
+ * (cudaMallocAsync on `stream`).  Uploads and memsets are ordered on `stream`,
+ * and the call synchronises only `stream`, never the whole device.
+ * qeq_destroy then frees with cudaFreeAsync on that stream.  Creating and
+ * destroying contexts this way does not stall work on other streams.  The
+ * serving loop relies on that to admit and retire requests while others run.
+ * The pool is set to keep freed memory cached (release threshold = max) for
+ * reuse by later contexts.  Use the context on `stream`, or synchronise its
+ * work before qeq_destroy. */
+int qeq_create_async(const qeq_params *p, void *stream, qeq_ctx **out);
+
+/* Free everything qeq_create allocated.  NULL is ignored.  Synchronises the
+ * device (contexts from qeq_create_async: stream-ordered frees, no sync). */
 void qeq_destroy(qeq_ctx *ctx);
 
 /* Message for the last failing call on ctx ("" when none).  ctx may be NULL,
@@ -284,6 +297,16 @@ int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int
  * Lets tests check the approximation against a reference erfc.
  */
 int qeq_selftest_erfc32(const float *x, float *out, int64_t n, void *stream);
+
+/*
+ * Diagnostic: evaluate the FP64 complementary error function and its
+ * derivative used by the FP64 real-space kernel.  It is a piecewise
+ * polynomial through Chebyshev nodes of a long-double erfc: 256 pieces of
+ * degree 9 on [0, 6.5), and 0 beyond.  Inputs are n device doubles x >= 0.
+ * The outputs out (erfc) and dout (d erfc / dx) are device doubles.
+ */
+int qeq_selftest_erfc64(qeq_ctx *ctx, const double *x, double *out, double *dout, int64_t n,
+                        void *stream);
 
 /*
  * Tracing.  The paper reports a per-component time breakdown of its MD runs

@@ -26,6 +26,7 @@ from ._lib import (  # noqa: F401
     md_state,
     qeq_coulomb_apply,
     qeq_create,
+    qeq_create_async,
     qeq_destroy,
     qeq_get_counters,
     qeq_get_sizes,
@@ -77,12 +78,13 @@ def make_params(n_atoms, box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(32, 32, 32)
 class System:
     """One periodic system on the current CUDA device, with apply outputs preallocated."""
 
-    def __init__(self, params: qeq_params, device=None):
+    def __init__(self, params: qeq_params, device=None, stream=None):
+        """stream=None: qeq_create; a torch.cuda.Stream: qeq_create_async on that stream."""
         self.params = params
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.n = int(params.n_atoms)
         with torch.cuda.device(self.device):
-            self.ctx = qeq_create(params)
+            self.ctx = qeq_create(params) if stream is None else qeq_create_async(params, stream)
         f64 = dict(dtype=torch.float64, device=self.device)
         self.v = torch.empty(self.n, **f64)
         self.E = torch.empty(self.n, 3, **f64)

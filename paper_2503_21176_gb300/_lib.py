@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_params_default.argtypes = [ctypes.POINTER(qeq_params)]
     L.qeq_params_default.restype = None
     L.qeq_create.argtypes = [ctypes.POINTER(qeq_params), ctypes.POINTER(P)]
+    L.qeq_create_async.argtypes = [ctypes.POINTER(qeq_params), P, ctypes.POINTER(P)]
+    L.qeq_create_async.restype = ctypes.c_int
     L.qeq_destroy.argtypes = [P]
     L.qeq_destroy.restype = None
     L.qeq_last_error.argtypes = [P]
@@ -109,6 +111,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_neighbor_build_noalloc.restype = ctypes.c_int
     L.qeq_selftest_erfc32.argtypes = [P, P, ctypes.c_int64, P]
     L.qeq_selftest_erfc32.restype = ctypes.c_int
+    L.qeq_selftest_erfc64.argtypes = [P, P, P, P, ctypes.c_int64, P]
+    L.qeq_selftest_erfc64.restype = ctypes.c_int
     L.qeq_profile_enable.argtypes = [P, ctypes.c_int]
     L.qeq_profile_read.argtypes = [P, P, P, ctypes.c_int]
     L.qeq_profile_phase_name.argtypes = [ctypes.c_int]
@@ -172,6 +176,13 @@ def qeq_params_default() -> qeq_params:
 def qeq_create(params: qeq_params):
     h = ctypes.c_void_p()
     rc = load().qeq_create(ctypes.byref(params), ctypes.byref(h))
+    _check(None, rc)
+    return h
+
+
+def qeq_create_async(params: qeq_params, stream=None):
+    h = ctypes.c_void_p()
+    rc = load().qeq_create_async(ctypes.byref(params), _stream(stream), ctypes.byref(h))
     _check(None, rc)
     return h
 
@@ -316,3 +327,9 @@ def qeq_selftest_erfc32(x, out, stream=None) -> None:
     _check(None, load().qeq_selftest_erfc32(ctypes.c_void_p(x.data_ptr()),
                                             ctypes.c_void_p(out.data_ptr()), x.numel(),
                                             _stream(stream)))
+
+
+def qeq_selftest_erfc64(ctx, x, out, dout, stream=None) -> None:
+    """FP64 piecewise erfc and its derivative of the real-space kernel (CUDA float64 tensors)."""
+    _check(ctx, load().qeq_selftest_erfc64(ctx, _dev(x, "x"), _dev(out, "out"), _dev(dout, "dout"),
+                                           x.numel(), _stream(stream)))

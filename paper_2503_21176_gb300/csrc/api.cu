@@ -33,6 +33,28 @@ int cuda_check(qeq_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, QEQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+int dev_alloc(qeq_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = ctx->async_alloc ? cudaMallocAsync(p, bytes, ctx->alloc_stream)
+                                     : cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed (%s)", bytes,
+                         cudaGetErrorString(e));
+    }
+    return QEQ_OK;
+}
+
+void dev_free(qeq_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->async_alloc)
+        cudaFreeAsync(p, ctx->alloc_stream);
+    else
+        cudaFree(p);
+}
+
 static int validate(const qeq_params *p) {
     if (!p) return set_error(nullptr, QEQ_ERR_INVALID, "params is NULL");
     if (p->n_atoms < 1 || p->n_atoms > kIndexMask)
@@ -59,6 +81,8 @@ static int validate(const qeq_params *p) {
         return set_error(nullptr, QEQ_ERR_INVALID, "dissipation_k must be in [3, 7]");
     if (p->short_range != QEQ_SHORT_NONE && p->short_range != QEQ_SHORT_WATER)
         return set_error(nullptr, QEQ_ERR_INVALID, "unknown short_range model %d", p->short_range);
+    if (p->short_range == QEQ_SHORT_WATER && p->n_atoms % 3 != 0)
+        return set_error(nullptr, QEQ_ERR_INVALID, "the water model needs atoms ordered O, H, H");
     if (!(p->dt > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "dt must be positive");
     if (!(p->mass_unit > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "mass_unit must be positive");
     if (p->max_neighbors < 0) return set_error(nullptr, QEQ_ERR_INVALID, "max_neighbors must be >= 0");
@@ -67,7 +91,7 @@ static int validate(const qeq_params *p) {
 
 static void destroy(qeq_ctx *ctx) {
     if (!ctx) return;
-    cudaDeviceSynchronize();
+    if (!ctx->async_alloc) cudaDeviceSynchronize();
     for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
     shadow_free(ctx);
     coulomb_free(ctx);
@@ -101,13 +125,17 @@ QEQ_API void qeq_params_default(qeq_params *p) {
     p->mass_unit = 103.6427;
 }
 
-QEQ_API int qeq_create(const qeq_params *p, qeq_ctx **out) {
+namespace {
+
+int create(const qeq_params *p, cudaStream_t stream, bool async_alloc, qeq_ctx **out) {
     if (!out) return set_error(nullptr, QEQ_ERR_INVALID, "out is NULL");
     *out = nullptr;
     int rc = validate(p);
     if (rc) return rc;
     qeq_ctx *ctx = new (std::nothrow) qeq_ctx();
     if (!ctx) return set_error(nullptr, QEQ_ERR_NOMEM, "host allocation failed");
+    ctx->async_alloc = async_alloc;
+    ctx->alloc_stream = stream;
     ctx->p = *p;
     ctx->n = p->n_atoms;
     ctx->fp32 = p->precision == QEQ_FP32_MIXED;
@@ -116,7 +144,9 @@ QEQ_API int qeq_create(const qeq_params *p, qeq_ctx **out) {
     if (!rc) rc = nl_alloc(ctx);
     if (!rc) rc = coulomb_alloc(ctx);
     if (!rc) rc = shadow_alloc(ctx);
-    if (!rc) rc = cuda_check(ctx, cudaDeviceSynchronize(), "create");
+    if (!rc)
+        rc = cuda_check(ctx, async_alloc ? cudaStreamSynchronize(stream) : cudaDeviceSynchronize(),
+                        "create");
     if (rc) {
         g_create_error = ctx->err;
         destroy(ctx);
@@ -124,6 +154,23 @@ QEQ_API int qeq_create(const qeq_params *p, qeq_ctx **out) {
     }
     *out = ctx;
     return QEQ_OK;
+}
+
+}  // namespace
+
+QEQ_API int qeq_create(const qeq_params *p, qeq_ctx **out) { return create(p, nullptr, false, out); }
+
+QEQ_API int qeq_create_async(const qeq_params *p, void *stream, qeq_ctx **out) {
+    // Keep freed blocks in the pool so that the next context reuses them without
+    // returning memory to the driver.
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    return create(p, (cudaStream_t)stream, true, out);
 }
 
 QEQ_API void qeq_destroy(qeq_ctx *ctx) { destroy(ctx); }
@@ -285,4 +332,17 @@ QEQ_API int qeq_selftest_erfc32(const float *x, float *out, int64_t n, void *str
     if (!x || !out || n < 0) return set_error(nullptr, QEQ_ERR_INVALID, "selftest: bad argument");
     if (n == 0) return QEQ_OK;
     return erfc32_selftest(x, out, n, (cudaStream_t)stream);
+}
+
+namespace qeq {
+int erfc64_selftest(qeq_ctx *ctx, const double *x, double *out, double *dout, int64_t n,
+                    cudaStream_t s);
+}
+
+QEQ_API int qeq_selftest_erfc64(qeq_ctx *ctx, const double *x, double *out, double *dout, int64_t n,
+                                void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!x || !out || !dout || n < 0) return set_error(ctx, QEQ_ERR_INVALID, "selftest: bad argument");
+    if (n == 0) return QEQ_OK;
+    return erfc64_selftest(ctx, x, out, dout, n, (cudaStream_t)stream);
 }

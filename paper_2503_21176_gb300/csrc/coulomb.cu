@@ -17,6 +17,7 @@
 // spreading, the FFT and the gather in float.  It accumulates rows in float
 // chunks of 32 flushed into double, and keeps the energies and outputs in double.
 #include <cmath>
+#include <new>
 #include <type_traits>
 #include <vector>
 
@@ -71,59 +72,131 @@ struct RealArgs {
     double ke;
 };
 
-__device__ __forceinline__ void decode_image(int32_t e, int &j, int &sx, int &sy, int &sz) {
-    j = e & kIndexMask;
-    const int code = (int)((uint32_t)e >> kIndexBits);
-    sx = code / 25 - 2;
-    sy = (code / 5) % 5 - 2;
-    sz = code % 5 - 2;
+// Threads per neighbour row.  TPR consecutive lanes share one row: lane s takes
+// entries s, s + TPR, ...  Their partial sums are combined with warp shuffles.
+// This multiplies the number of resident warps (one thread per row leaves most
+// of the 152 SMs' warp slots empty at 10^5 atoms) and shortens each thread's
+// chain of dependent loads.
+#ifndef QEQ_TPR
+#define QEQ_TPR 4
+#endif
+#ifndef QEQ_REAL_MIN_BLOCKS
+#define QEQ_REAL_MIN_BLOCKS 6
+#endif
+constexpr int kTPR = QEQ_TPR;
+
+// FP64 erfc by a piecewise polynomial: [0, kErfcXMax) is cut into kErfcPieces
+// equal pieces.  On each piece erfc is the degree-(kErfcCoef - 1) polynomial in
+// s in [-1, 1) through the Chebyshev nodes of that piece; the coefficients come
+// from the host's long-double erfc (erfc_table()).  Beyond kErfcXMax, where
+// erfc < 4e-20, the value and the derivative are 0.  One Horner pass gives
+// erfc(x) and d erfc / dx (so no exp is needed).  The relative error is below
+// 1e-14, far inside the 1e-10 parity of the FP64 path.
+constexpr int kErfcPieces = 256;
+constexpr int kErfcCoef = 10;
+constexpr double kErfcXMax = 6.5;
+
+__device__ __forceinline__ double erfc_pw(const double *__restrict__ tab, double x, double &dfdx) {
+    const double inv_h = kErfcPieces / kErfcXMax;
+    if (!(x < kErfcXMax)) {
+        dfdx = 0.0;
+        return 0.0;
+    }
+    const double u = x * inv_h;
+    const int k = (int)u;
+    const double s = 2.0 * (u - (double)k) - 1.0;
+    const double *c = tab + k * kErfcCoef;
+    double p = c[kErfcCoef - 1], dp = 0.0;
+#pragma unroll
+    for (int m = kErfcCoef - 2; m >= 0; --m) {
+        dp = fma(dp, s, p);
+        p = fma(p, s, c[m]);
+    }
+    dfdx = dp * (2.0 * inv_h);
+    return p;
 }
 
 template <bool FIELD>
 __global__ void __launch_bounds__(kThreads)
 k_real64(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
-         const double4_32a *__restrict__ xq, const double *__restrict__ sg, double *__restrict__ v_s,
-         double *__restrict__ E_s) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const double4_32a xi = xq[i];
-    const double si2 = sg[i] * sg[i];
-    const int c = cnt[i];
-    const double al = a.alpha, al2 = a.alpha * a.alpha;
+         const double4_32a *__restrict__ xq, const double *__restrict__ sg,
+         const double *__restrict__ erfc_tab, double *__restrict__ v_s, double *__restrict__ E_s) {
+    __shared__ double shift_tab[125][3];
+    __shared__ double tab[kErfcPieces * kErfcCoef];
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+        shift_tab[t][0] = (double)(t / 25 - 2) * a.Lx;
+        shift_tab[t][1] = (double)((t / 5) % 5 - 2) * a.Ly;
+        shift_tab[t][2] = (double)(t % 5 - 2) * a.Lz;
+    }
+    for (int t = threadIdx.x; t < kErfcPieces * kErfcCoef; t += blockDim.x) tab[t] = erfc_tab[t];
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kTPR, sub = t % kTPR;
+    const double al = a.alpha;
     double v = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    for (int k = 0; k < c; ++k) {
-        int j, sx, sy, sz;
-        decode_image(nbr[(size_t)k * a.n + i], j, sx, sy, sz);
-        const double4_32a xj = xq[j];
-        const double dx = (xj.x - xi.x) + sx * a.Lx;
-        const double dy = (xj.y - xi.y) + sy * a.Ly;
-        const double dz = (xj.z - xi.z) + sz * a.Lz;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (!(r2 < a.rc2)) continue;
-        const double r = sqrt(r2);
-        const double ir = 1.0 / r;
-        double f = erfc(al * r) * ir;
-        double dfr = -(f + kTwoOverSqrtPi * al * exp(-al2 * r2)) * ir;  // f'(r)
-        const double g2 = si2 + sg[j] * sg[j];
-        if (g2 > 0.0) {
-            const double ig = 1.0 / sqrt(g2);
-            const double fg = erfc(r * ig) * ir;
-            f -= fg;
-            dfr += (fg + kTwoOverSqrtPi * ig * exp(-r2 * ig * ig)) * ir;
-        }
-        v += xj.w * f;
-        if (FIELD) {
-            const double gq = xj.w * dfr * ir;
-            ex += gq * dx;
-            ey += gq * dy;
-            ez += gq * dz;
+    if (i < a.n) {
+        const double4_32a xi = xq[i];
+        const double si2 = sg[i] * sg[i];
+        const int c = cnt[i];
+        for (int k = sub; k < c; k += kTPR) {
+            const int32_t e = nbr[(size_t)k * a.n + i];
+            const int j = e & kIndexMask;
+            const double *sh = shift_tab[(uint32_t)e >> kIndexBits];
+            const double4_32a xj = xq[j];
+            const double dx = (xj.x - xi.x) + sh[0];
+            const double dy = (xj.y - xi.y) + sh[1];
+            const double dz = (xj.z - xi.z) + sh[2];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < a.rc2)) continue;
+            const double ir = rsqrt(r2);
+            const double r = r2 * ir;
+            double d1;
+            double f = erfc_pw(tab, al * r, d1) * ir;
+            double dfr = (al * d1 - f) * ir;  // d/dr [erfc(alpha r) / r]
+            const double g2 = si2 + sg[j] * sg[j];
+            if (g2 > 0.0) {
+                const double ig = rsqrt(g2);
+                double d2;
+                const double fg = erfc_pw(tab, r * ig, d2) * ir;
+                f -= fg;
+                dfr -= (ig * d2 - fg) * ir;
+            }
+            v += xj.w * f;
+            if (FIELD) {
+                const double gq = xj.w * dfr * ir;
+                ex += gq * dx;
+                ey += gq * dy;
+                ez += gq * dz;
+            }
         }
     }
-    v_s[i] = a.ke * v;
-    if (FIELD) {
-        E_s[3 * (size_t)i] = a.ke * ex;
-        E_s[3 * (size_t)i + 1] = a.ke * ey;
-        E_s[3 * (size_t)i + 2] = a.ke * ez;
+#pragma unroll
+    for (int o = 1; o < kTPR; o <<= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (FIELD) {
+            ex += __shfl_xor_sync(0xffffffffu, ex, o);
+            ey += __shfl_xor_sync(0xffffffffu, ey, o);
+            ez += __shfl_xor_sync(0xffffffffu, ez, o);
+        }
+    }
+    if (sub == 0 && i < a.n) {
+        v_s[i] = a.ke * v;
+        if (FIELD) {
+            E_s[3 * (size_t)i] = a.ke * ex;
+            E_s[3 * (size_t)i + 1] = a.ke * ey;
+            E_s[3 * (size_t)i + 2] = a.ke * ez;
+        }
+    }
+}
+
+// Self-test hook: the FP64 piecewise erfc and its derivative on n device inputs.
+__global__ void k_erfc64(int64_t n, const double *__restrict__ tab, const double *__restrict__ x,
+                         double *__restrict__ out, double *__restrict__ dout) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        double d;
+        out[t] = erfc_pw(tab, x[t], d);
+        dout[t] = d;
     }
 }
 
@@ -150,10 +223,11 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 }
 
 // FP32 pair math with one exp per erfc shared with the field term, image shifts
-// from a shared table, and FP32 chunk sums of 32 entries accumulated with
-// compensation (no FP64 arithmetic in the loop).
+// from a shared table, kTPR lanes per row, FP32 chunk sums of 32 entries
+// accumulated with compensation, and an FP32 shuffle combine of the lanes (no
+// FP64 arithmetic before the final scaling).
 template <bool FIELD>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, QEQ_REAL_MIN_BLOCKS)
 k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const float4 *__restrict__ xq, const float *__restrict__ sg, double *__restrict__ v_s,
          double *__restrict__ E_s) {
@@ -163,74 +237,92 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
                                    (float)((t / 5) % 5 - 2) * (float)a.Ly,
                                    (float)(t % 5 - 2) * (float)a.Lz, 0.f);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const float4 xi = xq[i];
-    const float si = sg[i];
-    const float si2 = si * si;
-    const int c = cnt[i];
-    const float al = (float)a.alpha, rc2 = (float)a.rc2;
-    const float tspa = (float)(kTwoOverSqrtPi * a.alpha);
-    const float tsp = (float)kTwoOverSqrtPi;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kTPR, sub = t % kTPR;
     float sv = 0.f, cv = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
     float vf = 0.f, exf = 0.f, eyf = 0.f, ezf = 0.f;
-    const int32_t *col = nbr + i;
+    if (i < a.n) {
+        const float4 xi = xq[i];
+        const float si = sg[i];
+        const float si2 = si * si;
+        const int c = cnt[i];
+        const float al = (float)a.alpha, rc2 = (float)a.rc2;
+        const float tspa = (float)(kTwoOverSqrtPi * a.alpha);
+        const float tsp = (float)kTwoOverSqrtPi;
+        const int32_t *col = nbr + i;
+        int chunk = 0;
 #pragma unroll 2
-    for (int k = 0; k < c; ++k) {
-        const int32_t e = __ldg(col + (size_t)k * a.n);
-        const int j = e & kIndexMask;
-        const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
-        const float4 xj = __ldg(xq + j);
-        const float dx = (xj.x - xi.x) + sh.x;
-        const float dy = (xj.y - xi.y) + sh.y;
-        const float dz = (xj.z - xi.z) + sh.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < rc2) {
-            const float ir = rsqrtf(r2);
-            const float r = r2 * ir;
-            const float x1 = al * r;
-            const float e1 = __expf(-x1 * x1);
-            float f = erfc_as7126(x1, e1) * ir;
-            float dfr = 0.f;
-            if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
-            const float sj = __ldg(sg + j);
-            const float g2 = fmaf(sj, sj, si2);
-            if (g2 > 0.f) {
-                const float ig = rsqrtf(g2);
-                const float x2 = r * ig;
-                const float e2 = __expf(-x2 * x2);
-                const float fg = erfc_as7126(x2, e2) * ir;
-                f -= fg;
-                if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
+        for (int k = sub; k < c; k += kTPR) {
+            const int32_t e = __ldg(col + (size_t)k * a.n);
+            const int j = e & kIndexMask;
+            const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
+            const float4 xj = __ldg(xq + j);
+            const float dx = (xj.x - xi.x) + sh.x;
+            const float dy = (xj.y - xi.y) + sh.y;
+            const float dz = (xj.z - xi.z) + sh.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 < rc2) {
+                const float ir = rsqrtf(r2);
+                const float r = r2 * ir;
+                const float x1 = al * r;
+                const float e1 = __expf(-x1 * x1);
+                float f = erfc_as7126(x1, e1) * ir;
+                float dfr = 0.f;
+                if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
+                const float sj = __ldg(sg + j);
+                const float g2 = fmaf(sj, sj, si2);
+                if (g2 > 0.f) {
+                    const float ig = rsqrtf(g2);
+                    const float x2 = r * ig;
+                    const float e2 = __expf(-x2 * x2);
+                    const float fg = erfc_as7126(x2, e2) * ir;
+                    f -= fg;
+                    if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
+                }
+                vf = fmaf(xj.w, f, vf);
+                if (FIELD) {
+                    const float gq = xj.w * dfr * ir;
+                    exf = fmaf(gq, dx, exf);
+                    eyf = fmaf(gq, dy, eyf);
+                    ezf = fmaf(gq, dz, ezf);
+                }
             }
-            vf = fmaf(xj.w, f, vf);
-            if (FIELD) {
-                const float gq = xj.w * dfr * ir;
-                exf = fmaf(gq, dx, exf);
-                eyf = fmaf(gq, dy, eyf);
-                ezf = fmaf(gq, dz, ezf);
+            if (++chunk == 32) {
+                chunk = 0;
+                kahan_add(sv, cv, vf);
+                vf = 0.f;
+                if (FIELD) {
+                    kahan_add(sx, cx, exf);
+                    kahan_add(sy, cy, eyf);
+                    kahan_add(sz, cz, ezf);
+                    exf = eyf = ezf = 0.f;
+                }
             }
         }
-        if ((k & 31) == 31) {
-            kahan_add(sv, cv, vf);
-            vf = 0.f;
-            if (FIELD) {
-                kahan_add(sx, cx, exf);
-                kahan_add(sy, cy, eyf);
-                kahan_add(sz, cz, ezf);
-                exf = eyf = ezf = 0.f;
-            }
+        kahan_add(sv, cv, vf);
+        if (FIELD) {
+            kahan_add(sx, cx, exf);
+            kahan_add(sy, cy, eyf);
+            kahan_add(sz, cz, ezf);
         }
     }
-    kahan_add(sv, cv, vf);
-    v_s[i] = a.ke * ((double)sv - (double)cv);
-    if (FIELD) {
-        kahan_add(sx, cx, exf);
-        kahan_add(sy, cy, eyf);
-        kahan_add(sz, cz, ezf);
-        E_s[3 * (size_t)i] = a.ke * ((double)sx - (double)cx);
-        E_s[3 * (size_t)i + 1] = a.ke * ((double)sy - (double)cy);
-        E_s[3 * (size_t)i + 2] = a.ke * ((double)sz - (double)cz);
+    float tv = sv - cv, tx = sx - cx, ty = sy - cy, tz = sz - cz;
+#pragma unroll
+    for (int o = 1; o < kTPR; o <<= 1) {
+        tv += __shfl_xor_sync(0xffffffffu, tv, o);
+        if (FIELD) {
+            tx += __shfl_xor_sync(0xffffffffu, tx, o);
+            ty += __shfl_xor_sync(0xffffffffu, ty, o);
+            tz += __shfl_xor_sync(0xffffffffu, tz, o);
+        }
+    }
+    if (sub == 0 && i < a.n) {
+        v_s[i] = a.ke * (double)tv;
+        if (FIELD) {
+            E_s[3 * (size_t)i] = a.ke * (double)tx;
+            E_s[3 * (size_t)i + 1] = a.ke * (double)ty;
+            E_s[3 * (size_t)i + 2] = a.ke * (double)tz;
+        }
     }
 }
 
@@ -281,6 +373,8 @@ __device__ __forceinline__ int wrap_index(int b, int K) {
     return r < 0 ? r + K : r;
 }
 
+// One thread per sorted atom; p^3 atomic adds per atom into the global mesh (the
+// mesh stays L2 resident; throughput is set by the L2 atomic units).
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads)
 k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__restrict__ sfrac,
@@ -308,111 +402,6 @@ k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__re
 #pragma unroll
             for (int c = 0; c < P; ++c) atomicAdd(row + iz[c], qab * Mz[c]);
         }
-    }
-}
-
-// Spread with a shared-memory brick.  Block b owns the atoms of cells
-// [b C, (b + 1) C), C consecutive cells along z of one cell column (C divides
-// the z cell count, so a block never straddles a column).  The block finds
-// the bounding box of its atoms' spline supports (base - (P-1) .. base per
-// axis).  It accumulates q M_x M_y M_z into that brick with shared-memory
-// atomics, then adds the nonzero brick points to the global mesh with one
-// atomic each.  A brick larger than `cap` points falls back to direct global
-// atomics for that block.
-template <typename T, int P>
-__global__ void __launch_bounds__(kThreads)
-k_spread_cells(int cells_per_block, const int32_t *__restrict__ cell_start,
-               const int4 *__restrict__ sbase, const typename V4<T>::type *__restrict__ sfrac,
-               int K0, int K1, int K2, int cap, T *__restrict__ mesh) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *brick = reinterpret_cast<T *>(smem_raw);
-    __shared__ int bmin[3], bmax[3];
-    const int c0 = blockIdx.x * cells_per_block;
-    const int a0 = cell_start[c0], a1 = cell_start[c0 + cells_per_block];
-    if (a1 == a0) return;  // uniform across the block
-    if (threadIdx.x < 3) {
-        bmin[threadIdx.x] = 0x7fffffff;
-        bmax[threadIdx.x] = -0x7fffffff;
-    }
-    __syncthreads();
-    int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
-    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
-        const int4 b = sbase[a];
-        lo[0] = min(lo[0], b.x); hi[0] = max(hi[0], b.x);
-        lo[1] = min(lo[1], b.y); hi[1] = max(hi[1], b.y);
-        lo[2] = min(lo[2], b.z); hi[2] = max(hi[2], b.z);
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-        }
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            atomicMin(&bmin[d], lo[d]);
-            atomicMax(&bmax[d], hi[d]);
-        }
-    }
-    __syncthreads();
-    const int ox = bmin[0] - (P - 1), oy = bmin[1] - (P - 1), oz = bmin[2] - (P - 1);
-    const int nx = bmax[0] - bmin[0] + P, ny = bmax[1] - bmin[1] + P, nz = bmax[2] - bmin[2] + P;
-    const int vol = nx * ny * nz;
-    const bool use_brick = vol <= cap;
-    if (use_brick) {
-        for (int t = threadIdx.x; t < vol; t += blockDim.x) brick[t] = T(0);
-        __syncthreads();
-    }
-    for (int a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
-        const int4 b = sbase[a];
-        const auto f = sfrac[a];
-        T Mx[P], My[P], Mz[P], dummy[P];
-        bspline<T, P, false>(f.x, Mx, dummy);
-        bspline<T, P, false>(f.y, My, dummy);
-        bspline<T, P, false>(f.z, Mz, dummy);
-        if (use_brick) {
-#pragma unroll
-            for (int ax = 0; ax < P; ++ax) {
-                const T qa = f.w * Mx[ax];
-#pragma unroll
-                for (int ay = 0; ay < P; ++ay) {
-                    const T qab = qa * My[ay];
-                    T *row = brick + ((b.x - ax - ox) * ny + (b.y - ay - oy)) * nz + (b.z - oz);
-#pragma unroll
-                    for (int az = 0; az < P; ++az) atomicAdd(row - az, qab * Mz[az]);
-                }
-            }
-        } else {
-            int iz[P];
-#pragma unroll
-            for (int az = 0; az < P; ++az) iz[az] = wrap_index(b.z - az, K2);
-#pragma unroll
-            for (int ax = 0; ax < P; ++ax) {
-                const int ix = wrap_index(b.x - ax, K0);
-                const T qa = f.w * Mx[ax];
-#pragma unroll
-                for (int ay = 0; ay < P; ++ay) {
-                    const int iy = wrap_index(b.y - ay, K1);
-                    const T qab = qa * My[ay];
-                    T *row = mesh + ((size_t)ix * K1 + iy) * K2;
-#pragma unroll
-                    for (int az = 0; az < P; ++az) atomicAdd(row + iz[az], qab * Mz[az]);
-                }
-            }
-        }
-    }
-    if (!use_brick) return;
-    __syncthreads();
-    const int nyz = ny * nz;
-    for (int t = threadIdx.x; t < vol; t += blockDim.x) {
-        const T val = brick[t];
-        if (val == T(0)) continue;
-        const int lx = t / nyz, rem = t - lx * nyz, ly = rem / nz, lz = rem - ly * nz;
-        const int ix = wrap_index(ox + lx, K0), iy = wrap_index(oy + ly, K1), iz = wrap_index(oz + lz, K2);
-        atomicAdd(mesh + ((size_t)ix * K1 + iy) * K2 + iz, val);
     }
 }
 
@@ -567,37 +556,53 @@ std::vector<double> bspline_mod2(int K, int p) {
     return out;
 }
 
-// Shared memory for one spread brick (bytes); the kernels are opted in at create time.
-constexpr int kSpreadSmemBytes = 64 * 1024;
+// Coefficients of the piecewise erfc: on piece k, [k h, (k + 1) h) with
+// h = kErfcXMax / kErfcPieces, the polynomial in s = 2 (x - k h) / h - 1 that
+// interpolates the long-double erfc at the kErfcCoef Chebyshev nodes of the
+// piece.  The Vandermonde system in s is solved by Gaussian elimination in long
+// double.
+std::vector<double> erfc_table() {
+    const int D = kErfcCoef;
+    std::vector<double> out((size_t)kErfcPieces * D);
+    const long double h = (long double)kErfcXMax / kErfcPieces;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = 0; k < kErfcPieces; ++k) {
+        long double A[kErfcCoef][kErfcCoef + 1];
+        for (int j = 0; j < D; ++j) {
+            const long double sj = cosl(pi * (j + 0.5L) / D);
+            const long double xj = k * h + (sj + 1.0L) * 0.5L * h;
+            long double pw = 1.0L;
+            for (int m = 0; m < D; ++m) {
+                A[j][m] = pw;
+                pw *= sj;
+            }
+            A[j][D] = erfcl(xj);
+        }
+        for (int c = 0; c < D; ++c) {
+            int best = c;
+            for (int r = c + 1; r < D; ++r)
+                if (fabsl(A[r][c]) > fabsl(A[best][c])) best = r;
+            for (int m = 0; m <= D; ++m) {
+                const long double tmp = A[c][m];
+                A[c][m] = A[best][m];
+                A[best][m] = tmp;
+            }
+            for (int r = 0; r < D; ++r) {
+                if (r == c) continue;
+                const long double f = A[r][c] / A[c][c];
+                for (int m = c; m <= D; ++m) A[r][m] -= f * A[c][m];
+            }
+        }
+        for (int m = 0; m < D; ++m) out[(size_t)k * D + m] = (double)(A[m][D] / A[m][m]);
+    }
+    return out;
+}
 
 template <typename T, int P>
 void launch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s) {
-    if (ctx->spread_cells_per_block > 0) {
-        const int blocks = (int)(ctx->ncell / ctx->spread_cells_per_block);
-        k_spread_cells<T, P><<<blocks, kThreads, kSpreadSmemBytes, s>>>(
-            ctx->spread_cells_per_block, ctx->cell_start, sb, (const typename V4<T>::type *)sf,
-            ctx->K[0], ctx->K[1], ctx->K[2], kSpreadSmemBytes / (int)sizeof(T), (T *)ctx->mesh);
-    } else {
-        k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
-            (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
-            (T *)ctx->mesh);
-    }
-}
-
-template <typename T, int P>
-cudaError_t opt_in_spread() {
-    return cudaFuncSetAttribute(k_spread_cells<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kSpreadSmemBytes);
-}
-
-template <typename T>
-cudaError_t opt_in_spread_all() {
-    cudaError_t e = opt_in_spread<T, 4>();
-    if (e == cudaSuccess) e = opt_in_spread<T, 5>();
-    if (e == cudaSuccess) e = opt_in_spread<T, 6>();
-    if (e == cudaSuccess) e = opt_in_spread<T, 7>();
-    if (e == cudaSuccess) e = opt_in_spread<T, 8>();
-    return e;
+    k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
+        (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
+        (T *)ctx->mesh);
 }
 
 template <typename T, int P, bool FIELD>
@@ -659,17 +664,17 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     prof_begin(ctx, kPhReal, s);
     if (f64) {
         if (need_field)
-            k_real64<true><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
-                                                            (double *)sg, ctx->v_s, ctx->E_s);
+            k_real64<true><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
+                                                            (double *)sg, ctx->erfc_tab64, ctx->v_s, ctx->E_s);
         else
-            k_real64<false><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
-                                                             (double *)sg, ctx->v_s, ctx->E_s);
+            k_real64<false><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
+                                                             (double *)sg, ctx->erfc_tab64, ctx->v_s, ctx->E_s);
     } else {
         if (need_field)
-            k_real32<true><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
+            k_real32<true><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
                                                             (float *)sg, ctx->v_s, ctx->E_s);
         else
-            k_real32<false><<<grid_for(n), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
+            k_real32<false><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
                                                              (float *)sg, ctx->v_s, ctx->E_s);
     }
 
@@ -761,18 +766,13 @@ int coulomb_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->energy4, sizeof(double) * 4},
     };
     for (auto &b : bufs) {
-        cudaError_t e = cudaMalloc(b.ptr, b.bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed", b.bytes);
-        }
+        int rc = dev_alloc(ctx, b.ptr, b.bytes);
+        if (rc) return rc;
     }
-    if (cudaMallocHost(&ctx->h_scal, sizeof(double) * kNumScal) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(ctx, QEQ_ERR_NOMEM, "pinned host allocation failed");
-    }
-    cudaMemset(ctx->scal, 0, sizeof(double) * kNumScal);
-    cudaMemset(ctx->part, 0, sizeof(double) * kMaxRedSlots * kRedBlocks);
+    ctx->h_scal = new (std::nothrow) double[kNumScal];
+    if (!ctx->h_scal) return set_error(ctx, QEQ_ERR_NOMEM, "host allocation failed");
+    cudaMemsetAsync(ctx->scal, 0, sizeof(double) * kNumScal, ctx->alloc_stream);
+    cudaMemsetAsync(ctx->part, 0, sizeof(double) * kMaxRedSlots * kRedBlocks, ctx->alloc_stream);
 
     // influence function G(m) = k_e (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2 * B(m) on the
     // half spectrum [K0][K1][K2/2+1], G(0) = 0 (Eq. ewald_rec with the smooth-PME B factor)
@@ -800,54 +800,73 @@ int coulomb_alloc(qeq_ctx *ctx) {
     cudaError_t e;
     if (ctx->fp32) {
         std::vector<float> Gf(G.begin(), G.end());
-        e = cudaMemcpy(ctx->G, Gf.data(), sizeof(float) * Gf.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(ctx->G, Gf.data(), sizeof(float) * Gf.size(), cudaMemcpyHostToDevice,
+                            ctx->alloc_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
     } else {
-        e = cudaMemcpy(ctx->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(ctx->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice,
+                            ctx->alloc_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
     }
     int rc = cuda_check(ctx, e, "influence upload");
     if (rc) return rc;
 
-    // spread bricks: C consecutive z cells per block, C | nc_z, brick within ~40 mesh points in z
+    // piecewise erfc table of the FP64 real-space kernel
     {
-        const int ncz = ctx->nc[2];
-        const double pts_per_cell = ctx->cw[2] * ctx->K[2] / p.box[2];
-        int best = 0;
-        for (int c = 1; c <= ncz; ++c)
-            if (ncz % c == 0 && c * pts_per_cell <= 40.0) best = c;
-        ctx->spread_cells_per_block = best;
-        cudaError_t ea = ctx->fp32 ? opt_in_spread_all<float>() : opt_in_spread_all<double>();
-        if (ea != cudaSuccess) {
-            cudaGetLastError();
-            ctx->spread_cells_per_block = 0;  // keep the direct-atomic spread
-        }
+        std::vector<double> tab = erfc_table();
+        rc = dev_alloc(ctx, (void **)&ctx->erfc_tab64, sizeof(double) * tab.size());
+        if (rc) return rc;
+        e = cudaMemcpyAsync(ctx->erfc_tab64, tab.data(), sizeof(double) * tab.size(),
+                            cudaMemcpyHostToDevice, ctx->alloc_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
+        rc = cuda_check(ctx, e, "erfc table upload");
+        if (rc) return rc;
     }
 
-    cufftResult cr = cufftPlan3d(&ctx->plan_r2c, ctx->K[0], ctx->K[1], ctx->K[2],
-                                 ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z);
-    if (cr == CUFFT_SUCCESS)
-        cr = cufftPlan3d(&ctx->plan_c2r, ctx->K[0], ctx->K[1], ctx->K[2],
-                         ctx->fp32 ? CUFFT_C2R : CUFFT_Z2D);
-    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftPlan3d failed (%d)", (int)cr);
+    // cuFFT plans with a work area from this library's allocator (no allocation inside cuFFT)
+    cufftResult cr = cufftCreate(&ctx->plan_r2c);
+    if (cr == CUFFT_SUCCESS) cr = cufftCreate(&ctx->plan_c2r);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftCreate failed (%d)", (int)cr);
     ctx->have_plans = true;
+    size_t ws1 = 0, ws2 = 0;
+    cr = cufftSetAutoAllocation(ctx->plan_r2c, 0);
+    if (cr == CUFFT_SUCCESS) cr = cufftSetAutoAllocation(ctx->plan_c2r, 0);
+    if (cr == CUFFT_SUCCESS)
+        cr = cufftMakePlan3d(ctx->plan_r2c, ctx->K[0], ctx->K[1], ctx->K[2],
+                             ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z, &ws1);
+    if (cr == CUFFT_SUCCESS)
+        cr = cufftMakePlan3d(ctx->plan_c2r, ctx->K[0], ctx->K[1], ctx->K[2],
+                             ctx->fp32 ? CUFFT_C2R : CUFFT_Z2D, &ws2);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftMakePlan3d failed (%d)", (int)cr);
+    rc = dev_alloc(ctx, &ctx->fft_work, ws1 > ws2 ? ws1 : ws2);
+    if (rc) return rc;
+    cr = cufftSetWorkArea(ctx->plan_r2c, ctx->fft_work);
+    if (cr == CUFFT_SUCCESS) cr = cufftSetWorkArea(ctx->plan_c2r, ctx->fft_work);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftSetWorkArea failed (%d)", (int)cr);
     return QEQ_OK;
 }
 
 void coulomb_free(qeq_ctx *ctx) {
-    void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
-                    ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
-                    ctx->scal, ctx->energy4};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->have_plans) {
         cufftDestroy(ctx->plan_r2c);
         cufftDestroy(ctx->plan_c2r);
     }
+    void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
+                    ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
+                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64};
+    for (void *p : ptrs) dev_free(ctx, p);
+    delete[] ctx->h_scal;
 }
 
 int erfc32_selftest(const float *x, float *out, int64_t n, cudaStream_t s) {
     k_erfc32<<<grid_for(n), kThreads, 0, s>>>(n, x, out);
     return cudaGetLastError() == cudaSuccess ? QEQ_OK : QEQ_ERR_CUDA;
+}
+
+int erfc64_selftest(qeq_ctx *ctx, const double *x, double *out, double *dout, int64_t n,
+                    cudaStream_t s) {
+    k_erfc64<<<grid_for(n), kThreads, 0, s>>>(n, ctx->erfc_tab64, x, out, dout);
+    return cuda_check(ctx, cudaGetLastError(), "erfc64 selftest");
 }
 
 int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,

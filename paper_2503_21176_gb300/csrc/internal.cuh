@@ -73,6 +73,10 @@ struct qeq_ctx {
     qeq_params p{};
     std::string err;
     int device = 0;
+    // Stream-ordered allocation (qeq_create_async): every device buffer comes
+    // from the device's default memory pool on alloc_stream.
+    bool async_alloc = false;
+    cudaStream_t alloc_stream = nullptr;
     int64_t n = 0;
     bool fp32 = false;
 
@@ -122,7 +126,8 @@ struct qeq_ctx {
     void *G = nullptr;         // influence function on the half spectrum (double or float)
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     bool have_plans = false;
-    int spread_cells_per_block = 0;  // 0: direct-atomic spread
+    void *fft_work = nullptr;  // cuFFT work area (shared by both plans, one stream at a time)
+    double *erfc_tab64 = nullptr;  // piecewise erfc coefficients of the FP64 real-space kernel
 
     // ---- reductions ----
     double *part = nullptr;    // [kMaxRedSlots][kRedBlocks]
@@ -150,6 +155,10 @@ namespace qeq {
 // ---- error helpers (api.cu) ----
 int set_error(qeq_ctx *ctx, int code, const char *fmt, ...);
 int cuda_check(qeq_ctx *ctx, cudaError_t e, const char *what);
+
+// ---- device memory (api.cu): cudaMalloc, or cudaMallocAsync on ctx->alloc_stream ----
+int dev_alloc(qeq_ctx *ctx, void **p, size_t bytes);
+void dev_free(qeq_ctx *ctx, void *p);
 
 // ---- neighbour list (nlist.cu) ----
 int nl_configure(qeq_ctx *ctx);  // cell grid from params

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "internal.cuh"
@@ -271,14 +272,10 @@ int nl_alloc_list(qeq_ctx *ctx, int width) {
     if (width > kMaxWidthLimit)
         return set_error(ctx, QEQ_ERR_CAPACITY, "neighbour row of %d entries exceeds the limit %d",
                          width, kMaxWidthLimit);
-    if (ctx->nbr) cudaFree(ctx->nbr);
+    dev_free(ctx, ctx->nbr);
     ctx->nbr = nullptr;
-    cudaError_t e = cudaMalloc(&ctx->nbr, sizeof(int32_t) * (size_t)width * ctx->n);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(ctx, QEQ_ERR_NOMEM, "cannot allocate a %d-wide neighbour list (%s)", width,
-                         cudaGetErrorString(e));
-    }
+    int rc = dev_alloc(ctx, (void **)&ctx->nbr, sizeof(int32_t) * (size_t)width * ctx->n);
+    if (rc) return rc;
     ctx->width = width;
     return QEQ_OK;
 }
@@ -304,16 +301,11 @@ int nl_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->d_flags, sizeof(int32_t) * kNumFlags},
     };
     for (auto &b : bufs) {
-        cudaError_t e = cudaMalloc(b.ptr, b.bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed", b.bytes);
-        }
+        int rc = dev_alloc(ctx, b.ptr, b.bytes);
+        if (rc) return rc;
     }
-    if (cudaMallocHost(&ctx->h_flags, sizeof(int32_t) * kNumFlags) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(ctx, QEQ_ERR_NOMEM, "pinned host allocation failed");
-    }
+    ctx->h_flags = new (std::nothrow) int32_t[kNumFlags];
+    if (!ctx->h_flags) return set_error(ctx, QEQ_ERR_NOMEM, "host allocation failed");
     int width = ctx->p.max_neighbors;
     if (width <= 0) {
         const double V = ctx->p.box[0] * ctx->p.box[1] * ctx->p.box[2];
@@ -328,9 +320,8 @@ void nl_free(qeq_ctx *ctx) {
     void *ptrs[] = {ctx->cell_of, ctx->cell_count, ctx->cell_start, ctx->cell_fill, ctx->tmp_list,
                     ctx->perm,    ctx->cell_s,     ctx->wrap_off,   ctx->R_build,   ctx->xs64,
                     ctx->xs32,    ctx->nbr,        ctx->cnt,        ctx->d_flags};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    for (void *p : ptrs) dev_free(ctx, p);
+    delete[] ctx->h_flags;
 }
 
 static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
@@ -414,7 +405,8 @@ int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr_out, int8_t *shift_out
     const int64_t n = ctx->n;
     const int w = ctx->width;
     std::vector<int32_t> perm(n), cnt(n), nbr((size_t)w * n);
-    int rc = cuda_check(ctx, cudaDeviceSynchronize(), "export sync");
+    int rc = cuda_check(ctx, ctx->async_alloc ? cudaStreamSynchronize(ctx->alloc_stream)
+                                              : cudaDeviceSynchronize(), "export sync");
     if (rc) return rc;
     rc = cuda_check(ctx, cudaMemcpy(perm.data(), ctx->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost),
                     "export perm");

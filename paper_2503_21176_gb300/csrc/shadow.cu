@@ -35,7 +35,7 @@ constexpr int S_MU = 40;    // sum (Phi w) / u
 constexpr int S_DOT = 41;   // Gram-Schmidt dot
 constexpr int S_OM = 48;    // O (kMaxRank^2, row-major) then g = R^T f (kMaxRank)
 constexpr int S_KE = 120;   // kinetic energy
-constexpr int S_SHORT = 121;
+constexpr int S_SHORT = 126;  // short-range energy: intramolecular, Lennard-Jones
 
 __global__ void k_lambda_part(int n, const double *__restrict__ chi, const double *__restrict__ u,
                               const double *__restrict__ v, double *__restrict__ inv_u,
@@ -244,7 +244,7 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
     }
     for (int a = 0; a < m; ++a) scal[S_OM + kMaxRank * kMaxRank + a] = x[a];
     const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
-    const double e_short = scal[S_SHORT];
+    const double e_short = scal[S_SHORT] + scal[S_SHORT + 1];
     energies[1] = scal[S_CHG + 1] + scal[S_CHG + 2] + scal[S_CHG + 3] - 0.5 * scal[S_CHG + 4] + e_short;
     energies[3] = e_short;
     energies[4] = lam;
@@ -366,17 +366,12 @@ int shadow_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->inv_m, sizeof(double) * n},
     };
     for (auto &b : bufs) {
-        cudaError_t e = cudaMalloc(b.ptr, b.bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation of %zu bytes failed", b.bytes);
-        }
+        int rc = dev_alloc(ctx, b.ptr, b.bytes);
+        if (rc) return rc;
     }
     if (ctx->p.short_range == QEQ_SHORT_WATER) {
-        if (cudaMalloc(&ctx->F_short, sizeof(double) * 3 * n) != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(ctx, QEQ_ERR_NOMEM, "device allocation failed");
-        }
+        int rc = dev_alloc(ctx, (void **)&ctx->F_short, sizeof(double) * 3 * n);
+        if (rc) return rc;
     }
     return QEQ_OK;
 }
@@ -384,8 +379,7 @@ int shadow_alloc(qeq_ctx *ctx) {
 void shadow_free(qeq_ctx *ctx) {
     void *ptrs[] = {ctx->v_n, ctx->E_n, ctx->phi, ctx->E_f, ctx->fvec, ctx->Wb,
                     ctx->Rb,  ctx->F_short, ctx->inv_u, ctx->inv_m};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    for (void *p : ptrs) dev_free(ctx, p);
 }
 
 int short_range_forces(qeq_ctx *ctx, const double *R, const double *mass, double *F_short,
@@ -410,7 +404,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         int rc = short_range_forces(ctx, st->R, prm->mass, ctx->F_short, scal + S_SHORT, s);
         if (rc) return rc;
     } else {
-        cudaMemsetAsync(scal + S_SHORT, 0, sizeof(double), s);
+        cudaMemsetAsync(scal + S_SHORT, 0, 2 * sizeof(double), s);
     }
     prof_end(ctx, s);
 
@@ -515,13 +509,6 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
     prof_end(ctx, s);
     ctx->launches += 3;
     return cuda_check(ctx, cudaGetLastError(), "shadow finish launch");
-}
-
-// Built-in short-range stand-in is added in a later translation unit; until then the
-// model reports that it is unavailable.
-int short_range_forces(qeq_ctx *ctx, const double *, const double *, double *, double *,
-                       cudaStream_t) {
-    return set_error(ctx, QEQ_ERR_UNSUPPORTED, "short-range water model not built in");
 }
 
 }  // namespace qeq

@@ -96,3 +96,39 @@ def test_neighbor_rebuild_during_run():
                              mesh=(16, 16, 16), r_cut=5.0, skin=0.05)
     assert np.abs(g["R"] - o["R"]).max() < 1e-9
     assert rel_max(g["q"], o["q"]) < 1e-8
+
+
+def test_shadow_md_with_water_short_range():
+    """Shadow MD with the built-in flexible-water V_short matches the oracle's step (FP64)."""
+    from oracle import short_range
+
+    qg = cuda_or_skip()
+    w = water_box(64, seed=77)
+    V0 = _maxwell(w, 0.02585, seed=5)
+    n0 = np.zeros(w.n_atoms)
+    mesh, r_cut, skin = (20, 20, 20), 6.0, 0.6
+    p = qg.make_params(w.n_atoms, w.box, alpha=0.34, r_cut=r_cut, skin=skin, mesh=mesh, order=4,
+                       krylov_rank=2, dissipation_k=5, dt=0.5, short_range=qg.QEQ_SHORT_WATER)
+    s = qg.System(p)
+    md = qg.ShadowMD(s, dev_tensor(w.chi), dev_tensor(w.eta), dev_tensor(w.sigma),
+                     dev_tensor(w.mass), dev_tensor(w.R), dev_tensor(V0), dev_tensor(n0))
+    md.init()
+
+    def coul(R, x, need_field=True):
+        o = ewald.coulomb_apply(R, x, w.sigma, w.box, 0.34, r_cut, recip="pme", mesh=mesh,
+                                order=4, gaussian_self=True)
+        return o["v"], o["E"]
+
+    osys = qeq.ShadowSystem(coul, w.chi, w.eta, w.mass, rank=2, dt=0.5, k_d=5,
+                            short=lambda R: short_range.water_short_range(R, w.box, r_cut))
+    st = osys.init_state(w.R, V0, n0)
+    e_short_ref = short_range.water_short_range(w.R, w.box, r_cut)[0]
+    assert abs(md.energy_dict()["short"] - e_short_ref) < 1e-9 * max(1.0, abs(e_short_ref))
+    for _ in range(10):
+        md.step()
+        st = osys.step(st)
+    assert np.abs(md.R.cpu().numpy() - st["R"]).max() < 1e-9
+    assert rel_max(md.F.cpu().numpy(), st["F"]) < 1e-8
+    e = md.energy_dict()
+    assert abs(e["total"] - (st["e_kin"] + st["e_pot"])) < 1e-8 * abs(st["e_pot"])
+    s.close()

@@ -6,6 +6,7 @@ dynamics arithmetic: both the CUDA path and the CPU oracle receive the arrays it
 produces and compute from them independently.
 """
 
+from .serving import serving_stream  # noqa: F401
 from .water import (  # noqa: F401
     WaterBox,
     water_box,
