@@ -530,6 +530,118 @@ def serve_bench(args):
     print(json.dumps(out))
 
 
+def table1_bench(args):
+    """Analogue of the paper's Table 1 (Sec. 4.1): regular BO-MD (GMRES + Jacobi) against
+    shadow MD (Krylov kernel to the same tolerance).  Shared settings: 100 water
+    molecules, NVE, 0.4 fs, about 300 K, the flexible-water V_short stand-in.
+    Reports Coulomb applies per step and the standard deviation of the total energy."""
+    import torch
+
+    import paper_2503_21176_gb300 as qg
+    from workloads import water_box
+
+    qg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = water_box(100, seed=2507)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    V0 = initial_state(w, 2508)
+    mesh, rc, alpha = (24, 24, 24), 7.0, 0.4
+    common = dict(alpha=alpha, r_cut=rc, skin=1.0, mesh=mesh, order=4, dt=0.4,
+                  short_range=qg.QEQ_SHORT_WATER, precision="fp64")
+    # reference charges at t = 0 from a tight solve
+    s0 = qg.System(qg.make_params(w.n_atoms, w.box, **common))
+    s0.neighbor_build(t(w.R))
+    q0 = torch.zeros(w.n_atoms, dtype=torch.float64, device=dev)
+    qg.qeq_solve(s0.ctx, t(w.R), t(w.chi), t(w.eta), t(w.sigma), q0, tol=1e-10)
+    s0.close()
+    rows = []
+    for method in ("shadow", "regular"):
+        for tol in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+            if method == "shadow":
+                s = qg.System(qg.make_params(w.n_atoms, w.box, krylov_rank=8, krylov_tol=tol, **common))
+                md = qg.ShadowMD(s, t(w.chi), t(w.eta), t(w.sigma), t(w.mass), t(w.R), t(V0), q0)
+            else:
+                s = qg.System(qg.make_params(w.n_atoms, w.box, **common))
+                md = qg.BOMD(s, t(w.chi), t(w.eta), t(w.sigma), t(w.mass), t(w.R), t(V0), q0, tol=tol)
+            md.init()
+            energies, applies = [], []
+            diverged = None
+            t_start = time.perf_counter()
+            for k in range(args.table1_steps):
+                try:
+                    md.step()
+                except qg.QeqError as exc:  # non-finite positions: the run blew up
+                    diverged = {"step": k, "error": str(exc)}
+                    break
+                e = md.energies.cpu().tolist()
+                if not math.isfinite(e[2]) or (energies and abs(e[2] - energies[0]) > 1e3):
+                    diverged = {"step": k, "error": "total energy diverged"}
+                    break
+                energies.append(e[2])
+                applies.append(e[7])
+            wall = time.perf_counter() - t_start
+            s.close()
+            E = np.array(energies) if energies else np.zeros(1)
+            rows.append({"method": method, "tol": tol, "applies_per_step": round(float(np.mean(applies)), 2)
+                         if applies else None, "energy_std_eV": float(np.std(E)),
+                         "energy_max_dev_eV": float(np.abs(E - E[0]).max()),
+                         "ms_per_step": round(1e3 * wall / max(1, len(energies)), 3),
+                         "diverged": diverged})
+    print(json.dumps({"experiment": "Table 1 analogue: shadow vs regular QEq-MD", "water_molecules": 100,
+                      "atoms": w.n_atoms, "steps": args.table1_steps, "dt_fs": 0.4,
+                      "settings": {"alpha": alpha, "r_cut": rc, "mesh": mesh, "order": 4,
+                                   "short_range": "flexible water stand-in", "precision": "fp64"},
+                      "rows": rows}))
+
+
+def crossover_bench(args):
+    """Regular Ewald (explicit k-sum) against PME for the charge-derivative apply, FP64, at
+    the paper's Sec. 4.2.2 settings: r_c 10 A, Ewald accuracy 5e-4 (alpha r_c = 2.46,
+    k_cut = 2 alpha sqrt(-ln 5e-4)), PME of order 6 with a mesh spacing near 1.3 A.
+    Water-like boxes of increasing size; milliseconds per apply (potential + field)."""
+    import torch
+
+    import paper_2503_21176_gb300 as qg
+    from workloads import water_box
+
+    qg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    r_c = 10.0
+    alpha = 2.4566 / r_c  # erfc(alpha r_c) = 5e-4
+    k_cut = 2.0 * alpha * math.sqrt(-math.log(5e-4))
+    rows = []
+    for n_mol in (50, 100, 200, 400, 800, 1600, 3200, 6400):
+        w = water_box(n_mol, seed=3000 + n_mol)
+        L = float(w.box[0])
+        K = max(8, int(math.ceil(L / 1.3 / 4.0)) * 4)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+        R, sig = t(w.R), t(w.sigma)
+        q = t(np.random.default_rng(n_mol).standard_normal(w.n_atoms) * 0.3)
+        row = {"atoms": w.n_atoms, "box_A": round(L, 2), "pme_mesh": K}
+        for method in ("pme", "ewald"):
+            p = qg.make_params(w.n_atoms, w.box, alpha=alpha, r_cut=r_c, skin=0.0, mesh=(K, K, K),
+                               order=6, recip=method, k_cut=k_cut)
+            s = qg.System(p)
+            s.neighbor_build(R)
+            for _ in range(3):
+                s.apply(R, q, sig)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(10):
+                s.apply(R, q, sig)
+            e1.record()
+            torch.cuda.synchronize()
+            row[f"{method}_ms"] = round(e0.elapsed_time(e1) / 10, 4)
+            s.close()
+        rows.append(row)
+    print(json.dumps({"experiment": "regular Ewald vs PME, FP64 charge derivatives and forces",
+                      "r_cut": r_c, "alpha": round(alpha, 5), "k_cut": round(k_cut, 4),
+                      "pme_order": 6, "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,12 +654,23 @@ def main():
     ap.add_argument("--reference-budget", type=float, default=200.0,
                     help="seconds of oracle work the reference arm may spend")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--table1", action="store_true",
+                    help="run the shadow vs regular QEq-MD tolerance sweep instead")
+    ap.add_argument("--table1-steps", type=int, default=2000)
+    ap.add_argument("--crossover", action="store_true",
+                    help="time the explicit Ewald k-sum against PME over system sizes instead")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-inflight", type=int, default=8)
     args = ap.parse_args()
     if args.serve:
         serve_bench(args)
+        return
+    if args.table1:
+        table1_bench(args)
+        return
+    if args.crossover:
+        crossover_bench(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -52,6 +52,11 @@ enum qeq_precision {
     QEQ_FP32_MIXED = 1  /* FP32 pair sum, spreading, FFT and gather with FP64 sums */
 };
 
+enum qeq_recip_method {
+    QEQ_RECIP_PME = 0,   /* smooth PME on the K^3 mesh (Alg. 2) */
+    QEQ_RECIP_EWALD = 1  /* explicit k-vector sum (Eq. ewald_rec), FP64 only */
+};
+
 enum qeq_short_model {
     QEQ_SHORT_NONE = 0, /* no short-range potential */
     QEQ_SHORT_WATER = 1 /* built-in flexible-water stand-in (not from the paper) */
@@ -80,12 +85,20 @@ enum qeq_short_model {
  *  max_neighbors   initial ELLPACK width (0 = estimate from density).  The
  *                  list grows by itself on overflow (Sec. 3.1).
  *  q_tot           total charge Q_tot of the constraint (Eq. linear_qeq).
- *  krylov_rank     m >= 1, rank of the low-rank kernel update (Sec. 3.5).
+ *  krylov_rank     m in 1..8, rank of the low-rank kernel update (Sec. 3.5);
+ *                  with krylov_tol > 0 it is the largest rank allowed.
+ *  krylov_tol      0: fixed rank m.  > 0: Krylov vectors are added until the
+ *                  least-squares residual |R c - f| / |f| of the kernel update
+ *                  is <= krylov_tol (the tolerance of the paper's Krylov solve
+ *                  of Eq. Jnddot).  Costs one host sync per added vector.
  *  dissipation_k   K_d in 3..7, the XL-BOMD dissipation window.
  *  dt              MD time step, in the time unit.
  *  short_range     enum qeq_short_model.
  *  mass_unit       length^2 * mass / time^2 expressed in the energy unit
  *                  (103.6427 for A, amu, fs, eV).
+ *  recip           enum qeq_recip_method: how Eq. ewald_rec is evaluated.
+ *  k_cut           |k| cutoff of the explicit k-sum (0: where
+ *                  exp(-k^2 / 4 alpha^2) falls below 1e-16).
  */
 typedef struct qeq_params {
     int64_t n_atoms;
@@ -100,11 +113,14 @@ typedef struct qeq_params {
     double k_e;
     int32_t max_neighbors;
     int32_t krylov_rank;
+    double krylov_tol;
     double q_tot;
     int32_t dissipation_k;
     int32_t short_range;
     double dt;
     double mass_unit;
+    int32_t recip;
+    double k_cut;
 } qeq_params;
 
 typedef struct qeq_ctx qeq_ctx;
@@ -167,6 +183,19 @@ int qeq_neighbor_build(qeq_ctx *ctx, const double *R, void *stream);
  * Any output may be NULL.  Synchronises.
  */
 int qeq_neighbor_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int8_t *shift);
+
+/*
+ * COO copy of the current list (Sec. 3.1: the sparse "coordinate list" format
+ * beside ELLPACK), written on the device: pair k is (pair_i[k], pair_j[k],
+ * image_code[k]).  Atom ids are in original numbering.  The image code is
+ * (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2), so that the displacement is
+ * x_j - x_i + s * box.  Pairs are grouped by row in the list's row order.
+ * capacity: the length of the three device arrays.  *n_pairs (host)
+ * receives the number of pairs.  When that exceeds the capacity, nothing is
+ * written and QEQ_ERR_CAPACITY is returned.  Synchronises `stream`.
+ */
+int qeq_neighbor_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *pair_i, int32_t *pair_j,
+                            int8_t *image_code, int64_t *n_pairs, void *stream);
 
 /*
  * Largest squared displacement of any atom since the last build, written to
@@ -286,9 +315,58 @@ int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, vo
  */
 int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, void *stream);
 
+/* Replay of qeq_shadow_step through a CUDA graph (default on).  The
+ * evaluation and second half kick of a fixed-rank step are captured on the
+ * first step and replayed afterwards (re-captured when buffers change).  It
+ * is skipped with krylov_tol > 0, with the profiler on, and on the legacy
+ * default stream.  on = 0 always launches kernel by kernel. */
+int qeq_set_graphs(qeq_ctx *ctx, int on);
+
 /* Same as qeq_shadow_step repeated n_steps times. */
 int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int32_t n_steps,
                    void *stream);
+
+/*
+ * Regular charge equilibration (Sec. 3.4, Eq. linear_qeq):
+ *   [diag(u) + Phi, 1; 1^T, 0] [q; lambda] = [-chi; Q_tot],
+ * solved matrix-free (one potential-only Coulomb apply per iteration) by
+ * restarted GMRES with a right Jacobi preconditioner, as the paper does for
+ * its regular BO-MD (Sec. 4.1).  The preconditioner diagonal is u_i plus the
+ * Gaussian self-energy when that term is on.  Iteration stops when
+ * ||b - A x|| / ||b|| <= tol (the paper's solver tolerance) or after max_iter
+ * iterations.
+ * q: device [N], the initial guess on entry and the solution on exit (lambda
+ * starts at 0).  info (host, nullable) receives iterations, Coulomb applies,
+ * the final true relative residual and lambda.  Synchronises once per
+ * iteration.  Needs a current neighbour list.
+ */
+typedef struct qeq_solve_info {
+    int32_t iterations;
+    int32_t applies;
+    double rel_residual;
+    double lambda;
+} qeq_solve_info;
+
+int qeq_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *eta,
+              const double *sigma, double *q, double tol, int32_t max_iter, int32_t restart,
+              qeq_solve_info *info, void *stream);
+
+/*
+ * Regular Born-Oppenheimer MD (Sec. 3.4), with the same state layout as the
+ * shadow step.  Kf and n_hist are unused and may be NULL.  q is the solution
+ * and also the warm start of the next solve.
+ * qeq_bomd_init: solve at the current R, then compute forces F = q o E[q]
+ * (+ short range) and energies.
+ * qeq_bomd_step: velocity-Verlet half kick and drift, a neighbour rebuild
+ * when due, the same evaluation, and the second half kick.
+ * energies (device [8]): 0 kinetic, 1 potential sum q chi + 1/2 sum u q^2 +
+ * 1/2 q.Phi q (+ short range), 2 total, 3 short range, 4 lambda, 5 sum q,
+ * 6 final relative residual, 7 Coulomb applies in the evaluation.
+ */
+int qeq_bomd_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
+                  int32_t max_iter, qeq_solve_info *info, void *stream);
+int qeq_bomd_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
+                  int32_t max_iter, qeq_solve_info *info, void *stream);
 
 /*
  * Diagnostic: evaluate the FP32 complementary error function used by the

@@ -94,11 +94,13 @@ def jacobian_apply(phi_x, x, u):
     return -(phi_x + mu) * inv_u - x
 
 
-def krylov_kernel(f, phi_f, apply_phi, u, m):
+def krylov_kernel(f, phi_f, apply_phi, u, m, tol=0.0):
     """Rank-m approximation of K f = J^{-1} f.
 
     ``phi_f`` is Phi f (already computed for the forces).  ``apply_phi(x)``
-    returns Phi x.  Returns (Kf, number of extra applies).
+    returns Phi x.  With tol > 0 the rank grows only until the least-squares
+    residual |R c - f| / |f| is <= tol (m is then the largest rank).
+    Returns (Kf, number of extra applies).
     """
     nrm = float(np.linalg.norm(f))
     if nrm == 0.0:
@@ -114,6 +116,11 @@ def krylov_kernel(f, phi_f, apply_phi, u, m):
         r = jacobian_apply(phi_w, w, u)
         W.append(w)
         Rk.append(r)
+        if tol > 0.0:
+            Rm = np.stack(Rk, axis=1)
+            c = np.linalg.solve(Rm.T @ Rm, Rm.T @ f)
+            if np.linalg.norm(Rm @ c - f) <= tol * nrm:
+                break
         if k + 1 < m:
             # next basis vector: r orthonormalised against w_1..w_k (modified Gram-Schmidt)
             nv = r.copy()
@@ -141,7 +148,7 @@ class ShadowSystem:
     ``short(R)`` returns (energy, forces) of V_short, or None.
     """
 
-    def __init__(self, coulomb, chi, u, mass, rank, dt, k_d=5, q_tot=0.0, short=None):
+    def __init__(self, coulomb, chi, u, mass, rank, dt, k_d=5, q_tot=0.0, short=None, krylov_tol=0.0):
         self.coulomb = coulomb
         self.chi = np.asarray(chi, dtype=np.float64)
         self.u = np.asarray(u, dtype=np.float64)
@@ -151,6 +158,7 @@ class ShadowSystem:
         self.k_d = int(k_d)
         self.q_tot = float(q_tot)
         self.short = short
+        self.krylov_tol = float(krylov_tol)
         self.kappa, self.alpha_d, self.c = xlbomd_coefficients(self.k_d)
 
     def evaluate(self, R, n):
@@ -165,7 +173,7 @@ class ShadowSystem:
             e_short, F_short = self.short(R)
             F = F + F_short
         Kf, extra = krylov_kernel(f, phi_f, lambda x: self.coulomb(R, x, False)[0], self.u,
-                                  self.rank)
+                                  self.rank, self.krylov_tol)
         e_pot = shadow_energy(q, n, v_n, self.chi, self.u) + e_short
         return {"q": q, "F": F, "Kf": Kf, "f": f, "v_n": v_n, "lam": lam,
                 "e_shadow": e_pot, "e_short": e_short, "applies": 2 + extra}
@@ -198,3 +206,128 @@ class ShadowSystem:
         V = V + 0.5 * dt * acc
         return {"R": R, "V": V, "hist": hist, "F": ev["F"], "Kf": ev["Kf"], "q": ev["q"],
                 "e_pot": ev["e_shadow"], "e_kin": self.kinetic(V), "applies": ev["applies"]}
+
+
+
+# ---------------------------------------------------------------------------
+# Regular QEq by GMRES and regular BO-MD (Sec. 3.4, Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def qeq_gmres(apply_phi, chi, u, q0, tol, max_iter=500, restart=40, q_tot=0.0, precond=None,
+              final_check=True, lam0=0.0):
+    """Restarted GMRES on the bordered QEq system, right-preconditioned by M = diag(d, 1).
+
+    ``apply_phi(x)`` returns Phi x.  ``precond`` is the diagonal d (defaults to u).
+    The stopping test is on the true relative residual ||b - A z|| / ||b||, the
+    paper's solver tolerance.  The Arnoldi basis is built by modified
+    Gram-Schmidt and the least-squares problem by Givens rotations.  Returns
+    (q, lambda, info).
+    """
+    chi = np.asarray(chi, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    n = chi.size
+    d = np.asarray(u if precond is None else precond, dtype=np.float64)
+    dinv = np.concatenate([1.0 / d, [1.0]])
+
+    def A(z):
+        y = np.empty(n + 1)
+        y[:n] = u * z[:n] + apply_phi(z[:n]) + z[n]
+        y[n] = z[:n].sum()
+        return y
+
+    b = np.concatenate([-chi, [q_tot]])
+    bnorm = np.linalg.norm(b) or 1.0
+    z = np.concatenate([np.asarray(q0, dtype=np.float64), [float(lam0)]])
+    iters = applies = 0
+    while True:
+        r = b - A(z)
+        applies += 1
+        beta = np.linalg.norm(r)
+        relres = beta / bnorm
+        if relres <= tol or iters >= max_iter or beta == 0.0:
+            break
+        V = [r / beta]
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        j = 0
+        while j < restart and iters < max_iter:
+            w = A(dinv * V[j])
+            applies += 1
+            iters += 1
+            for k in range(j + 1):
+                H[k, j] = V[k] @ w
+                w = w - H[k, j] * V[k]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V.append(w / H[j + 1, j])
+            for k in range(j):
+                a, bb = H[k, j], H[k + 1, j]
+                H[k, j], H[k + 1, j] = cs[k] * a + sn[k] * bb, -sn[k] * a + cs[k] * bb
+            rr = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = (H[j, j] / rr, H[j + 1, j] / rr) if rr > 0 else (1.0, 0.0)
+            H[j, j], H[j + 1, j] = rr, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j += 1
+            if abs(g[j]) / bnorm <= tol or len(V) <= j:
+                break
+        y = np.linalg.solve(np.triu(H[:j, :j]), g[:j]) if j else np.zeros(0)
+        z = z + dinv * (np.stack(V[:j], axis=1) @ y if j else 0.0)
+        if (abs(g[j]) / bnorm <= tol or iters >= max_iter) and not final_check:
+            relres = abs(g[j]) / bnorm
+            break
+        if abs(g[j]) / bnorm <= tol or iters >= max_iter:
+            r = b - A(z)
+            applies += 1
+            relres = np.linalg.norm(r) / bnorm
+            break
+    return z[:n], float(z[n]), {"iterations": iters, "applies": applies, "rel_residual": relres}
+
+
+class BOSystem:
+    """Regular BO-MD: a GMRES QEq solve per step (warm start), forces F = q o E[q] + F_short."""
+
+    def __init__(self, coulomb, chi, u, mass, dt, tol, max_iter=500, short=None, precond=None):
+        self.coulomb = coulomb
+        self.chi = np.asarray(chi, dtype=np.float64)
+        self.u = np.asarray(u, dtype=np.float64)
+        self.mass = np.asarray(mass, dtype=np.float64)
+        self.dt = float(dt)
+        self.tol = float(tol)
+        self.max_iter = int(max_iter)
+        self.short = short
+        self.precond = precond
+
+    def evaluate(self, R, q_guess, lam_guess=0.0):
+        q, lam, info = qeq_gmres(lambda x: self.coulomb(R, x, False)[0], self.chi, self.u, q_guess,
+                                 self.tol, self.max_iter, precond=self.precond, final_check=False,
+                                 lam0=lam_guess)
+        v, E = self.coulomb(R, q, True)
+        F = q[:, None] * E
+        e_short = 0.0
+        if self.short is not None:
+            e_short, Fs = self.short(R)
+            F = F + Fs
+        e_pot = float(q @ self.chi + 0.5 * np.sum(self.u * q * q) + 0.5 * q @ v) + e_short
+        return {"q": q, "lam": lam, "F": F, "e_pot": e_pot, "applies": info["applies"] + 1,
+                "info": info}
+
+    def kinetic(self, V):
+        return 0.5 * AMU_A2_FS2_IN_EV * float(np.sum(self.mass[:, None] * V * V))
+
+    def init_state(self, R, V, q0):
+        ev = self.evaluate(R, q0)
+        return {"R": np.array(R, dtype=np.float64), "V": np.array(V, dtype=np.float64),
+                "q": ev["q"], "lam": ev["lam"], "F": ev["F"], "e_pot": ev["e_pot"],
+                "e_kin": self.kinetic(V), "applies": ev["applies"]}
+
+    def step(self, st):
+        dt = self.dt
+        V = st["V"] + 0.5 * dt * st["F"] / (self.mass[:, None] * AMU_A2_FS2_IN_EV)
+        R = st["R"] + dt * V
+        ev = self.evaluate(R, st["q"], st["lam"])
+        V = V + 0.5 * dt * ev["F"] / (self.mass[:, None] * AMU_A2_FS2_IN_EV)
+        return {"R": R, "V": V, "q": ev["q"], "lam": ev["lam"], "F": ev["F"], "e_pot": ev["e_pot"],
+                "e_kin": self.kinetic(V), "applies": ev["applies"]}

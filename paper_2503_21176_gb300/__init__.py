@@ -39,9 +39,12 @@ from ._lib import (  # noqa: F401
     qeq_profile_enable,
     qeq_profile_phase_name,
     qeq_profile_read,
+    qeq_bomd_init,
+    qeq_bomd_step,
     qeq_shadow_init,
     qeq_shadow_run,
     qeq_shadow_step,
+    qeq_solve,
 )
 
 from .autograd import CoulombEnergy, coulomb_energy  # noqa: E402,F401
@@ -52,7 +55,7 @@ PRECISIONS = {"fp64": QEQ_FP64, "fp32_mixed": QEQ_FP32_MIXED}
 def make_params(n_atoms, box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(32, 32, 32), order=4,
                 precision="fp64", gaussian_self=True, k_e=14.3996454784, max_neighbors=0,
                 krylov_rank=2, q_tot=0.0, dissipation_k=5, dt=0.5, short_range=QEQ_SHORT_NONE,
-                mass_unit=103.6427) -> qeq_params:
+                mass_unit=103.6427, krylov_tol=0.0, recip="pme", k_cut=0.0) -> qeq_params:
     p = qeq_params_default()
     p.n_atoms = int(n_atoms)
     for d in range(3):
@@ -67,6 +70,10 @@ def make_params(n_atoms, box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(32, 32, 32)
     p.k_e = float(k_e)
     p.max_neighbors = int(max_neighbors)
     p.krylov_rank = int(krylov_rank)
+    p.krylov_tol = float(krylov_tol)
+    p.recip = {"pme": _lib.QEQ_RECIP_PME, "ewald": _lib.QEQ_RECIP_EWALD}[recip] \
+        if isinstance(recip, str) else int(recip)
+    p.k_cut = float(k_cut)
     p.q_tot = float(q_tot)
     p.dissipation_k = int(dissipation_k)
     p.dt = float(dt)
@@ -150,3 +157,33 @@ class ShadowMD:
         e = self.energies.cpu().tolist()
         return {"kinetic": e[0], "shadow_potential": e[1], "total": e[2], "short": e[3],
                 "lambda": e[4], "sum_q": e[5], "residual_norm": e[6], "applies": e[7]}
+
+
+class BOMD:
+    """Caller-side state of regular Born-Oppenheimer MD with a GMRES QEq solve per step."""
+
+    def __init__(self, system: System, chi, eta, sigma, mass, R, V, q0, tol, max_iter=500):
+        self.sys = system
+        n = system.n
+        f64 = dict(dtype=torch.float64, device=system.device)
+        self.chi, self.eta, self.sigma, self.mass = (t.contiguous() for t in (chi, eta, sigma, mass))
+        self.R = R.clone().contiguous()
+        self.V = V.clone().contiguous()
+        self.F = torch.zeros(n, 3, **f64)
+        self.q = q0.clone().contiguous()
+        self.energies = torch.zeros(8, **f64)
+        self.tol = float(tol)
+        self.max_iter = int(max_iter)
+        self._prm = md_params(self.chi, self.eta, self.sigma, self.mass)
+        self._st = _lib._bo_state(self.R, self.V, self.F, self.q, self.energies)
+
+    def init(self, stream=None):
+        return qeq_bomd_init(self.sys.ctx, self._prm, self._st, self.tol, self.max_iter, stream)
+
+    def step(self, stream=None):
+        return qeq_bomd_step(self.sys.ctx, self._prm, self._st, self.tol, self.max_iter, stream)
+
+    def energy_dict(self):
+        e = self.energies.cpu().tolist()
+        return {"kinetic": e[0], "potential": e[1], "total": e[2], "short": e[3], "lambda": e[4],
+                "sum_q": e[5], "rel_residual": e[6], "applies": e[7]}

@@ -18,6 +18,8 @@ from . import _build
 QEQ_OK = 0
 QEQ_FP64 = 0
 QEQ_FP32_MIXED = 1
+QEQ_RECIP_PME = 0
+QEQ_RECIP_EWALD = 1
 QEQ_SHORT_NONE = 0
 QEQ_SHORT_WATER = 1
 
@@ -53,11 +55,14 @@ class qeq_params(ctypes.Structure):
         ("k_e", ctypes.c_double),
         ("max_neighbors", ctypes.c_int32),
         ("krylov_rank", ctypes.c_int32),
+        ("krylov_tol", ctypes.c_double),
         ("q_tot", ctypes.c_double),
         ("dissipation_k", ctypes.c_int32),
         ("short_range", ctypes.c_int32),
         ("dt", ctypes.c_double),
         ("mass_unit", ctypes.c_double),
+        ("recip", ctypes.c_int32),
+        ("k_cut", ctypes.c_double),
     ]
 
 
@@ -67,6 +72,11 @@ class qeq_md_state(ctypes.Structure):
 
 class qeq_md_params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in ("chi", "eta", "sigma", "mass")]
+
+
+class qeq_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("applies", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("lambda_", ctypes.c_double)]
 
 
 _lib = None
@@ -113,6 +123,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_selftest_erfc32.restype = ctypes.c_int
     L.qeq_selftest_erfc64.argtypes = [P, P, P, P, ctypes.c_int64, P]
     L.qeq_selftest_erfc64.restype = ctypes.c_int
+    SI = ctypes.POINTER(qeq_solve_info)
+    L.qeq_solve.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, SI, P]
+    L.qeq_solve.restype = ctypes.c_int
+    for name in ("qeq_bomd_init", "qeq_bomd_step"):
+        getattr(L, name).argtypes = [P, ctypes.POINTER(qeq_md_params), ctypes.POINTER(qeq_md_state),
+                                     ctypes.c_double, ctypes.c_int32, SI, P]
+        getattr(L, name).restype = ctypes.c_int
+    L.qeq_neighbor_export_coo.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.POINTER(ctypes.c_int64), P]
+    L.qeq_neighbor_export_coo.restype = ctypes.c_int
+    L.qeq_set_graphs.argtypes = [P, ctypes.c_int]
+    L.qeq_set_graphs.restype = ctypes.c_int
     L.qeq_profile_enable.argtypes = [P, ctypes.c_int]
     L.qeq_profile_read.argtypes = [P, P, P, ctypes.c_int]
     L.qeq_profile_phase_name.argtypes = [ctypes.c_int]
@@ -333,3 +354,55 @@ def qeq_selftest_erfc64(ctx, x, out, dout, stream=None) -> None:
     """FP64 piecewise erfc and its derivative of the real-space kernel (CUDA float64 tensors)."""
     _check(ctx, load().qeq_selftest_erfc64(ctx, _dev(x, "x"), _dev(out, "out"), _dev(dout, "dout"),
                                            x.numel(), _stream(stream)))
+
+
+def qeq_solve(ctx, R, chi, eta, sigma, q, tol, max_iter=500, restart=40, stream=None):
+    """Regular QEq by GMRES; q (CUDA float64 [N]) is the guess on entry, the solution on exit."""
+    info = qeq_solve_info()
+    _check(ctx, load().qeq_solve(ctx, _dev(R, "R"), _dev(chi, "chi"), _dev(eta, "eta"),
+                                 _dev(sigma, "sigma"), _dev(q, "q"), float(tol), int(max_iter),
+                                 int(restart), ctypes.byref(info), _stream(stream)))
+    return {"iterations": info.iterations, "applies": info.applies,
+            "rel_residual": info.rel_residual, "lambda": info.lambda_}
+
+
+def _bo_state(R, V, F, q, energies) -> qeq_md_state:
+    return qeq_md_state(_dev(R, "R"), _dev(V, "V"), _dev(F, "F"), None, None, _dev(q, "q"),
+                        _dev(energies, "energies"))
+
+
+def qeq_bomd_init(ctx, prm, st, tol, max_iter=500, stream=None):
+    info = qeq_solve_info()
+    _check(ctx, load().qeq_bomd_init(ctx, ctypes.byref(prm), ctypes.byref(st), float(tol),
+                                     int(max_iter), ctypes.byref(info), _stream(stream)))
+    return {"iterations": info.iterations, "applies": info.applies,
+            "rel_residual": info.rel_residual, "lambda": info.lambda_}
+
+
+def qeq_bomd_step(ctx, prm, st, tol, max_iter=500, stream=None):
+    info = qeq_solve_info()
+    _check(ctx, load().qeq_bomd_step(ctx, ctypes.byref(prm), ctypes.byref(st), float(tol),
+                                     int(max_iter), ctypes.byref(info), _stream(stream)))
+    return {"iterations": info.iterations, "applies": info.applies,
+            "rel_residual": info.rel_residual, "lambda": info.lambda_}
+
+
+def qeq_neighbor_export_coo(ctx, capacity=None, stream=None):
+    """Device COO copy of the list: (pair_i, pair_j, image_code) CUDA tensors."""
+    n, w = qeq_get_sizes(ctx)
+    cap = int(capacity) if capacity is not None else n * w
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pi = torch.empty(cap, dtype=torch.int32, device=dev)
+    pj = torch.empty(cap, dtype=torch.int32, device=dev)
+    code = torch.empty(cap, dtype=torch.int8, device=dev)
+    npairs = ctypes.c_int64(0)
+    _check(ctx, load().qeq_neighbor_export_coo(ctx, cap, ctypes.c_void_p(pi.data_ptr()),
+                                               ctypes.c_void_p(pj.data_ptr()),
+                                               ctypes.c_void_p(code.data_ptr()), ctypes.byref(npairs),
+                                               _stream(stream)))
+    m = int(npairs.value)
+    return pi[:m], pj[:m], code[:m]
+
+
+def qeq_set_graphs(ctx, on: bool) -> None:
+    _check(ctx, load().qeq_set_graphs(ctx, int(bool(on))))

@@ -75,6 +75,13 @@ static int validate(const qeq_params *p) {
     if (p->precision != QEQ_FP64 && p->precision != QEQ_FP32_MIXED)
         return set_error(nullptr, QEQ_ERR_INVALID, "unknown precision %d", p->precision);
     if (!(p->k_e > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "k_e must be positive");
+    if (p->recip != QEQ_RECIP_PME && p->recip != QEQ_RECIP_EWALD)
+        return set_error(nullptr, QEQ_ERR_INVALID, "unknown reciprocal method %d", p->recip);
+    if (p->recip == QEQ_RECIP_EWALD && p->precision != QEQ_FP64)
+        return set_error(nullptr, QEQ_ERR_UNSUPPORTED, "the explicit k-sum runs in FP64 only");
+    if (!(p->k_cut >= 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "k_cut must be >= 0");
+    if (!(p->krylov_tol >= 0.0))
+        return set_error(nullptr, QEQ_ERR_INVALID, "krylov_tol must be >= 0");
     if (p->krylov_rank < 1 || p->krylov_rank > kMaxRank)
         return set_error(nullptr, QEQ_ERR_INVALID, "krylov_rank must be in [1, %d]", kMaxRank);
     if (p->dissipation_k < 3 || p->dissipation_k > 7)
@@ -89,10 +96,19 @@ static int validate(const qeq_params *p) {
     return QEQ_OK;
 }
 
+static void drop_graph(qeq_ctx *ctx) {
+    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+    ctx->step_exec = nullptr;
+    ctx->step_graph = nullptr;
+}
+
 static void destroy(qeq_ctx *ctx) {
     if (!ctx) return;
     if (!ctx->async_alloc) cudaDeviceSynchronize();
+    drop_graph(ctx);
     for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+    solver_free(ctx);
     shadow_free(ctx);
     coulomb_free(ctx);
     nl_free(ctx);
@@ -118,6 +134,9 @@ QEQ_API void qeq_params_default(qeq_params *p) {
     p->k_e = 14.3996454784;
     p->max_neighbors = 0;
     p->krylov_rank = 2;
+    p->krylov_tol = 0.0;
+    p->recip = QEQ_RECIP_PME;
+    p->k_cut = 0.0;
     p->q_tot = 0.0;
     p->dissipation_k = 5;
     p->short_range = QEQ_SHORT_NONE;
@@ -199,6 +218,16 @@ QEQ_API int qeq_neighbor_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int
     return nl_export(ctx, counts, nbr, shift);
 }
 
+QEQ_API int qeq_neighbor_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *pair_i,
+                                    int32_t *pair_j, int8_t *image_code, int64_t *n_pairs,
+                                    void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!pair_i || !pair_j || !image_code || !n_pairs)
+        return set_error(ctx, QEQ_ERR_INVALID, "NULL argument");
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "no neighbour list built yet");
+    return nl_export_coo(ctx, capacity, pair_i, pair_j, image_code, n_pairs, (cudaStream_t)stream);
+}
+
 QEQ_API int qeq_neighbor_displacement(qeq_ctx *ctx, const double *R, double *max_disp2,
                                       void *stream) {
     if (!ctx) return QEQ_ERR_INVALID;
@@ -240,6 +269,56 @@ QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
     return shadow_finish(ctx, prm, st, false, s);
 }
 
+// The evaluation and the second half kick of a fixed-rank shadow step contain
+// no host synchronisation, so they are captured once into a CUDA graph and
+// replayed.  The graph is re-captured when the state, parameter or neighbour-list
+// buffers it was recorded with change.  It is not used with a tolerance-driven
+// Krylov rank (host reads), with the profiler on, or on the legacy default
+// stream (which cannot be captured).
+static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
+                               cudaStream_t s) {
+    const bool graphable = ctx->use_graphs && s != nullptr && !(ctx->p.krylov_tol > 0.0) &&
+                           !ctx->prof.on;
+    if (!graphable) {
+        int rc = shadow_evaluate(ctx, prm, st, s);
+        if (rc) return rc;
+        return shadow_finish(ctx, prm, st, true, s);
+    }
+    const void *key[14] = {st->R, st->V, st->F, st->Kf, st->n_hist, st->q, st->energies,
+                           prm->chi, prm->eta, prm->sigma, prm->mass, ctx->nbr, nullptr, nullptr};
+    bool same = ctx->step_exec && ctx->graph_width == ctx->width;
+    for (int k = 0; k < 14 && same; ++k) same = key[k] == ctx->graph_key[k];
+    if (!same) {
+        drop_graph(ctx);
+        const int64_t l0 = ctx->launches, a0 = ctx->applies;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture begin");
+        int rc = shadow_evaluate(ctx, prm, st, s);
+        if (!rc) rc = shadow_finish(ctx, prm, st, true, s);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture end");
+        e = cudaGraphInstantiate(&ctx->step_exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_check(ctx, e, "graph instantiate");
+        }
+        ctx->step_graph = g;
+        ctx->graph_width = ctx->width;
+        ctx->graph_launches = ctx->launches - l0;
+        ctx->launches = l0;
+        ctx->applies = a0;
+        for (int k = 0; k < 14; ++k) ctx->graph_key[k] = key[k];
+    }
+    ctx->launches += ctx->graph_launches;
+    ctx->applies += ctx->p.krylov_rank + 1;
+    return cuda_check(ctx, cudaGraphLaunch(ctx->step_exec, s), "graph launch");
+}
+
 QEQ_API int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
                             void *stream) {
     int rc = check_md(ctx, prm, st);
@@ -248,9 +327,14 @@ QEQ_API int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
     cudaStream_t s = (cudaStream_t)stream;
     rc = shadow_advance(ctx, prm, st, s);
     if (rc) return rc;
-    rc = shadow_evaluate(ctx, prm, st, s);
-    if (rc) return rc;
-    return shadow_finish(ctx, prm, st, true, s);
+    return evaluate_and_finish(ctx, prm, st, s);
+}
+
+QEQ_API int qeq_set_graphs(qeq_ctx *ctx, int on) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    ctx->use_graphs = on != 0;
+    if (!ctx->use_graphs) drop_graph(ctx);
+    return QEQ_OK;
 }
 
 QEQ_API int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
@@ -345,4 +429,68 @@ QEQ_API int qeq_selftest_erfc64(qeq_ctx *ctx, const double *x, double *out, doub
     if (!x || !out || !dout || n < 0) return set_error(ctx, QEQ_ERR_INVALID, "selftest: bad argument");
     if (n == 0) return QEQ_OK;
     return erfc64_selftest(ctx, x, out, dout, n, (cudaStream_t)stream);
+}
+
+// ---- regular QEq by GMRES, regular BO-MD ----
+
+QEQ_API int qeq_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *eta,
+                      const double *sigma, double *q, double tol, int32_t max_iter, int32_t restart,
+                      qeq_solve_info *info, void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!R || !chi || !eta || !sigma || !q) return set_error(ctx, QEQ_ERR_INVALID, "NULL argument");
+    if (!(tol > 0.0) || max_iter < 1 || restart < 1)
+        return set_error(ctx, QEQ_ERR_INVALID, "tol, max_iter and restart must be positive");
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "qeq_solve before neighbor_build");
+    ctx->err.clear();
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = solver_alloc(ctx, restart > 64 ? 64 : restart);
+    if (rc) return rc;
+    if (!ctx->gmSol) {
+        rc = dev_alloc(ctx, (void **)&ctx->gmSol, sizeof(double) * (ctx->n + 1));
+        if (rc) return rc;
+    }
+    cudaMemsetAsync(ctx->gmSol, 0, sizeof(double) * (ctx->n + 1), s);
+    cudaMemcpyAsync(ctx->gmSol, q, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, s);
+    qeq_solve_info local{};
+    rc = gmres_solve(ctx, R, chi, eta, sigma, ctx->gmSol, tol, max_iter, restart, true, &local, s);
+    if (rc) return rc;
+    cudaMemcpyAsync(q, ctx->gmSol, sizeof(double) * ctx->n, cudaMemcpyDeviceToDevice, s);
+    if (info) *info = local;
+    return cuda_check(ctx, cudaStreamSynchronize(s), "qeq_solve");
+}
+
+static int check_bo(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *st) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!prm || !st || !prm->chi || !prm->eta || !prm->sigma || !prm->mass)
+        return set_error(ctx, QEQ_ERR_INVALID, "NULL md params");
+    if (!st->R || !st->V || !st->F || !st->q || !st->energies)
+        return set_error(ctx, QEQ_ERR_INVALID, "NULL state array");
+    ctx->err.clear();
+    return QEQ_OK;
+}
+
+QEQ_API int qeq_bomd_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
+                          int32_t max_iter, qeq_solve_info *info, void *stream) {
+    int rc = check_bo(ctx, prm, st);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->list_valid) {
+        rc = nl_build(ctx, st->R, s);
+        if (rc) return rc;
+    }
+    rc = bomd_evaluate(ctx, prm, st, tol, max_iter, info, s);
+    if (rc) return rc;
+    return shadow_finish(ctx, prm, st, false, s);
+}
+
+QEQ_API int qeq_bomd_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
+                          int32_t max_iter, qeq_solve_info *info, void *stream) {
+    int rc = check_bo(ctx, prm, st);
+    if (rc) return rc;
+    if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "call qeq_bomd_init first");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = bomd_advance(ctx, prm, st, s);
+    if (!rc) rc = bomd_evaluate(ctx, prm, st, tol, max_iter, info, s);
+    if (!rc) rc = shadow_finish(ctx, prm, st, true, s);
+    return rc;
 }

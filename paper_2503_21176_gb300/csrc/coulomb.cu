@@ -154,7 +154,8 @@ k_real64(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
             double f = erfc_pw(tab, al * r, d1) * ir;
             double dfr = (al * d1 - f) * ir;  // d/dr [erfc(alpha r) / r]
             const double g2 = si2 + sg[j] * sg[j];
-            if (g2 > 0.0) {
+            // Gaussian correction; the table is exactly 0 beyond r / gamma = kErfcXMax
+            if (r2 < kErfcXMax * kErfcXMax * g2) {
                 const double ig = rsqrt(g2);
                 double d2;
                 const double fg = erfc_pw(tab, r * ig, d2) * ir;
@@ -271,7 +272,9 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
                 if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
                 const float sj = __ldg(sg + j);
                 const float g2 = fmaf(sj, sj, si2);
-                if (g2 > 0.f) {
+                // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
+                // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
+                if (r * r < 25.f * g2) {
                     const float ig = rsqrtf(g2);
                     const float x2 = r * ig;
                     const float e2 = __expf(-x2 * x2);
@@ -680,6 +683,15 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
 
     prof_end(ctx, s);
     ctx->launches++;
+    if (p.recip == QEQ_RECIP_EWALD) {
+        int rc = ewald_recip_and_combine(ctx, q, sigma, v, E, F, need_field, s);
+        if (rc) return rc;
+        if (energy4) {
+            k_finalize<<<4, kThreads, 0, s>>>(ctx->part, energy4);
+            ctx->launches++;
+        }
+        return cuda_check(ctx, cudaGetLastError(), "coulomb apply launch");
+    }
     prof_begin(ctx, kPhSpread, s);
     cudaMemsetAsync(ctx->mesh, 0, sizeof(T) * ctx->mesh_n, s);
     dispatch_spread<T>(ctx, ctx->sbase, ctx->sfrac, s);
@@ -811,6 +823,11 @@ int coulomb_alloc(qeq_ctx *ctx) {
     int rc = cuda_check(ctx, e, "influence upload");
     if (rc) return rc;
 
+    if (p.recip == QEQ_RECIP_EWALD) {
+        rc = ewald_alloc(ctx);
+        if (rc) return rc;
+    }
+
     // piecewise erfc table of the FP64 real-space kernel
     {
         std::vector<double> tab = erfc_table();
@@ -855,6 +872,7 @@ void coulomb_free(qeq_ctx *ctx) {
                     ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
                     ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64};
     for (void *p : ptrs) dev_free(ctx, p);
+    ewald_free(ctx);
     delete[] ctx->h_scal;
 }
 

@@ -21,8 +21,14 @@ constexpr int kThreads = 256;
 // that reduce write one partial per block into a [slot][kRedBlocks] table, and a
 // one-block finalize sums each slot in a fixed order (deterministic results).
 constexpr int kRedBlocks = 1216;
-constexpr int kMaxRedSlots = 32;
 constexpr int kMaxRank = 8;
+// Reduction slots: the largest user is the GMRES multi-dot (restart <= 64
+// vectors plus the norm); the Krylov normal equations need
+// kMaxRank (kMaxRank + 1) / 2 + kMaxRank.
+constexpr int kMaxGmresRestart = 64;
+constexpr int kMaxRedSlots = 72;
+static_assert(kMaxRank * (kMaxRank + 1) / 2 + kMaxRank <= kMaxRedSlots, "reduction slots");
+static_assert(kMaxGmresRestart + 1 <= kMaxRedSlots, "reduction slots");
 constexpr int kMaxHist = 8;
 // A neighbour entry packs the sorted atom index (low 24 bits) and the image
 // code (high 8 bits): code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2), |s| <= 2.
@@ -39,7 +45,7 @@ enum Flag { kFlagMaxRow = 0, kFlagNonFinite = 1, kNumFlags = 4 };
 
 // Device scalar table (double).  Slot 4 holds the last max displacement^2;
 // shadow.cu uses slots 32..127 for its reductions.
-enum Scal { kScMaxDisp2 = 4, kNumScal = 128 };
+enum Scal { kScMaxDisp2 = 4, kNumScal = 160 };
 
 // Phases timed by the optional CUDA-event profiler (qeq_profile_*).
 enum Phase {
@@ -129,6 +135,12 @@ struct qeq_ctx {
     void *fft_work = nullptr;  // cuFFT work area (shared by both plans, one stream at a time)
     double *erfc_tab64 = nullptr;  // piecewise erfc coefficients of the FP64 real-space kernel
 
+    // ---- explicit k-vector Ewald (ewald.cu) ----
+    void *ewald_k = nullptr;        // [nk] double4 (kx, ky, kz, g)
+    void *ewald_S = nullptr;        // [nk] double2 structure factor
+    void *ewald_partial = nullptr;  // [nchunk][nk] double2
+    int ewald_nk = 0, ewald_nchunk = 0;
+
     // ---- reductions ----
     double *part = nullptr;    // [kMaxRedSlots][kRedBlocks]
     double *scal = nullptr;    // [kNumScal]
@@ -141,7 +153,24 @@ struct qeq_ctx {
     double *F_short = nullptr; // [N][3]
     double *inv_u = nullptr;   // [N] 1 / u of the current evaluation
     double *inv_m = nullptr;   // [N] 1 / (m * mass_unit) of the current step
+
+    // ---- GMRES solver of the regular QEq (solver.cu) ----
+    double *gmV = nullptr;     // [restart + 1][N + 1] Arnoldi basis
+    double *gmW = nullptr;     // [2][N + 1] work vectors
+    double *gmZ = nullptr;     // [N + 1] preconditioned vector
+    double *gmDinv = nullptr;  // [N + 1] Jacobi inverse diagonal
+    double *gmH = nullptr;     // small device scratch
+    double *gmSol = nullptr;   // [N + 1] BO-MD solution [q; lambda]
+    int gm_restart = 0;
     double *energy4 = nullptr; // [4] energy parts of the last apply
+
+    // ---- CUDA graph of the shadow evaluation + second half kick (api.cu) ----
+    cudaGraph_t step_graph = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    const void *graph_key[14] = {};  // state / parameter / list pointers it was captured with
+    int graph_width = 0;
+    int64_t graph_launches = 0;      // this library's kernels inside the graph
+    bool use_graphs = true;
 
     // ---- tracing ----
     qeq::Profiler prof;
@@ -166,6 +195,8 @@ int nl_alloc(qeq_ctx *ctx);
 int nl_alloc_list(qeq_ctx *ctx, int width);
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s);
 int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr, int8_t *shift);
+int nl_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *coo_i, int32_t *coo_j, int8_t *coo_code,
+                  int64_t *n_pairs, cudaStream_t s);
 int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_disp2);
 void nl_free(qeq_ctx *ctx);
 
@@ -178,6 +209,12 @@ int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const dou
                        double *v, double *E, double *F, double *energy4, bool need_field,
                        cudaStream_t s);
 
+// ---- explicit k-vector Ewald (ewald.cu) ----
+int ewald_alloc(qeq_ctx *ctx);
+void ewald_free(qeq_ctx *ctx);
+int ewald_recip_and_combine(qeq_ctx *ctx, const double *q, const double *sigma, double *v,
+                            double *E, double *F, bool need_field, cudaStream_t s);
+
 // ---- reductions (coulomb.cu) ----
 // Sum nslots partial tables of kRedBlocks entries each, starting at part, into out[0..nslots).
 void launch_finalize(const double *part, int nslots, double *out, cudaStream_t s);
@@ -189,6 +226,16 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
 int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
 int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
                   cudaStream_t s);
+
+// ---- regular QEq / BO-MD (solver.cu) ----
+int solver_alloc(qeq_ctx *ctx, int restart);
+void solver_free(qeq_ctx *ctx);
+int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *u,
+                const double *sigma, double *z, double tol, int max_iter, int restart,
+                bool final_check, qeq_solve_info *info, cudaStream_t s);
+int bomd_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
+int bomd_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
+                  int max_iter, qeq_solve_info *info, cudaStream_t s);
 
 // ---- device helpers ----
 __device__ __forceinline__ double warp_sum(double v) {

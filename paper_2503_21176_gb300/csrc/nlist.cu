@@ -138,17 +138,21 @@ struct EmitArgs {
     int width;
 };
 
-__global__ void __launch_bounds__(kThreads)
-k_emit(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
-       const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
-       int32_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int c = cell_s[i];
-    const int cx = c / (a.ncy * a.ncz), cy = (c / a.ncz) % a.ncy, cz = c % a.ncz;
-    const double4_32a xi = xs64[i];
-    const float4 xf = xs32[i];
-    int count = 0;
+// Rows are written in 8 shells of equal volume (equal steps of d^2 / r_list^2), so
+// that the entries of a row go roughly from near to far.  Lanes that run the same
+// iteration then hold neighbours at similar distances, and the real-space kernel's
+// distance branches (cutoff test, Gaussian correction) agree across the warp.
+// Pass 0 counts each shell, pass 1 places the entries.
+constexpr int kShells = 8;
+
+template <bool PLACE>
+__device__ __forceinline__ void emit_sweep(const EmitArgs &a, int i, int cx, int cy, int cz,
+                                           const double4_32a &xi, const float4 &xf,
+                                           const double4_32a *__restrict__ xs64,
+                                           const float4 *__restrict__ xs32,
+                                           const int32_t *__restrict__ cell_start, int (&cnt)[kShells],
+                                           int32_t *__restrict__ nbr) {
+    const float inv_rl2 = (float)(kShells / a.rl2);
     for (int ox = -a.rx; ox <= a.rx; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
         const double shx = __dmul_rn((double)sx, a.Lx);
@@ -187,15 +191,64 @@ k_emit(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *__restric
                         keep = d2 < a.rl2;
                     }
                     if (keep) {
-                        if (count < a.width) nbr[(size_t)count * a.n + i] = j | code;
-                        ++count;
+                        const int shell = min(kShells - 1, max(0, (int)(d2f * inv_rl2)));
+                        if (PLACE) {
+                            const int slot = cnt[shell]++;
+                            if (slot < a.width) nbr[(size_t)slot * a.n + i] = j | code;
+                        } else {
+                            ++cnt[shell];
+                        }
                     }
                 }
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_emit(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
+       const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
+       int32_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int c = cell_s[i];
+    const int cx = c / (a.ncy * a.ncz), cy = (c / a.ncz) % a.ncy, cz = c % a.ncz;
+    const double4_32a xi = xs64[i];
+    const float4 xf = xs32[i];
+    int shell[kShells];
+#pragma unroll
+    for (int b = 0; b < kShells; ++b) shell[b] = 0;
+    emit_sweep<false>(a, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, shell, nbr);
+    // shell counts -> first slot of each shell
+    int count = 0;
+#pragma unroll
+    for (int b = 0; b < kShells; ++b) {
+        const int c_b = shell[b];
+        shell[b] = count;
+        count += c_b;
+    }
+    emit_sweep<true>(a, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, shell, nbr);
     cnt[i] = min(count, a.width);
     if (count > a.width) atomicMax(&flags[kFlagMaxRow], count);
+}
+
+// COO scatter: sorted row i with entries k < cnt[i] goes to slots offset[i] + k as
+// (original i, original j, image code), so the pair order is the list's.
+__global__ void k_coo_scatter(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ nbr,
+                              const int32_t *__restrict__ cnt, const int32_t *__restrict__ offset,
+                              int32_t *__restrict__ coo_i, int32_t *__restrict__ coo_j,
+                              int8_t *__restrict__ coo_code) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cnt[i];
+    const int base = offset[i];
+    const int ai = perm[i];
+    for (int k = 0; k < c; ++k) {
+        const int32_t e = nbr[(size_t)k * n + i];
+        coo_i[base + k] = ai;
+        coo_j[base + k] = perm[e & kIndexMask];
+        coo_code[base + k] = (int8_t)((uint32_t)e >> kIndexBits);
+    }
 }
 
 __global__ void k_max_disp2(int n, const double *__restrict__ R, const double *__restrict__ R0,
@@ -399,6 +452,36 @@ int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_d
         *max_disp2 = ctx->h_scal[kScMaxDisp2];
     }
     return QEQ_OK;
+}
+
+// Device COO copy of the current list: an exclusive scan of the row counts
+// (k_scan into a temporary buffer) gives each row's first slot.
+int nl_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *coo_i, int32_t *coo_j, int8_t *coo_code,
+                  int64_t *n_pairs, cudaStream_t s) {
+    const int n = (int)ctx->n;
+    int32_t *scan_out = nullptr;
+    int rc = dev_alloc(ctx, (void **)&scan_out, sizeof(int32_t) * (size_t)(n + 1) * 2);
+    if (rc) return rc;
+    k_scan<<<1, 1024, 0, s>>>(n, ctx->cnt, scan_out, scan_out + n + 1);
+    int32_t total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, scan_out + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    rc = cuda_check(ctx, e, "coo scan");
+    if (!rc) {
+        *n_pairs = total;
+        if (total > capacity) {
+            rc = set_error(ctx, QEQ_ERR_CAPACITY, "COO needs %d pairs, capacity is %lld", total,
+                           (long long)capacity);
+        } else {
+            k_coo_scatter<<<grid_for(n), kThreads, 0, s>>>(n, ctx->perm, ctx->nbr, ctx->cnt, scan_out,
+                                                          coo_i, coo_j, coo_code);
+            ctx->launches += 2;
+            rc = cuda_check(ctx, cudaGetLastError(), "coo scatter");
+        }
+    }
+    dev_free(ctx, scan_out);
+    if (!ctx->async_alloc) cudaDeviceSynchronize();
+    return rc;
 }
 
 int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr_out, int8_t *shift_out) {

@@ -35,6 +35,7 @@ constexpr int S_MU = 40;    // sum (Phi w) / u
 constexpr int S_DOT = 41;   // Gram-Schmidt dot
 constexpr int S_OM = 48;    // O (kMaxRank^2, row-major) then g = R^T f (kMaxRank)
 constexpr int S_KE = 120;   // kinetic energy
+constexpr int S_RES = 121;  // relative least-squares residual |R c - f| / |f| of the kernel update
 constexpr int S_SHORT = 126;  // short-range energy: intramolecular, Lennard-Jones
 
 __global__ void k_lambda_part(int n, const double *__restrict__ chi, const double *__restrict__ u,
@@ -243,6 +244,11 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
         x[c] = acc / A[c][c];
     }
     for (int a = 0; a < m; ++a) scal[S_OM + kMaxRank * kMaxRank + a] = x[a];
+    // |R c - f|^2 = |f|^2 - c . R^T f at the least-squares solution
+    double cg = 0.0;
+    for (int a = 0; a < m; ++a) cg += x[a] * sums[nO + a];
+    const double f2 = scal[S_CHG];
+    scal[S_RES] = f2 > 0.0 ? sqrt(fmax(f2 - cg, 0.0) / f2) : 0.0;
     const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
     const double e_short = scal[S_SHORT] + scal[S_SHORT + 1];
     energies[1] = scal[S_CHG + 1] + scal[S_CHG + 2] + scal[S_CHG + 3] - 0.5 * scal[S_CHG + 4] + e_short;
@@ -251,6 +257,24 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
     energies[5] = scal[S_CHG + 5];
     energies[6] = sqrt(scal[S_CHG]);
     energies[7] = (double)applies;
+}
+
+// partial of |R c - f|^2 for the current c (rank m): the least-squares residual of
+// the kernel update, computed directly (the normal-equation identity
+// |f|^2 - c.R^T f cancels catastrophically once the residual is small)
+__global__ void k_ls_residual(int n, int m, const double *__restrict__ Rb,
+                              const double *__restrict__ f, const double *__restrict__ scal,
+                              double *__restrict__ part) {
+    const double *c = scal + S_OM + kMaxRank * kMaxRank;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double r = -f[i];
+        for (int a = 0; a < m; ++a) r += c[a] * Rb[(size_t)a * n + i];
+        acc += r * r;
+    }
+    double vals[1] = {acc};
+    block_sum<1>(vals);
+    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
 }
 
 __global__ void k_kf(int n, int m, const double *__restrict__ Wb, const double *__restrict__ scal,
@@ -425,6 +449,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
                             true, s);
     if (rc) return rc;
     // 4. forces, w_1, r_1 (and, when m > 1, the start of w_2)
+    const bool adaptive = ctx->p.krylov_tol > 0.0;
     prof_begin(ctx, kPhShadow, s);
     k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
                                        ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr,
@@ -438,8 +463,38 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         ctx->launches++;
     }
     prof_end(ctx, s);
+    // normal equations, m x m solve and energies for rank k; with a tolerance, the
+    // host reads the least-squares residual and stops adding vectors when it is met
+    auto solve_rank = [&](int k, bool *done) -> int {
+        const int nO = k * (k + 1) / 2;
+        prof_begin(ctx, kPhShadow, s);
+        k_normal_part<<<G, kThreads, 0, s>>>(n, k, ctx->Rb, ctx->fvec, part);
+        k_normal_solve<<<1, kThreads, 0, s>>>(k, ctx->p.q_tot, k + 1, part, scal, st->energies);
+        ctx->launches += 2;
+        prof_end(ctx, s);
+        (void)nO;
+        *done = true;
+        if (!adaptive || k == m) return QEQ_OK;
+        k_ls_residual<<<G, kThreads, 0, s>>>(n, k, ctx->Rb, ctx->fvec, scal, part);
+        fin(1, S_RES);
+        double hv[2] = {0.0, 0.0};  // |R c - f|^2 and |f|^2
+        cudaError_t e = cudaMemcpyAsync(&hv[0], scal + S_RES, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hv[1], scal + S_CHG, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int rc2 = cuda_check(ctx, e, "krylov residual");
+        if (rc2) return rc2;
+        *done = !(hv[0] > ctx->p.krylov_tol * ctx->p.krylov_tol * hv[1]);
+        return QEQ_OK;
+    };
+    int m_used = 1;
+    bool done = !adaptive && m > 1 ? false : true;
+    if (adaptive) {
+        rc = solve_rank(1, &done);
+        if (rc) return rc;
+    }
     // 5. further Krylov vectors: w_k starts as r_{k-1} with <w_0, w_k> already reduced
-    for (int k = 1; k < m; ++k) {
+    for (int k = 1; k < m && !(adaptive && done); ++k) {
         double *Wk = ctx->Wb + (size_t)k * n;
         prof_begin(ctx, kPhShadow, s);
         // modified Gram-Schmidt: Wk -= <w_j, Wk> w_j for j = 0..k-1, then normalise
@@ -468,13 +523,21 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
             ctx->launches++;
         }
         prof_end(ctx, s);
+        m_used = k + 1;
+        if (adaptive) {
+            rc = solve_rank(m_used, &done);
+            if (rc) return rc;
+        }
     }
-    // 6. normal equations, m x m solve and energies in one block; Kf = W c
+    if (!adaptive) {
+        m_used = m;
+        rc = solve_rank(m, &done);
+        if (rc) return rc;
+    }
+    // 6. Kf = W c
     prof_begin(ctx, kPhShadow, s);
-    k_normal_part<<<G, kThreads, 0, s>>>(n, m, ctx->Rb, ctx->fvec, part);
-    k_normal_solve<<<1, kThreads, 0, s>>>(m, ctx->p.q_tot, m + 1, part, scal, st->energies);
-    k_kf<<<G, kThreads, 0, s>>>(n, m, ctx->Wb, scal, st->Kf);
-    ctx->launches += 3;
+    k_kf<<<G, kThreads, 0, s>>>(n, m_used, ctx->Wb, scal, st->Kf);
+    ctx->launches++;
     prof_end(ctx, s);
     return cuda_check(ctx, cudaGetLastError(), "shadow evaluate launch");
 }

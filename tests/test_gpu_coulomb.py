@@ -170,3 +170,29 @@ def test_full_size_sampled_rows(precision):
     else:
         assert rel_max(v[rows], v_ref) < 1e-5
         assert np.sqrt(np.mean((E[rows] - E_ref) ** 2) / np.mean(E_ref ** 2)) < 1e-4
+
+
+@pytest.mark.parametrize("n_mol,box_scale", [(216, 1.0), (60, 1.0), (30, 1.3)])
+def test_fp64_explicit_ewald_matches_oracle(n_mol, box_scale):
+    """The GPU explicit k-vector sum (recip = ewald) against the oracle's k-sum, same k_cut."""
+    qg = cuda_or_skip()
+    w = water_box(n_mol, seed=n_mol)
+    w.box *= box_scale
+    q = random_neutral_charges(w.n_atoms, seed=3, scale=0.4)
+    k_cut = ewald.kspace_cutoff(0.34, 1e-14)
+    p = qg.make_params(w.n_atoms, w.box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(8, 8, 8),
+                       recip="ewald", k_cut=k_cut)
+    s = qg.System(p)
+    R = dev_tensor(w.R)
+    s.neighbor_build(R)
+    v, E, F, en = s.apply(R, dev_tensor(q), dev_tensor(w.sigma))
+    o = ewald.coulomb_apply(w.R, q, w.sigma, w.box, 0.34, 8.0, recip="ewald", k_cut=k_cut,
+                            gaussian_self=True)
+    assert rel_max(v.cpu().numpy(), o["v"]) < TOL64
+    assert rel_max(F.cpu().numpy(), o["F"]) < TOL64
+    e = en.cpu().numpy()
+    assert abs(e[2] - o["energy_recip"]) < TOL64 * abs(o["energy_recip"])
+    assert abs(e[0] - o["energy"]) < TOL64 * (abs(o["energy_real"]) + abs(o["energy_recip"]))
+    s.close()
+    with pytest.raises(qg.QeqError):
+        qg.System(qg.make_params(w.n_atoms, w.box, recip="ewald", precision="fp32_mixed"))

@@ -83,3 +83,26 @@ def test_nonfinite_position_is_reported():
         s.neighbor_build(dev_tensor(R))
     assert ei.value.code == -7
     s.close()
+
+
+def test_coo_export_equals_pair_set():
+    """The COO format (Sec. 3.1) holds exactly the brute-force pair set."""
+    qg = cuda_or_skip()
+    w = water_box(300, seed=19)
+    r_cut, skin = 7.0, 1.0
+    s = qg.System(qg.make_params(w.n_atoms, w.box, r_cut=r_cut, skin=skin, mesh=(8, 8, 8)))
+    s.neighbor_build(dev_tensor(w.R))
+    pi, pj, code = qg._lib.qeq_neighbor_export_coo(s.ctx)
+    pi, pj, code = pi.cpu().numpy(), pj.cpu().numpy(), code.cpu().numpy().astype(np.int32)
+    off, j, sh = neighbors.brute_force_pairs(w.R, w.box, r_cut + skin)
+    want = set()
+    for i in range(w.n_atoms):
+        for k in range(off[i], off[i + 1]):
+            want.add((i, int(j[k]), int((sh[k, 0] + 2) * 25 + (sh[k, 1] + 2) * 5 + (sh[k, 2] + 2))))
+    got = set(zip(pi.tolist(), pj.tolist(), code.tolist()))
+    assert len(got) == len(pi) == len(want)
+    assert got == want
+    with pytest.raises(qg.QeqError) as ei:
+        qg._lib.qeq_neighbor_export_coo(s.ctx, capacity=10)
+    assert ei.value.code == -8
+    s.close()

@@ -183,3 +183,44 @@ def test_shadow_md_conserves_charge_and_energy():
     es = np.array(es)
     # 20 fs of NVE: the shadow total energy drifts by far less than the kinetic energy (~1 eV)
     assert np.abs(es - e0).max() < 2e-4
+
+
+def test_gmres_converges_to_dense_solution(system):
+    """The oracle GMRES of the bordered system reaches the dense LU solution; looser
+    tolerances stop earlier with the requested true relative residual."""
+    w, Phi = system
+    qd, lam = qeq.qeq_dense_solve(Phi, w.chi, w.eta)
+    prev_iters = -1
+    for tol in (1e-1, 1e-3, 1e-6, 1e-12):
+        q, l, info = qeq.qeq_gmres(lambda x: Phi @ x, w.chi, w.eta, np.zeros(w.n_atoms), tol)
+        assert info["rel_residual"] <= tol
+        assert info["iterations"] >= prev_iters
+        prev_iters = info["iterations"]
+        A_res = np.concatenate([(Phi + np.diag(w.eta)) @ q + l + w.chi, [q.sum()]])
+        b = np.concatenate([-w.chi, [0.0]])
+        assert abs(np.linalg.norm(A_res) / np.linalg.norm(b) - info["rel_residual"]) < 1e-10
+    assert np.abs(q - qd).max() < 1e-10 and abs(l - lam) < 1e-9
+    assert info["iterations"] <= w.n_atoms + 1
+
+
+def test_gmres_warm_start_is_cheaper(system):
+    """A guess near the solution (as in MD, from the previous step) converges in fewer iterations."""
+    w, Phi = system
+    qd, lam = qeq.qeq_dense_solve(Phi, w.chi, w.eta)
+    rng = np.random.default_rng(4)
+    guess = qd + 1e-3 * rng.standard_normal(w.n_atoms)
+    _, _, cold = qeq.qeq_gmres(lambda x: Phi @ x, w.chi, w.eta, np.zeros(w.n_atoms), 1e-6)
+    _, _, warm = qeq.qeq_gmres(lambda x: Phi @ x, w.chi, w.eta, guess, 1e-6, lam0=lam)
+    assert warm["iterations"] < cold["iterations"]
+
+
+def test_adaptive_krylov_stops_at_tolerance(system):
+    w, Phi = system
+    n = random_neutral_charges(w.n_atoms, seed=3, scale=0.3)
+    q, _ = qeq.shadow_charges(Phi @ n, w.chi, w.eta)
+    f = q - n
+    for tol in (0.5, 0.1, 1e-3):
+        Kf, extra = qeq.krylov_kernel(f, Phi @ f, lambda x: Phi @ x, w.eta, 8, tol)
+        N = w.n_atoms
+        J = np.stack([qeq.jacobian_apply(Phi[:, j], np.eye(N)[j], w.eta) for j in range(N)], axis=1)
+        assert np.linalg.norm(J @ Kf - f) <= tol * np.linalg.norm(f) * (1 + 1e-9) or extra == 7
