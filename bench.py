@@ -211,35 +211,46 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
         for _ in range(warmup):
             md.step(1, stream)
         torch.cuda.synchronize(device)
-        c0 = qg.qeq_get_counters(sysm.ctx)
-        if profile:
-            qg.qeq_profile_enable(sysm.ctx, True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        e_tot = []
-        sampler = ClockSampler(device.index)
-        with sampler:
+
+        def timed(n):
+            c0 = qg.qeq_get_counters(sysm.ctx)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(n)]
             torch.cuda.synchronize(device)
-            for k in range(steps):
+            for k in range(n):
                 flush.zero_()
                 ev[k][0].record(stream)
                 md.step(1, stream)
                 ev[k][1].record(stream)
             torch.cuda.synchronize(device)
-        sms = [a.elapsed_time(b) for a, b in ev]
-        prof = qg.qeq_profile_read(sysm.ctx) if profile else None
+            c1 = qg.qeq_get_counters(sysm.ctx)
+            return [a.elapsed_time(b) for a, b in ev], [b - a for a, b in zip(c0, c1)]
+
+        # timed region: the production path (each step's evaluation replayed from a
+        # CUDA graph), clocks sampled throughout
+        sampler = ClockSampler(device.index)
+        with sampler:
+            sms, dc = timed(steps)
+        # profiled pass over as many further steps: per-phase device time from CUDA
+        # events on the launching stream (the profiler records events between
+        # phases, so these steps run un-graphed)
+        prof, prof_ms = None, None
         if profile:
+            qg.qeq_profile_enable(sysm.ctx, True)
+            pms, _ = timed(steps)
+            prof = qg.qeq_profile_read(sysm.ctx)
             qg.qeq_profile_enable(sysm.ctx, False)
-        c1 = qg.qeq_get_counters(sysm.ctx)
+            prof_ms = statistics.mean(pms)
         e = md.energy_dict()
         res.update({
             "steps_per_s": round(1e3 / statistics.mean(sms), 3),
             "ms_per_step": round(statistics.mean(sms), 4),
             "step_ms_p50": round(pct(sms, 50), 4),
             "step_ms_p99": round(pct(sms, 99), 4),
-            "gpu_launches": c1[0] - c0[0],
-            "neighbor_rebuilds": c1[1] - c0[1],
-            "applies_in_timed_steps": c1[2] - c0[2],
+            "gpu_launches": dc[0],
+            "neighbor_rebuilds": dc[1],
+            "applies_in_timed_steps": dc[2],
+            "ms_per_step_profiled_pass": None if prof_ms is None else round(prof_ms, 4),
             "clocks": sampler.summary(),
             "final_energy_eV": {k: round(v, 6) for k, v in e.items()},
         })
@@ -307,6 +318,95 @@ def roofline(res, precision, n_pairs_rc, peaks):
     out.update({"avg_launch_ms": round(avg_ms, 4), "launches": cnt, "share_of_profiled": round(share, 4),
                 "phases_ms": {k: round(v[0], 3) for k, v in prof.items()}})
     return out
+
+
+def precision_report(s32, s64, w, device, stream):
+    """FP32-mixed against FP64 on the same charges and positions.  The FP64 apply
+    matches the oracle to 1e-10, so these are the errors against the oracle."""
+    import torch
+
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    R, sig = t(w.R), t(w.sigma)
+    q = t(np.random.default_rng(7).standard_normal(w.n_atoms) * 0.3)
+    out = {}
+    for name, sysm in (("fp32", s32), ("fp64", s64)):
+        sysm.neighbor_build(R, stream)
+        with torch.cuda.stream(stream):
+            v, E, F, en = sysm.apply(R, q, sig, stream=stream)
+            stream.synchronize()
+        out[name] = (v.cpu().numpy().copy(), F.cpu().numpy().copy(), en.cpu().numpy().copy())
+    v32, F32, e32 = out["fp32"]
+    v64, F64, e64 = out["fp64"]
+    return {
+        "rel_energy": float(abs(e32[0] - e64[0]) / abs(e64[0])),
+        "rel_potential_max": float(np.abs(v32 - v64).max() / np.abs(v64).max()),
+        "rel_potential_rms": float(np.sqrt(np.mean((v32 - v64) ** 2) / np.mean(v64 ** 2))),
+        "rel_rms_force": float(np.sqrt(np.mean((F32 - F64) ** 2) / np.mean(F64 ** 2))),
+        "charges": "N(0, 0.3 e), seed 7",
+    }
+
+
+def drift_bench(args):
+    """Total-energy drift per atom of the shadow step, 300k-atom water with the flexible-water
+    V_short stand-in, in both precisions; one line of JSON."""
+    import torch
+
+    import paper_2503_21176_gb300 as qg
+    from workloads import water_box
+
+    qg.load()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = water_box(args.n_mol, seed=SEED)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    rows = {}
+    for prec, steps in (("fp32_mixed", args.drift_steps), ("fp64", args.drift_steps_fp64)):
+        K = MESH if args.n_mol == N_MOL else 4 * math.ceil(float(w.box[0]) / 4.0)
+        p = qg.make_params(w.n_atoms, w.box, alpha=ALPHA, r_cut=R_CUT, skin=SKIN,
+                           mesh=(K, K, K), order=ORDER, precision=prec, krylov_rank=RANK,
+                           dissipation_k=KD, dt=DT, short_range=qg.QEQ_SHORT_WATER)
+        sysm = qg.System(p)
+        with torch.cuda.stream(stream):
+            md = qg.ShadowMD(sysm, t(w.chi), t(w.eta), t(w.sigma), t(w.mass), t(w.R),
+                             t(initial_state(w, SEED + 1)),
+                             torch.zeros(w.n_atoms, dtype=torch.float64, device=dev))
+            md.init(stream)
+            md.n_hist.copy_(md.q.reshape(1, -1).expand_as(md.n_hist))
+            md.init(stream)
+            e = [md.energies[2].item()]
+            qmax = [float(md.q.abs().max().item())]
+            every = max(1, steps // 100)
+            diverged = None
+            t0 = time.perf_counter()
+            for k in range(steps):
+                try:
+                    md.step(1, stream)
+                except qg.QeqError as exc:  # non-finite positions: the run blew up
+                    diverged = {"step": k, "error": str(exc)}
+                    break
+                if (k + 1) % every == 0:
+                    e.append(md.energies[2].item())
+                    qmax.append(float(md.q.abs().max().item()))
+                    if not math.isfinite(e[-1]):
+                        diverged = {"step": k, "error": "total energy not finite"}
+                        break
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+            done = k + 1 if diverged is None else k
+        sysm.close()
+        E = np.array([x for x in e if math.isfinite(x)])
+        x = np.arange(len(E)) * every * DT
+        slope = float(np.polyfit(x, E, 1)[0]) if len(E) > 2 else 0.0
+        rows[prec] = {"atoms": w.n_atoms, "mesh": K, "steps": done, "fs": done * DT,
+                      "drift_per_atom_eV": float((E[-1] - E[0]) / w.n_atoms),
+                      "slope_per_atom_eV_per_ps": slope * 1000.0 / w.n_atoms,
+                      "std_per_atom_eV": float(np.std(E) / w.n_atoms),
+                      "max_abs_q": float(max(qmax)), "ms_per_step": 1e3 * wall / max(1, done),
+                      "diverged": diverged,
+                      "energy_trace_eV": [round(float(v), 4) for v in e[:: max(1, len(e) // 20)]]}
+    print(json.dumps({"experiment": "shadow XL-BOMD total-energy drift, water + V_short stand-in",
+                      "config": workload_config(args.n_mol), "rows": rows}))
 
 
 def count_pairs_within_rc(sysm, w):
@@ -385,6 +485,10 @@ def ours(args):
 
     head = results["fp32_mixed"]
     sysm, md = head["_sys"], head["_md"]
+    precision = None
+    if "fp64" in results:
+        precision = precision_report(results["fp32_mixed"]["_sys"], results["fp64"]["_sys"], w,
+                                     device, stream)
     # directed pairs inside r_c at the initial positions (fresh list) for the roofline
     sysm.neighbor_build(torch.as_tensor(w.R, dtype=torch.float64, device=device), stream)
     n_pairs = count_pairs_within_rc(sysm, w)
@@ -423,6 +527,7 @@ def ours(args):
             "fp32_mixed": {k: v for k, v in head.items() if not k.startswith("_")},
             "fp64": fp64,
             "directed_pairs_within_rc": n_pairs,
+            "precision_fp32_vs_fp64": precision,
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": head["gpu_launches"],
@@ -657,6 +762,9 @@ def main():
     ap.add_argument("--table1", action="store_true",
                     help="run the shadow vs regular QEq-MD tolerance sweep instead")
     ap.add_argument("--table1-steps", type=int, default=2000)
+    ap.add_argument("--drift", action="store_true", help="run the energy-drift measurement instead")
+    ap.add_argument("--drift-steps", type=int, default=10000)
+    ap.add_argument("--drift-steps-fp64", type=int, default=2000)
     ap.add_argument("--crossover", action="store_true",
                     help="time the explicit Ewald k-sum against PME over system sizes instead")
     ap.add_argument("--serve-requests", type=int, default=512)
@@ -671,6 +779,9 @@ def main():
         return
     if args.crossover:
         crossover_bench(args)
+        return
+    if args.drift:
+        drift_bench(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -80,10 +80,17 @@ struct RealArgs {
 #ifndef QEQ_TPR
 #define QEQ_TPR 4
 #endif
+// Resident blocks per SM asked of the FP32 real-space kernel (register cap
+// 65536 / (threads x blocks)) and its block size.  Five 256-thread blocks leave
+// 48 registers a thread, enough for the software-pipelined loop without spills.
 #ifndef QEQ_REAL_MIN_BLOCKS
-#define QEQ_REAL_MIN_BLOCKS 6
+#define QEQ_REAL_MIN_BLOCKS 5
+#endif
+#ifndef QEQ_REAL_THREADS
+#define QEQ_REAL_THREADS 256
 #endif
 constexpr int kTPR = QEQ_TPR;
+constexpr int kRealThreads = QEQ_REAL_THREADS;
 
 // FP64 erfc by a piecewise polynomial: [0, kErfcXMax) is cut into kErfcPieces
 // equal pieces.  On each piece erfc is the degree-(kErfcCoef - 1) polynomial in
@@ -223,12 +230,57 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
+// One FP32 pair term: the erfc(alpha r) / r potential minus the Gaussian-charge
+// correction erfc(r / gamma_ij) / r, and (FIELD) the field coefficient, added to
+// the running chunk sums.
+template <bool FIELD>
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, float sj, float si2,
+                                       float al, float rc2, float tspa, float tsp, float &vf,
+                                       float &exf, float &eyf, float &ezf) {
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < rc2) {
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
+        const float x1 = al * r;
+        const float e1 = __expf(-x1 * x1);
+        float f = erfc_as7126(x1, e1) * ir;
+        float dfr = 0.f;
+        if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
+        const float g2 = fmaf(sj, sj, si2);
+        // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
+        // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
+        if (r * r < 25.f * g2) {
+            const float ig = rsqrtf(g2);
+            const float x2 = r * ig;
+            const float e2 = __expf(-x2 * x2);
+            const float fg = erfc_as7126(x2, e2) * ir;
+            f -= fg;
+            if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
+        }
+        vf = fmaf(qj, f, vf);
+        if (FIELD) {
+            const float gq = qj * dfr * ir;
+            exf = fmaf(gq, dx, exf);
+            eyf = fmaf(gq, dy, eyf);
+            ezf = fmaf(gq, dz, ezf);
+        }
+    }
+}
+
+// Software pipelining of the real-space loop: the list entry two iterations
+// ahead and x_j, sigma_j one iteration ahead are loaded before the current
+// pair is evaluated, so the DRAM latency of the streamed list and the L1/L2
+// latency of the gathered positions overlap the pair arithmetic.
+#ifndef QEQ_REAL_PIPE
+#define QEQ_REAL_PIPE 1
+#endif
+
 // FP32 pair math with one exp per erfc shared with the field term, image shifts
 // from a shared table, kTPR lanes per row, FP32 chunk sums of 32 entries
 // accumulated with compensation, and an FP32 shuffle combine of the lanes (no
 // FP64 arithmetic before the final scaling).
 template <bool FIELD>
-__global__ void __launch_bounds__(kThreads, QEQ_REAL_MIN_BLOCKS)
+__global__ void __launch_bounds__(kRealThreads, QEQ_REAL_MIN_BLOCKS)
 k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const float4 *__restrict__ xq, const float *__restrict__ sg, double *__restrict__ v_s,
          double *__restrict__ E_s) {
@@ -251,45 +303,39 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
         const float tspa = (float)(kTwoOverSqrtPi * a.alpha);
         const float tsp = (float)kTwoOverSqrtPi;
         const int32_t *col = nbr + i;
+        const size_t step = (size_t)kTPR * a.n;
         int chunk = 0;
+#if QEQ_REAL_PIPE
+        // e0: entry of the current iteration, e1: the next one; x_j, sigma_j of
+        // the current entry are in xj, sj.  Entries past the row end read as 0
+        // (atom 0, image code 0: a valid address, never evaluated).
+        const int32_t *pk = col + (size_t)sub * a.n;
+        int32_t e0 = sub < c ? __ldg(pk) : 0;
+        int32_t e1 = sub + kTPR < c ? __ldg(pk + step) : 0;
+        float4 xj = __ldg(xq + (e0 & kIndexMask));
+        float sj = __ldg(sg + (e0 & kIndexMask));
+        for (int k = sub; k < c; k += kTPR) {
+            const int32_t e = e0;
+            const float4 xc = xj;
+            const float sc = sj;
+            e0 = e1;
+            pk += step;
+            e1 = k + 2 * kTPR < c ? __ldg(pk + step) : 0;
+            xj = __ldg(xq + (e0 & kIndexMask));
+            sj = __ldg(sg + (e0 & kIndexMask));
+            const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
+            pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w, sc,
+                          si2, al, rc2, tspa, tsp, vf, exf, eyf, ezf);
+#else
 #pragma unroll 2
         for (int k = sub; k < c; k += kTPR) {
             const int32_t e = __ldg(col + (size_t)k * a.n);
             const int j = e & kIndexMask;
             const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
-            const float4 xj = __ldg(xq + j);
-            const float dx = (xj.x - xi.x) + sh.x;
-            const float dy = (xj.y - xi.y) + sh.y;
-            const float dz = (xj.z - xi.z) + sh.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 < rc2) {
-                const float ir = rsqrtf(r2);
-                const float r = r2 * ir;
-                const float x1 = al * r;
-                const float e1 = __expf(-x1 * x1);
-                float f = erfc_as7126(x1, e1) * ir;
-                float dfr = 0.f;
-                if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
-                const float sj = __ldg(sg + j);
-                const float g2 = fmaf(sj, sj, si2);
-                // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
-                // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
-                if (r * r < 25.f * g2) {
-                    const float ig = rsqrtf(g2);
-                    const float x2 = r * ig;
-                    const float e2 = __expf(-x2 * x2);
-                    const float fg = erfc_as7126(x2, e2) * ir;
-                    f -= fg;
-                    if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
-                }
-                vf = fmaf(xj.w, f, vf);
-                if (FIELD) {
-                    const float gq = xj.w * dfr * ir;
-                    exf = fmaf(gq, dx, exf);
-                    eyf = fmaf(gq, dy, eyf);
-                    ezf = fmaf(gq, dz, ezf);
-                }
-            }
+            const float4 xc = __ldg(xq + j);
+            pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w,
+                          __ldg(sg + j), si2, al, rc2, tspa, tsp, vf, exf, eyf, ezf);
+#endif
             if (++chunk == 32) {
                 chunk = 0;
                 kahan_add(sv, cv, vf);
@@ -371,6 +417,12 @@ __device__ __forceinline__ void bspline(T w, T (&M)[P], T (&dM)[P]) {
     }
 }
 
+// Vector reduction of two adjacent floats (sm_90+): one L2 atomic for 8 bytes.
+// p must be 8-byte aligned.
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
 __device__ __forceinline__ int wrap_index(int b, int K) {
     int r = b % K;
     return r < 0 ? r + K : r;
@@ -393,6 +445,9 @@ k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__re
     int iz[P];
 #pragma unroll
     for (int c = 0; c < P; ++c) iz[c] = wrap_index(b.z - c, K2);
+    // the P z-points base - P + 1 .. base are contiguous unless they wrap
+    const int z0 = b.z - (P - 1);
+    const bool contiguous = z0 >= 0 && b.z < K2;
 #pragma unroll
     for (int a = 0; a < P; ++a) {
         const int ix = wrap_index(b.x - a, K0);
@@ -402,6 +457,21 @@ k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__re
             const int iy = wrap_index(b.y - bb, K1);
             const T qab = qa * My[bb];
             T *row = mesh + ((size_t)ix * K1 + iy) * K2;
+            if constexpr (std::is_same<T, float>::value && P == 4) {
+                if (contiguous) {
+                    // two 8-byte vector reductions per row (one when the start is odd)
+                    float *p0 = row + z0;
+                    if ((((size_t)ix * K1 + iy) * K2 + z0 & 1) == 0) {
+                        red_add_v2(p0, qab * Mz[3], qab * Mz[2]);
+                        red_add_v2(p0 + 2, qab * Mz[1], qab * Mz[0]);
+                    } else {
+                        atomicAdd(p0, qab * Mz[3]);
+                        red_add_v2(p0 + 1, qab * Mz[2], qab * Mz[1]);
+                        atomicAdd(p0 + 3, qab * Mz[0]);
+                    }
+                    continue;
+                }
+            }
 #pragma unroll
             for (int c = 0; c < P; ++c) atomicAdd(row + iz[c], qab * Mz[c]);
         }
@@ -674,10 +744,10 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                                                              (double *)sg, ctx->erfc_tab64, ctx->v_s, ctx->E_s);
     } else {
         if (need_field)
-            k_real32<true><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
+            k_real32<true><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
                                                             (float *)sg, ctx->v_s, ctx->E_s);
         else
-            k_real32<false><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
+            k_real32<false><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
                                                              (float *)sg, ctx->v_s, ctx->E_s);
     }
 
