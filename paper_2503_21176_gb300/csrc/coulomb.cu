@@ -70,6 +70,10 @@ struct RealArgs {
     double alpha;
     double rc2;
     double ke;
+    // FP32 copies for k_real32, rounded once on the host: a double-to-float
+    // conversion in the kernel runs on the FP64 pipe (1/64 rate on GB300), and
+    // under register pressure the compiler re-derives such values inside the loop.
+    float alpha_f, rc2_f, tspa_f, Lx_f, Ly_f, Lz_f;
 };
 
 // Threads per neighbour row.  TPR consecutive lanes share one row: lane s takes
@@ -286,9 +290,8 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
          double *__restrict__ E_s) {
     __shared__ float4 shift_tab[128];
     for (int t = threadIdx.x; t < 125; t += blockDim.x)
-        shift_tab[t] = make_float4((float)(t / 25 - 2) * (float)a.Lx,
-                                   (float)((t / 5) % 5 - 2) * (float)a.Ly,
-                                   (float)(t % 5 - 2) * (float)a.Lz, 0.f);
+        shift_tab[t] = make_float4((float)(t / 25 - 2) * a.Lx_f, (float)((t / 5) % 5 - 2) * a.Ly_f,
+                                   (float)(t % 5 - 2) * a.Lz_f, 0.f);
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / kTPR, sub = t % kTPR;
@@ -299,8 +302,7 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
         const float si = sg[i];
         const float si2 = si * si;
         const int c = cnt[i];
-        const float al = (float)a.alpha, rc2 = (float)a.rc2;
-        const float tspa = (float)(kTwoOverSqrtPi * a.alpha);
+        const float al = a.alpha_f, rc2 = a.rc2_f, tspa = a.tspa_f;
         const float tsp = (float)kTwoOverSqrtPi;
         const int32_t *col = nbr + i;
         const size_t step = (size_t)kTPR * a.n;
@@ -734,6 +736,12 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.alpha = p.alpha;
     ra.rc2 = p.r_cut * p.r_cut;
     ra.ke = p.k_e;
+    ra.alpha_f = (float)ra.alpha;
+    ra.rc2_f = (float)ra.rc2;
+    ra.tspa_f = (float)(kTwoOverSqrtPi * ra.alpha);
+    ra.Lx_f = (float)ra.Lx;
+    ra.Ly_f = (float)ra.Ly;
+    ra.Lz_f = (float)ra.Lz;
     prof_begin(ctx, kPhReal, s);
     if (f64) {
         if (need_field)

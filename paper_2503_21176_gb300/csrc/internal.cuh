@@ -17,10 +17,14 @@
 namespace qeq {
 
 constexpr int kThreads = 256;
-// Fixed reduction grid: 8 blocks per SM on a 152-SM GB300.  Grid-stride kernels
-// that reduce write one partial per block into a [slot][kRedBlocks] table, and a
-// one-block finalize sums each slot in a fixed order (deterministic results).
-constexpr int kRedBlocks = 1216;
+// Fixed reduction grid: QEQ_RED_BLOCKS blocks (a multiple of the 152 SMs of a
+// GB300).  Grid-stride kernels that reduce write one partial per block into a
+// [slot][kRedBlocks] table, and a one-block finalize sums each slot in a fixed
+// order (deterministic results).
+#ifndef QEQ_RED_BLOCKS
+#define QEQ_RED_BLOCKS 304
+#endif
+constexpr int kRedBlocks = QEQ_RED_BLOCKS;
 constexpr int kMaxRank = 8;
 // Reduction slots: the largest user is the GMRES multi-dot (restart <= 64
 // vectors plus the norm); the Krylov normal equations need

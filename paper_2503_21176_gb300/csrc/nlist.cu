@@ -127,11 +127,28 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start,
     }
 }
 
+// Cells per list radius.  With cells r_list / 2 wide the emit visits 125 cells
+// holding about 1.16 (4 pi / 3)^-1 x 125 / 8 = 4.6x the atoms of the list ball,
+// against 27 cells and 6.4x with cells r_list wide.
+#ifndef QEQ_NL_CELL_DIV
+#define QEQ_NL_CELL_DIV 2
+#endif
+constexpr int kCellDiv = QEQ_NL_CELL_DIV;
+
+// s L for an image index s in [-2, 2]: exact in FP64 (a multiple of L by 0, 1 or
+// 2), selected without an FP64 multiply.
+__device__ __forceinline__ double image_shift(int s, double L, double L2) {
+    const double a = (s == 1 || s == -1) ? L : L2;
+    const double m = s < 0 ? -a : a;
+    return s == 0 ? 0.0 : m;
+}
+
 struct EmitArgs {
     int n;
     int ncx, ncy, ncz;
     int rx, ry, rz;
     double Lx, Ly, Lz;
+    double L2x, L2y, L2z;  // 2 L, exact
     float Lfx, Lfy, Lfz;
     double rl2;
     float lo, hi;
@@ -155,15 +172,15 @@ __device__ __forceinline__ void emit_sweep(const EmitArgs &a, int i, int cx, int
     const float inv_rl2 = (float)(kShells / a.rl2);
     for (int ox = -a.rx; ox <= a.rx; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
-        const double shx = __dmul_rn((double)sx, a.Lx);
+        const double shx = image_shift(sx, a.Lx, a.L2x);
         const float shxf = (float)sx * a.Lfx;
         for (int oy = -a.ry; oy <= a.ry; ++oy) {
             const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
-            const double shy = __dmul_rn((double)sy, a.Ly);
+            const double shy = image_shift(sy, a.Ly, a.L2y);
             const float shyf = (float)sy * a.Lfy;
             for (int oz = -a.rz; oz <= a.rz; ++oz) {
                 const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
-                const double shz = __dmul_rn((double)sz, a.Lz);
+                const double shz = image_shift(sz, a.Lz, a.L2z);
                 const float shzf = (float)sz * a.Lfz;
                 const int cn = (wx * a.ncy + wy) * a.ncz + wz;
                 const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
@@ -297,9 +314,10 @@ int nl_configure(qeq_ctx *ctx) {
     for (int d = 0; d < 3; ++d) {
         const double L = p.box[d];
         lmax = std::max(lmax, L);
-        // cells at least r_list wide (with a relative margin so that rounding in
-        // the cell index cannot move an atom by more than one cell)
-        int nc = (int)std::floor(L / (ctx->rl * (1.0 + 1e-9)));
+        // cells at least r_list / kCellDiv wide (with a relative margin so that
+        // rounding in the cell index cannot move an atom by more than one cell);
+        // the emit then visits (2 reach + 1)^3 cells
+        int nc = (int)std::floor(L / (ctx->rl / kCellDiv * (1.0 + 1e-9)));
         if (nc < 1) nc = 1;
         if (nc > 1024) nc = 1024;
         ctx->nc[d] = nc;
@@ -383,6 +401,7 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     a.ncx = ctx->nc[0]; a.ncy = ctx->nc[1]; a.ncz = ctx->nc[2];
     a.rx = ctx->reach[0]; a.ry = ctx->reach[1]; a.rz = ctx->reach[2];
     a.Lx = ctx->p.box[0]; a.Ly = ctx->p.box[1]; a.Lz = ctx->p.box[2];
+    a.L2x = 2.0 * a.Lx; a.L2y = 2.0 * a.Ly; a.L2z = 2.0 * a.Lz;
     a.Lfx = (float)a.Lx; a.Lfy = (float)a.Ly; a.Lfz = (float)a.Lz;
     a.rl2 = ctx->rl2;
     a.lo = ctx->rl2f_lo;
@@ -613,15 +632,15 @@ k_emit_original(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *
     int count = 0;
     for (int ox = -a.rx; ox <= a.rx; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
-        const double shx = __dmul_rn((double)sx, a.Lx);
+        const double shx = image_shift(sx, a.Lx, a.L2x);
         const float shxf = (float)sx * a.Lfx;
         for (int oy = -a.ry; oy <= a.ry; ++oy) {
             const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
-            const double shy = __dmul_rn((double)sy, a.Ly);
+            const double shy = image_shift(sy, a.Ly, a.L2y);
             const float shyf = (float)sy * a.Lfy;
             for (int oz = -a.rz; oz <= a.rz; ++oz) {
                 const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
-                const double shz = __dmul_rn((double)sz, a.Lz);
+                const double shz = image_shift(sz, a.Lz, a.L2z);
                 const float shzf = (float)sz * a.Lfz;
                 const int cn = (wx * a.ncy + wy) * a.ncz + wz;
                 const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
@@ -722,6 +741,7 @@ QEQ_API int qeq_neighbor_build_noalloc(const double *R, int64_t n_atoms, const d
     a.ncx = nc[0]; a.ncy = nc[1]; a.ncz = nc[2];
     a.rx = reach[0]; a.ry = reach[1]; a.rz = reach[2];
     a.Lx = box[0]; a.Ly = box[1]; a.Lz = box[2];
+    a.L2x = 2.0 * a.Lx; a.L2y = 2.0 * a.Ly; a.L2z = 2.0 * a.Lz;
     a.Lfx = (float)box[0]; a.Lfy = (float)box[1]; a.Lfz = (float)box[2];
     a.rl2 = r_list * r_list;
     const double margin = 4e-5 * r_list * (lmax + r_list) + 1e-6;
