@@ -43,8 +43,15 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
                             const double *__restrict__ w, const double *__restrict__ q,
                             const double *__restrict__ sigma, double sK0, double sK1, double sK2,
                             typename V4<T>::type *__restrict__ xq, T *__restrict__ sg,
-                            int4 *__restrict__ sbase, typename V4<T>::type *__restrict__ sfrac) {
+                            int4 *__restrict__ sbase, typename V4<T>::type *__restrict__ sfrac,
+                            int32_t *__restrict__ smax_bits) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (smax_bits) {
+        // max |sigma| as float bits (non-negative floats order like their bits)
+        int32_t b = i < n ? __float_as_int(fabsf((float)sigma[perm[i]])) : 0;
+        b = __reduce_max_sync(0xffffffffu, b);
+        if ((threadIdx.x & 31) == 0 && b > 0) atomicMax(smax_bits, b);
+    }
     if (i >= n) return;
     const int a = perm[i];
     const double x = R[3 * (size_t)a] + w[3 * (size_t)a];
@@ -93,8 +100,13 @@ struct RealArgs {
 #ifndef QEQ_REAL_THREADS
 #define QEQ_REAL_THREADS 256
 #endif
+// Read sigma_j only for pairs inside the row's Gaussian-correction bound.
+#ifndef QEQ_REAL_LAZY_SIGMA
+#define QEQ_REAL_LAZY_SIGMA 1
+#endif
 constexpr int kTPR = QEQ_TPR;
 constexpr int kRealThreads = QEQ_REAL_THREADS;
+constexpr bool kRealLazySigma = QEQ_REAL_LAZY_SIGMA != 0;
 
 // FP64 erfc by a piecewise polynomial: [0, kErfcXMax) is cut into kErfcPieces
 // equal pieces.  On each piece erfc is the degree-(kErfcCoef - 1) polynomial in
@@ -236,9 +248,12 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 
 // One FP32 pair term: the erfc(alpha r) / r potential minus the Gaussian-charge
 // correction erfc(r / gamma_ij) / r, and (FIELD) the field coefficient, added to
-// the running chunk sums.
+// the running chunk sums.  sigma_j is read only when r^2 is below the row's
+// bound gpre = 25 (sigma_i^2 + max sigma^2) (x 1.0001 against rounding), the
+// only pairs where the correction can be kept.
 template <bool FIELD>
-__device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, float sj, float si2,
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
+                                       const float *__restrict__ sgj, float si2, float gpre,
                                        float al, float rc2, float tspa, float tsp, float &vf,
                                        float &exf, float &eyf, float &ezf) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -250,16 +265,19 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, f
         float f = erfc_as7126(x1, e1) * ir;
         float dfr = 0.f;
         if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
-        const float g2 = fmaf(sj, sj, si2);
-        // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
-        // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
-        if (r * r < 25.f * g2) {
-            const float ig = rsqrtf(g2);
-            const float x2 = r * ig;
-            const float e2 = __expf(-x2 * x2);
-            const float fg = erfc_as7126(x2, e2) * ir;
-            f -= fg;
-            if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
+        if (r2 < gpre) {
+            const float sj = __ldg(sgj);
+            const float g2 = fmaf(sj, sj, si2);
+            // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
+            // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
+            if (r * r < 25.f * g2) {
+                const float ig = rsqrtf(g2);
+                const float x2 = r * ig;
+                const float e2 = __expf(-x2 * x2);
+                const float fg = erfc_as7126(x2, e2) * ir;
+                f -= fg;
+                if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
+            }
         }
         vf = fmaf(qj, f, vf);
         if (FIELD) {
@@ -271,22 +289,26 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, f
     }
 }
 
-// Software pipelining of the real-space loop: the list entry two iterations
-// ahead and x_j, sigma_j one iteration ahead are loaded before the current
-// pair is evaluated, so the DRAM latency of the streamed list and the L1/L2
-// latency of the gathered positions overlap the pair arithmetic.
-#ifndef QEQ_REAL_PIPE
-#define QEQ_REAL_PIPE 1
+// Loop shape of the FP32 real-space kernel.  Each lane walks its entries k =
+// sub, sub + kTPR, ... in chunks of 32 (FP32 sums, flushed with compensation).
+// The list entry two iterations ahead and x_j one iteration ahead are loaded
+// before the current pair is evaluated (software pipelining), so the DRAM
+// latency of the streamed list and the L1/L2 latency of the gathered
+// positions overlap the pair arithmetic.
+#ifndef QEQ_REAL_UNROLL
+#define QEQ_REAL_UNROLL 1
 #endif
 
 // FP32 pair math with one exp per erfc shared with the field term, image shifts
 // from a shared table, kTPR lanes per row, FP32 chunk sums of 32 entries
 // accumulated with compensation, and an FP32 shuffle combine of the lanes (no
-// FP64 arithmetic before the final scaling).
+// FP64 arithmetic before the final scaling).  smax_bits holds the float bits of
+// max |sigma| over the atoms (written by the gather of the same apply).
 template <bool FIELD>
 __global__ void __launch_bounds__(kRealThreads, QEQ_REAL_MIN_BLOCKS)
 k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
-         const float4 *__restrict__ xq, const float *__restrict__ sg, double *__restrict__ v_s,
+         const float4 *__restrict__ xq, const float *__restrict__ sg,
+         const int32_t *__restrict__ smax_bits, double *__restrict__ v_s,
          double *__restrict__ E_s) {
     __shared__ float4 shift_tab[128];
     for (int t = threadIdx.x; t < 125; t += blockDim.x)
@@ -296,65 +318,50 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / kTPR, sub = t % kTPR;
     float sv = 0.f, cv = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-    float vf = 0.f, exf = 0.f, eyf = 0.f, ezf = 0.f;
     if (i < a.n) {
         const float4 xi = xq[i];
         const float si = sg[i];
         const float si2 = si * si;
+        float gpre = 3.4e38f;  // every pair checks sigma_j when max |sigma| is unknown
+        if (kRealLazySigma) {
+            const float smax = __int_as_float(__ldg(smax_bits));
+            gpre = 25.0001f * fmaf(smax, smax, si2);
+        }
         const int c = cnt[i];
         const float al = a.alpha_f, rc2 = a.rc2_f, tspa = a.tspa_f;
         const float tsp = (float)kTwoOverSqrtPi;
-        const int32_t *col = nbr + i;
         const size_t step = (size_t)kTPR * a.n;
-        int chunk = 0;
-#if QEQ_REAL_PIPE
-        // e0: entry of the current iteration, e1: the next one; x_j, sigma_j of
-        // the current entry are in xj, sj.  Entries past the row end read as 0
-        // (atom 0, image code 0: a valid address, never evaluated).
-        const int32_t *pk = col + (size_t)sub * a.n;
+        // e0: entry of the current iteration, e1: the next one; x_j of the current
+        // entry is in xj.  Entries past the row end read as 0 (atom 0, image code 0:
+        // a valid address, never evaluated).
+        const int32_t *pk = nbr + i + (size_t)sub * a.n;
         int32_t e0 = sub < c ? __ldg(pk) : 0;
         int32_t e1 = sub + kTPR < c ? __ldg(pk + step) : 0;
         float4 xj = __ldg(xq + (e0 & kIndexMask));
-        float sj = __ldg(sg + (e0 & kIndexMask));
-        for (int k = sub; k < c; k += kTPR) {
-            const int32_t e = e0;
-            const float4 xc = xj;
-            const float sc = sj;
-            e0 = e1;
-            pk += step;
-            e1 = k + 2 * kTPR < c ? __ldg(pk + step) : 0;
-            xj = __ldg(xq + (e0 & kIndexMask));
-            sj = __ldg(sg + (e0 & kIndexMask));
-            const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
-            pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w, sc,
-                          si2, al, rc2, tspa, tsp, vf, exf, eyf, ezf);
-#else
-#pragma unroll 2
-        for (int k = sub; k < c; k += kTPR) {
-            const int32_t e = __ldg(col + (size_t)k * a.n);
-            const int j = e & kIndexMask;
-            const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
-            const float4 xc = __ldg(xq + j);
-            pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w,
-                          __ldg(sg + j), si2, al, rc2, tspa, tsp, vf, exf, eyf, ezf);
-#endif
-            if (++chunk == 32) {
-                chunk = 0;
-                kahan_add(sv, cv, vf);
-                vf = 0.f;
-                if (FIELD) {
-                    kahan_add(sx, cx, exf);
-                    kahan_add(sy, cy, eyf);
-                    kahan_add(sz, cz, ezf);
-                    exf = eyf = ezf = 0.f;
-                }
+        const int n_it = c > sub ? (c - sub + kTPR - 1) / kTPR : 0;
+        for (int base = 0; base < n_it; base += 32) {
+            const int lim = min(32, n_it - base);
+            float vf = 0.f, exf = 0.f, eyf = 0.f, ezf = 0.f;
+            QEQ_UNROLL(QEQ_REAL_UNROLL)
+            for (int it = 0; it < lim; ++it) {
+                const int k = sub + (base + it) * kTPR;
+                const int32_t e = e0;
+                const float4 xc = xj;
+                e0 = e1;
+                pk += step;
+                e1 = k + 2 * kTPR < c ? __ldg(pk + step) : 0;
+                xj = __ldg(xq + (e0 & kIndexMask));
+                const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
+                pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w,
+                              sg + (e & kIndexMask), si2, gpre, al, rc2, tspa, tsp, vf, exf, eyf,
+                              ezf);
             }
-        }
-        kahan_add(sv, cv, vf);
-        if (FIELD) {
-            kahan_add(sx, cx, exf);
-            kahan_add(sy, cy, eyf);
-            kahan_add(sz, cz, ezf);
+            kahan_add(sv, cv, vf);
+            if (FIELD) {
+                kahan_add(sx, cx, exf);
+                kahan_add(sy, cy, eyf);
+                kahan_add(sz, cz, ezf);
+            }
         }
     }
     float tv = sv - cv, tx = sx - cx, ty = sy - cy, tz = sz - cz;
@@ -724,9 +731,11 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     const qeq_params &p = ctx->p;
     ctx->applies++;
     prof_begin(ctx, kPhGatherIn, s);
+    int32_t *smax_bits = (!f64 && kRealLazySigma) ? ctx->d_flags + kFlagSigmaMax : nullptr;
+    if (smax_bits) cudaMemsetAsync(smax_bits, 0, sizeof(int32_t), s);
     k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
         n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
-        ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac);
+        ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac, smax_bits);
     prof_end(ctx, s);
     ctx->launches++;
 
@@ -752,11 +761,13 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                                                              (double *)sg, ctx->erfc_tab64, ctx->v_s, ctx->E_s);
     } else {
         if (need_field)
-            k_real32<true><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
-                                                            (float *)sg, ctx->v_s, ctx->E_s);
+            k_real32<true><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(
+                ra, ctx->nbr, ctx->cnt, (float4 *)xq, (float *)sg, ctx->d_flags + kFlagSigmaMax, ctx->v_s,
+                ctx->E_s);
         else
-            k_real32<false><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (float4 *)xq,
-                                                             (float *)sg, ctx->v_s, ctx->E_s);
+            k_real32<false><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(
+                ra, ctx->nbr, ctx->cnt, (float4 *)xq, (float *)sg, ctx->d_flags + kFlagSigmaMax, ctx->v_s,
+                ctx->E_s);
     }
 
     prof_end(ctx, s);

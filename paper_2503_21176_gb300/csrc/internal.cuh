@@ -14,6 +14,11 @@
 
 #define QEQ_API extern "C" __attribute__((visibility("default")))
 
+// #pragma unroll with a macro argument (loop-shape tunables)
+#define QEQ_PRAGMA_(x) _Pragma(#x)
+#define QEQ_UNROLL_(n) QEQ_PRAGMA_(unroll n)
+#define QEQ_UNROLL(n) QEQ_UNROLL_(n)
+
 namespace qeq {
 
 constexpr int kThreads = 256;
@@ -45,7 +50,8 @@ constexpr double kSqrtTwoOverPi = 0.79788456080286535588;
 constexpr double kPi = 3.14159265358979323846;
 
 // Device-side status words (int32).
-enum Flag { kFlagMaxRow = 0, kFlagNonFinite = 1, kNumFlags = 4 };
+// kFlagSigmaMax: float bits of max |sigma| of the last FP32 apply's inputs.
+enum Flag { kFlagMaxRow = 0, kFlagNonFinite = 1, kFlagSigmaMax = 2, kNumFlags = 4 };
 
 // Device scalar table (double).  Slot 4 holds the last max displacement^2;
 // shadow.cu uses slots 32..127 for its reductions.

@@ -63,31 +63,72 @@ __global__ void k_wrap_bin(int n, const double *__restrict__ R, double Lx, doubl
     atomicAdd(&cell_count[cell], 1);
 }
 
-// Single-block exclusive scan of ncell ints (any size: each thread scans a chunk).
-__global__ void k_scan(int64_t ncell, const int32_t *__restrict__ count, int32_t *__restrict__ start,
-                       int32_t *__restrict__ fill) {
-    __shared__ int32_t sh[1024];
-    const int t = threadIdx.x;
-    const int64_t chunk = (ncell + blockDim.x - 1) / blockDim.x;
-    const int64_t b = t * chunk, e = min(ncell, b + chunk);
-    int32_t s = 0;
-    for (int64_t k = b; k < e; ++k) s += count[k];
-    sh[t] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the per-thread sums
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        int32_t add = t >= off ? sh[t - off] : 0;
+// Single-block exclusive scan of ncell ints (any size), launched with kScanThreads
+// threads.  Tiles of kScanTile counts are loaded coalesced into shared memory;
+// each thread scans kScanPer consecutive counts, a warp-shuffle scan of the
+// thread sums and one of the warp sums give the offsets, and the tile is
+// written back coalesced with the running carry.  Also zeroes fill.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(int64_t ncell, const int32_t *__restrict__ count, int32_t *__restrict__ start,
+       int32_t *__restrict__ fill) {
+    // stride kScanPer + 1 per thread keeps the per-thread reads conflict-free
+    __shared__ int32_t tile[kScanThreads * (kScanPer + 1)];
+    __shared__ int32_t warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int32_t carry = 0;
+    for (int64_t base = 0; base < ncell; base += kScanTile) {
+        for (int k = t; k < kScanTile; k += kScanThreads) {
+            const int64_t g = base + k;
+            tile[(k / kScanPer) * (kScanPer + 1) + k % kScanPer] = g < ncell ? count[g] : 0;
+        }
         __syncthreads();
-        sh[t] += add;
+        int32_t v[kScanPer];
+        int32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            v[j] = tile[t * (kScanPer + 1) + j];
+            s += v[j];
+        }
+        int32_t x = s;  // inclusive scan of the thread sums within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t w = warp_sum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        int32_t run = carry + (wid > 0 ? warp_sum[wid - 1] : 0) + (x - s);
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            tile[t * (kScanPer + 1) + j] = run;
+            run += v[j];
+        }
+        carry += warp_sum[31];
+        __syncthreads();
+        for (int k = t; k < kScanTile; k += kScanThreads) {
+            const int64_t g = base + k;
+            if (g < ncell) {
+                start[g] = tile[(k / kScanPer) * (kScanPer + 1) + k % kScanPer];
+                fill[g] = 0;
+            }
+        }
         __syncthreads();
     }
-    int32_t run = sh[t] - s;
-    for (int64_t k = b; k < e; ++k) {
-        start[k] = run;
-        fill[k] = 0;
-        run += count[k];
-    }
-    if (t == blockDim.x - 1) start[ncell] = sh[t];
+    if (t == 0) start[ncell] = carry;
 }
 
 __global__ void k_scatter(int n, const int32_t *__restrict__ cell_of,
@@ -134,6 +175,10 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start,
 #define QEQ_NL_CELL_DIV 2
 #endif
 constexpr int kCellDiv = QEQ_NL_CELL_DIV;
+// Unroll of the candidate loop of the emit (independent candidate loads in flight).
+#ifndef QEQ_NL_UNROLL
+#define QEQ_NL_UNROLL 1
+#endif
 
 // s L for an image index s in [-2, 2]: exact in FP64 (a multiple of L by 0, 1 or
 // 2), selected without an FP64 multiply.
@@ -186,6 +231,7 @@ __device__ __forceinline__ void emit_sweep(const EmitArgs &a, int i, int cx, int
                 const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
                 const int32_t code = ((sx + 2) * 25 + (sy + 2) * 5 + (sz + 2)) << kIndexBits;
                 const int jb = cell_start[cn], je = cell_start[cn + 1];
+                QEQ_UNROLL(QEQ_NL_UNROLL)
                 for (int j = jb; j < je; ++j) {
                     if (self_img && j == i) continue;
                     const float4 xj = xs32[j];
@@ -421,7 +467,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
         n, R, ctx->p.box[0], ctx->p.box[1], ctx->p.box[2], ctx->cw[0], ctx->cw[1], ctx->cw[2],
         ctx->nc[0], ctx->nc[1], ctx->nc[2], ctx->cell_of, ctx->cell_count, ctx->wrap_off,
         ctx->R_build, ctx->d_flags);
-    k_scan<<<1, 1024, 0, s>>>(ctx->ncell, ctx->cell_count, ctx->cell_start, ctx->cell_fill);
+    k_scan<<<1, kScanThreads, 0, s>>>(ctx->ncell, ctx->cell_count, ctx->cell_start, ctx->cell_fill);
     k_scatter<<<grid_for(n), kThreads, 0, s>>>(n, ctx->cell_of, ctx->cell_start, ctx->cell_fill,
                                                ctx->tmp_list);
     k_cell_sort<<<grid_for(ctx->ncell * 32), kThreads, 0, s>>>(
@@ -481,7 +527,7 @@ int nl_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *coo_i, int32_t *coo_j
     int32_t *scan_out = nullptr;
     int rc = dev_alloc(ctx, (void **)&scan_out, sizeof(int32_t) * (size_t)(n + 1) * 2);
     if (rc) return rc;
-    k_scan<<<1, 1024, 0, s>>>(n, ctx->cnt, scan_out, scan_out + n + 1);
+    k_scan<<<1, kScanThreads, 0, s>>>(n, ctx->cnt, scan_out, scan_out + n + 1);
     int32_t total = 0;
     cudaError_t e = cudaMemcpyAsync(&total, scan_out + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -730,7 +776,7 @@ QEQ_API int qeq_neighbor_build_noalloc(const double *R, int64_t n_atoms, const d
     k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(n, R, box[0], box[1], box[2], cw[0], cw[1], cw[2],
                                                 nc[0], nc[1], nc[2], S->cell_of, S->cell_count,
                                                 S->wrap_off, S->R_build, S->flags);
-    k_scan<<<1, 1024, 0, s>>>(ncell, S->cell_count, S->cell_start, S->cell_fill);
+    k_scan<<<1, kScanThreads, 0, s>>>(ncell, S->cell_count, S->cell_start, S->cell_fill);
     k_scatter<<<grid_for(n), kThreads, 0, s>>>(n, S->cell_of, S->cell_start, S->cell_fill,
                                                S->tmp_list);
     k_cell_sort<<<grid_for(ncell * 32), kThreads, 0, s>>>(ncell, S->cell_start, S->tmp_list, R,

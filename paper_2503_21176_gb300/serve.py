@@ -73,6 +73,7 @@ class Result:
     t_arrival: float
     t_admit: float
     t_done: float
+    phases_ms: dict = field(default_factory=dict)  # host wall time per stage of the request
 
     @property
     def latency_ms(self) -> float:
@@ -110,6 +111,7 @@ class Server:
     def _execute(self, req: Request, slot: int, t0: float, t_admit: float) -> Result:
         stream = self.streams[slot]
         dev = self.device
+        marks = [("start", time.perf_counter())]
         with torch.cuda.device(dev), torch.cuda.stream(stream):
             def up(a):
                 h = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
@@ -121,23 +123,32 @@ class Server:
             p = make_params(req.n_atoms, req.box, alpha=req.alpha, r_cut=req.r_cut, skin=req.skin,
                             mesh=req.mesh, order=req.order, precision=req.precision,
                             krylov_rank=req.rank, dissipation_k=req.k_d, dt=req.dt)
+            marks.append(("upload", time.perf_counter()))
             sysm = System(p, device=dev.index, stream=stream)
+            marks.append(("create", time.perf_counter()))
             try:
                 sysm.neighbor_build(R, stream)
+                marks.append(("neighbor_build", time.perf_counter()))
                 md = ShadowMD(sysm, chi, eta, sigma, mass, R, V,
                               torch.zeros(req.n_atoms, dtype=torch.float64, device=dev))
                 md.init(stream)
+                marks.append(("init", time.perf_counter()))
                 if req.kind == "md" and req.steps > 0:
                     md.step(req.steps, stream)
+                    marks.append(("steps", time.perf_counter()))
                 out = [t.to("cpu", non_blocking=True) for t in (md.q, md.F, md.R, md.energies)]
                 stream.synchronize()
+                marks.append(("download", time.perf_counter()))
             finally:
                 sysm.close()
+                marks.append(("close", time.perf_counter()))
         e = out[3].tolist()
         energies = {"kinetic": e[0], "shadow_potential": e[1], "total": e[2], "lambda": e[4],
                     "sum_q": e[5], "residual_norm": e[6], "applies": e[7]}
+        phases = {b[0]: 1e3 * (b[1] - a[1]) for a, b in zip(marks, marks[1:])}
         return Result(req.rid, req.kind, req.n_atoms, out[0].numpy(), out[1].numpy(),
-                      out[2].numpy(), energies, t0 + req.arrival, t_admit, time.perf_counter())
+                      out[2].numpy(), energies, t0 + req.arrival, t_admit, time.perf_counter(),
+                      phases)
 
     # -- dispatcher -----------------------------------------------------------------
     def serve(self, requests, realtime=True):
@@ -194,6 +205,10 @@ class Server:
             "max_concurrent": max_conc,
             "atoms_total": int(sum(r.n_atoms for r in res)),
             "md_steps_total": int(sum(r.steps for r in requests if r.kind == "md")),
+            "queue_ms_mean": round(float(np.mean([1e3 * (r.t_admit - r.t_arrival) for r in res])), 3),
+            "stage_ms_mean": {k: round(float(np.mean([r.phases_ms.get(k, 0.0) for r in res])), 3)
+                              for k in ("upload", "create", "neighbor_build", "init", "steps",
+                                        "download", "close")},
         }
         return res, stats
 
