@@ -267,31 +267,42 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
 
 
 def e2e_steps(qg, md, steps, stream, device):
-    """Same step through the C ABI with HOST buffers: pinned H2D of the state and
-    parameters, the step, and D2H of the results, all inside the timed region."""
+    """Same step through the C ABI with the state kept in HOST memory: every step
+    copies the whole MD state (R, V, F, K f, n history) and the per-atom parameters
+    from pinned host buffers to the device, runs the step, and copies the advanced
+    state, the charges and the energies back to pinned host buffers, all inside the
+    timed region.  Two host state buffers alternate (the results of step k are the
+    inputs of step k + 1), so the trajectory stays on the host with no host copy."""
     import torch
 
-    names_in = ["R", "V", "F", "Kf", "n_hist", "chi", "eta", "sigma", "mass"]
-    dev_in = {k: getattr(md, k) for k in names_in}
-    host_in = {k: v.cpu().pin_memory() for k, v in dev_in.items()}
-    names_out = ["R", "V", "F", "q", "energies"]
-    host_out = {k: torch.empty_like(getattr(md, k), device="cpu").pin_memory() for k in names_out}
-    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    names_state = ["R", "V", "F", "Kf", "n_hist"]
+    names_param = ["chi", "eta", "sigma", "mass"]
+    names_extra = ["q", "energies"]
+    dev = {k: getattr(md, k) for k in names_state + names_param + names_extra}
+    host = [{k: dev[k].cpu().pin_memory() for k in names_state},
+            {k: torch.empty_like(dev[k], device="cpu").pin_memory() for k in names_state}]
+    host_par = {k: dev[k].cpu().pin_memory() for k in names_param}
+    host_extra = {k: torch.empty_like(dev[k], device="cpu").pin_memory() for k in names_extra}
+    nbytes = lambda ts: sum(v.numel() * v.element_size() for v in ts)
+    h2d = nbytes(list(host[0].values()) + list(host_par.values()))
+    d2h = nbytes(list(host[1].values()) + list(host_extra.values()))
     with torch.cuda.stream(stream):
         torch.cuda.synchronize(device)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        for _ in range(steps):
-            for k in names_in:
-                dev_in[k].copy_(host_in[k], non_blocking=True)
+        for k in range(steps):
+            src, dst = host[k % 2], host[(k + 1) % 2]
+            for name in names_state:
+                dev[name].copy_(src[name], non_blocking=True)
+            for name in names_param:
+                dev[name].copy_(host_par[name], non_blocking=True)
             md.step(1, stream)
-            for k in names_out:
-                host_out[k].copy_(getattr(md, k), non_blocking=True)
-            stream.synchronize()
-            for k in ("R", "V", "F"):  # the caller keeps the advanced state on the host
-                host_in[k].copy_(host_out[k])
+            for name in names_state:
+                dst[name].copy_(dev[name], non_blocking=True)
+            for name in names_extra:
+                host_extra[name].copy_(dev[name], non_blocking=True)
+            stream.synchronize()  # the caller reads the step's results on the host
         t1.record(stream)
         torch.cuda.synchronize(device)
     ms = t0.elapsed_time(t1) / steps

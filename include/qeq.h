@@ -76,7 +76,7 @@ enum qeq_short_model {
  *  skin            neighbour-list skin.  The list radius is r_cut + skin, and
  *                  a rebuild is due when an atom has moved more than skin / 2
  *                  since the last build (Sec. 4.2.3).
- *  mesh            PME mesh K[3], each between 4 and 4096 (Alg. 2).
+ *  mesh            PME mesh K[3], each between 4 and 4096, K0 K1 K2 <= 2^31 - 1 (Alg. 2).
  *  order           B-spline points per dimension p, 4..8 (Alg. 2, step 1).
  *  precision       enum qeq_precision.
  *  k_e             Coulomb constant multiplying every term.

@@ -67,6 +67,8 @@ static int validate(const qeq_params *p) {
         if (p->mesh[d] < p->order)
             return set_error(nullptr, QEQ_ERR_INVALID, "mesh[%d] is smaller than the spline order", d);
     }
+    if ((int64_t)p->mesh[0] * p->mesh[1] * p->mesh[2] > INT32_MAX)
+        return set_error(nullptr, QEQ_ERR_UNSUPPORTED, "mesh of more than 2^31 - 1 points");
     if (!(p->alpha > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "alpha must be positive");
     if (!(p->r_cut > 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "r_cut must be positive");
     if (!(p->skin >= 0.0)) return set_error(nullptr, QEQ_ERR_INVALID, "skin must be >= 0");

@@ -80,7 +80,7 @@ struct RealArgs {
     // FP32 copies for k_real32, rounded once on the host: a double-to-float
     // conversion in the kernel runs on the FP64 pipe (1/64 rate on GB300), and
     // under register pressure the compiler re-derives such values inside the loop.
-    float alpha_f, rc2_f, tspa_f, Lx_f, Ly_f, Lz_f;
+    float alpha_f, rc2_f, tspa_f, c1_f, Lx_f, Ly_f, Lz_f;
 };
 
 // Threads per neighbour row.  TPR consecutive lanes share one row: lane s takes
@@ -92,10 +92,12 @@ struct RealArgs {
 #define QEQ_TPR 4
 #endif
 // Resident blocks per SM asked of the FP32 real-space kernel (register cap
-// 65536 / (threads x blocks)) and its block size.  Five 256-thread blocks leave
-// 48 registers a thread, enough for the software-pipelined loop without spills.
+// 65536 / (threads x blocks)) and its block size.  Six 256-thread blocks leave
+// 40 registers a thread; with the single-instruction SFU forms the loop fits
+// without spills, and the extra resident warps hide more gather latency (0.313
+// against 0.334 ms at five blocks, 300,000 atoms).
 #ifndef QEQ_REAL_MIN_BLOCKS
-#define QEQ_REAL_MIN_BLOCKS 5
+#define QEQ_REAL_MIN_BLOCKS 6
 #endif
 #ifndef QEQ_REAL_THREADS
 #define QEQ_REAL_THREADS 256
@@ -227,16 +229,44 @@ __global__ void k_erfc64(int64_t n, const double *__restrict__ tab, const double
 // erfc(x), x >= 0, in FP32 by Abramowitz & Stegun, Handbook of Mathematical
 // Functions, eq. 7.1.26 (Hastings' approximation):
 //   erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),  t = 1 / (1 + p x),
-// with an absolute error of at most 1.5e-7.  exp(-x^2) is an argument because the
-// field term needs the same exponential.
-__device__ __forceinline__ float erfc_as7126(float x, float ex2) {
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+// with an absolute error of at most 1.5e-7.  t and exp(-x^2) are arguments: the
+// field term needs the same exponential, and the callers form t themselves.
+constexpr float kAsP = 0.3275911f;
+__device__ __forceinline__ float erfc_as7126_t(float t, float ex2) {
     float p = fmaf(t, 1.061405429f, -1.453152027f);
     p = fmaf(t, p, 1.421413741f);
     p = fmaf(t, p, -0.284496736f);
     p = fmaf(t, p, 0.254829592f);
     return t * p * ex2;
 }
+
+// Single-instruction approximations of the special-function unit (PTX
+// rsqrt / rcp / ex2 .approx.ftz).  The arguments of the real-space kernel are
+// never subnormal (r^2 >= 0.1 A^2 between distinct atoms, 1 + p x >= 1, and the
+// exponents lie in [-37, 0]), so flushing subnormals changes no result.
+// exp(-y) is formed as 2^(-y log2 e) with log2 e folded into a kernel constant.
+constexpr float kLog2E = 1.4426950408889634f;
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// erfc(x) with exp(-x^2) passed in, x >= 0 (self-test and Gaussian-correction form).
+__device__ __forceinline__ float erfc_as7126(float x, float ex2) {
+    return erfc_as7126_t(rcp_ftz(fmaf(kAsP, x, 1.0f)), ex2);
+}
+__device__ __forceinline__ float exp_neg_sq(float x) { return ex2_ftz(-(x * x) * kLog2E); }
 
 // Kahan-compensated FP32 accumulation of a chunk sum.
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
@@ -248,21 +278,21 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 
 // One FP32 pair term: the erfc(alpha r) / r potential minus the Gaussian-charge
 // correction erfc(r / gamma_ij) / r, and (FIELD) the field coefficient, added to
-// the running chunk sums.  sigma_j is read only when r^2 is below the row's
-// bound gpre = 25 (sigma_i^2 + max sigma^2) (x 1.0001 against rounding), the
-// only pairs where the correction can be kept.
+// the running chunk sums.  The correction is evaluated only when r^2 is below
+// the row's bound gpre = 25 (sigma_i^2 + max sigma^2) (x 1.0001 against
+// rounding), the only pairs where it can be kept.  c1 = -alpha^2 log2 e, so
+// exp(-alpha^2 r^2) = 2^(c1 r^2).
 template <bool FIELD>
 __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
                                        const float *__restrict__ sgj, float si2, float gpre,
-                                       float al, float rc2, float tspa, float tsp, float &vf,
+                                       float pal, float c1, float rc2, float tspa, float &vf,
                                        float &exf, float &eyf, float &ezf) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 < rc2) {
-        const float ir = rsqrtf(r2);
+        const float ir = rsqrt_ftz(r2);
         const float r = r2 * ir;
-        const float x1 = al * r;
-        const float e1 = __expf(-x1 * x1);
-        float f = erfc_as7126(x1, e1) * ir;
+        const float e1 = ex2_ftz(r2 * c1);
+        float f = erfc_as7126_t(rcp_ftz(fmaf(pal, r, 1.0f)), e1) * ir;
         float dfr = 0.f;
         if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
         if (r2 < gpre) {
@@ -270,13 +300,13 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
             const float g2 = fmaf(sj, sj, si2);
             // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
             // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
-            if (r * r < 25.f * g2) {
-                const float ig = rsqrtf(g2);
+            if (r2 < 25.f * g2) {
+                const float ig = rsqrt_ftz(g2);
                 const float x2 = r * ig;
-                const float e2 = __expf(-x2 * x2);
+                const float e2 = exp_neg_sq(x2);
                 const float fg = erfc_as7126(x2, e2) * ir;
                 f -= fg;
-                if (FIELD) dfr += fmaf(tsp * ig, e2, fg) * ir;
+                if (FIELD) dfr += fmaf((float)kTwoOverSqrtPi * ig, e2, fg) * ir;
             }
         }
         vf = fmaf(qj, f, vf);
@@ -292,8 +322,8 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
 // Loop shape of the FP32 real-space kernel.  Each lane walks its entries k =
 // sub, sub + kTPR, ... in chunks of 32 (FP32 sums, flushed with compensation).
 // The list entry two iterations ahead and x_j one iteration ahead are loaded
-// before the current pair is evaluated (software pipelining), so the DRAM
-// latency of the streamed list and the L1/L2 latency of the gathered
+// before the current pair is evaluated (software pipelining), so the
+// DRAM latency of the streamed list and the L1/L2 latency of the gathered
 // positions overlap the pair arithmetic.
 #ifndef QEQ_REAL_UNROLL
 #define QEQ_REAL_UNROLL 1
@@ -328,8 +358,7 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
             gpre = 25.0001f * fmaf(smax, smax, si2);
         }
         const int c = cnt[i];
-        const float al = a.alpha_f, rc2 = a.rc2_f, tspa = a.tspa_f;
-        const float tsp = (float)kTwoOverSqrtPi;
+        const float pal = kAsP * a.alpha_f, c1 = a.c1_f, rc2 = a.rc2_f, tspa = a.tspa_f;
         const size_t step = (size_t)kTPR * a.n;
         // e0: entry of the current iteration, e1: the next one; x_j of the current
         // entry is in xj.  Entries past the row end read as 0 (atom 0, image code 0:
@@ -353,7 +382,7 @@ k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict_
                 xj = __ldg(xq + (e0 & kIndexMask));
                 const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
                 pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w,
-                              sg + (e & kIndexMask), si2, gpre, al, rc2, tspa, tsp, vf, exf, eyf,
+                              sg + (e & kIndexMask), si2, gpre, pal, c1, rc2, tspa, vf, exf, eyf,
                               ezf);
             }
             kahan_add(sv, cv, vf);
@@ -389,7 +418,7 @@ __global__ void k_erfc32(int64_t n, const float *__restrict__ x, float *__restri
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) {
         const float xv = x[t];
-        out[t] = erfc_as7126(xv, __expf(-xv * xv));
+        out[t] = erfc_as7126(xv, exp_neg_sq(xv));
     }
 }
 
@@ -489,24 +518,35 @@ k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__re
 
 // Q^ *= G on the half spectrum; partial sums of the mesh energy 1/2 sum_full G |Q^|^2,
 // where every half-spectrum point stands for itself and its mirror except on the
-// planes m3 = 0 and (K3 even) m3 = K3/2.
+// planes m3 = 0 and (K3 even) m3 = K3/2.  Grid-stride over the flat half spectrum;
+// m3 = t mod K2h is carried incrementally (stride_mod = stride mod K2h), so the
+// loop has no integer division.  FP32 mode sums each thread's terms in FP32 with
+// compensation; the block partials are FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_influence(int64_t nc, int K2h, int K2, typename C2<T>::type *__restrict__ meshc,
+k_influence(int nc, int K2h, int K2, int stride_mod, typename C2<T>::type *__restrict__ meshc,
             const T *__restrict__ G, double *__restrict__ part) {
-    double e = 0.0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int m3 = (int)(t % K2h);
-        const double wgt = (m3 == 0 || (2 * m3 == K2)) ? 0.5 : 1.0;
+    const int stride = gridDim.x * blockDim.x;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int m3 = t % K2h;
+    T s = T(0), comp = T(0);
+    for (; t < nc; t += stride) {
+        const T wgt = (m3 == 0 || 2 * m3 == K2) ? T(0.5) : T(1);
         auto z = meshc[t];
         const T g = G[t];
-        e += wgt * (double)g * ((double)z.x * (double)z.x + (double)z.y * (double)z.y);
+        const T term = wgt * g * (z.x * z.x + z.y * z.y);
+        if constexpr (std::is_same<T, float>::value) {
+            kahan_add(s, comp, term);
+        } else {
+            s += term;
+        }
         z.x *= g;
         z.y *= g;
         meshc[t] = z;
+        m3 += stride_mod;
+        if (m3 >= K2h) m3 -= K2h;
     }
-    double vals[1] = {e};
+    double vals[1] = {(double)s - (double)comp};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
 }
@@ -748,6 +788,7 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.alpha_f = (float)ra.alpha;
     ra.rc2_f = (float)ra.rc2;
     ra.tspa_f = (float)(kTwoOverSqrtPi * ra.alpha);
+    ra.c1_f = (float)(-ra.alpha * ra.alpha * 1.4426950408889634);
     ra.Lx_f = (float)ra.Lx;
     ra.Ly_f = (float)ra.Ly;
     ra.Lz_f = (float)ra.Lz;
@@ -799,9 +840,12 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ctx->fft_execs++;
     if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "forward FFT failed (%d)", (int)cr);
     prof_begin(ctx, kPhInfluence, s);
-    k_influence<T><<<kRedBlocks, kThreads, 0, s>>>(
-        ctx->meshc_n, ctx->K[2] / 2 + 1, ctx->K[2], (typename C2<T>::type *)ctx->meshc,
-        (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+    {
+        const int K2h = ctx->K[2] / 2 + 1;
+        k_influence<T><<<kRedBlocks, kThreads, 0, s>>>(
+            (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
+            (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+    }
     prof_end(ctx, s);
     ctx->launches++;
     prof_begin(ctx, kPhFftInv, s);
