@@ -274,7 +274,8 @@ QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
 // The evaluation and the second half kick of a fixed-rank shadow step contain
 // no host synchronisation, so they are captured once into a CUDA graph and
 // replayed.  The graph is re-captured when the state, parameter or neighbour-list
-// buffers it was recorded with change.  It is not used with a tolerance-driven
+// buffers it was recorded with change, or the launch capacities of the
+// real-space kernels (tile and brick size) grow.  It is not used with a tolerance-driven
 // Krylov rank (host reads), with the profiler on, or on the legacy default
 // stream (which cannot be captured).
 static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
@@ -287,8 +288,10 @@ static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_st
         return shadow_finish(ctx, prm, st, true, s);
     }
     const void *key[14] = {st->R, st->V, st->F, st->Kf, st->n_hist, st->q, st->energies,
-                           prm->chi, prm->eta, prm->sigma, prm->mass, ctx->nbr, nullptr, nullptr};
-    bool same = ctx->step_exec && ctx->graph_width == ctx->width;
+                           prm->chi, prm->eta, prm->sigma, prm->mass, ctx->nbr, ctx->tile_scratch,
+                           nullptr};
+    bool same = ctx->step_exec && ctx->graph_width == ctx->width &&
+                ctx->graph_tile == ctx->tile_cap && ctx->graph_rows == ctx->rows_cap;
     for (int k = 0; k < 14 && same; ++k) same = key[k] == ctx->graph_key[k];
     if (!same) {
         drop_graph(ctx);
@@ -311,6 +314,8 @@ static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_st
         }
         ctx->step_graph = g;
         ctx->graph_width = ctx->width;
+        ctx->graph_tile = ctx->tile_cap;
+        ctx->graph_rows = ctx->rows_cap;
         ctx->graph_launches = ctx->launches - l0;
         ctx->launches = l0;
         ctx->applies = a0;

@@ -80,35 +80,8 @@ struct RealArgs {
     // FP32 copies for k_real32, rounded once on the host: a double-to-float
     // conversion in the kernel runs on the FP64 pipe (1/64 rate on GB300), and
     // under register pressure the compiler re-derives such values inside the loop.
-    float alpha_f, rc2_f, tspa_f, c1_f, Lx_f, Ly_f, Lz_f;
+    float alpha_f, rc2_f, tspa_f, c1_f, pal_f, Lx_f, Ly_f, Lz_f;
 };
-
-// Threads per neighbour row.  TPR consecutive lanes share one row: lane s takes
-// entries s, s + TPR, ...  Their partial sums are combined with warp shuffles.
-// This multiplies the number of resident warps (one thread per row leaves most
-// of the 152 SMs' warp slots empty at 10^5 atoms) and shortens each thread's
-// chain of dependent loads.
-#ifndef QEQ_TPR
-#define QEQ_TPR 4
-#endif
-// Resident blocks per SM asked of the FP32 real-space kernel (register cap
-// 65536 / (threads x blocks)) and its block size.  Six 256-thread blocks leave
-// 40 registers a thread; with the single-instruction SFU forms the loop fits
-// without spills, and the extra resident warps hide more gather latency (0.313
-// against 0.334 ms at five blocks, 300,000 atoms).
-#ifndef QEQ_REAL_MIN_BLOCKS
-#define QEQ_REAL_MIN_BLOCKS 6
-#endif
-#ifndef QEQ_REAL_THREADS
-#define QEQ_REAL_THREADS 256
-#endif
-// Read sigma_j only for pairs inside the row's Gaussian-correction bound.
-#ifndef QEQ_REAL_LAZY_SIGMA
-#define QEQ_REAL_LAZY_SIGMA 1
-#endif
-constexpr int kTPR = QEQ_TPR;
-constexpr int kRealThreads = QEQ_REAL_THREADS;
-constexpr bool kRealLazySigma = QEQ_REAL_LAZY_SIGMA != 0;
 
 // FP64 erfc by a piecewise polynomial: [0, kErfcXMax) is cut into kErfcPieces
 // equal pieces.  On each piece erfc is the degree-(kErfcCoef - 1) polynomial in
@@ -141,76 +114,166 @@ __device__ __forceinline__ double erfc_pw(const double *__restrict__ tab, double
     return p;
 }
 
-template <bool FIELD>
-__global__ void __launch_bounds__(kThreads)
-k_real64(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
-         const double4_32a *__restrict__ xq, const double *__restrict__ sg,
-         const double *__restrict__ erfc_tab, double *__restrict__ v_s, double *__restrict__ E_s) {
-    __shared__ double shift_tab[125][3];
-    __shared__ double tab[kErfcPieces * kErfcCoef];
-    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
-        shift_tab[t][0] = (double)(t / 25 - 2) * a.Lx;
-        shift_tab[t][1] = (double)((t / 5) % 5 - 2) * a.Ly;
-        shift_tab[t][2] = (double)(t % 5 - 2) * a.Lz;
-    }
-    for (int t = threadIdx.x; t < kErfcPieces * kErfcCoef; t += blockDim.x) tab[t] = erfc_tab[t];
+// Lanes per neighbour row.  kTPR consecutive lanes share one row: lane s takes
+// the row's entries s, s + kTPR, ..., which the list stores next to each other
+// (kListGroup), and their partial sums are combined with warp shuffles.
+constexpr int kTPR = kListGroup;
+// One block per brick; its blockDim is kTPR x (largest brick, rounded to warps),
+// at most kRealMaxThreads.  Larger bricks take several passes.
+constexpr int kRealMaxThreads = 512;
+// Resident blocks per SM asked of the FP32 real-space kernel (register cap
+// 65536 / (kRealMaxThreads x blocks): three give 40 registers a thread, and
+// four 384-thread blocks of the 300,000-atom box fit; two blocks at 54
+// registers ran 0.29 ms against 0.24 ms).
+#ifndef QEQ_REAL_MIN_BLOCKS
+#define QEQ_REAL_MIN_BLOCKS 3
+#endif
+// Read sigma_j only for pairs inside the row's Gaussian-correction bound.
+#ifndef QEQ_REAL_LAZY_SIGMA
+#define QEQ_REAL_LAZY_SIGMA 1
+#endif
+constexpr bool kRealLazySigma = QEQ_REAL_LAZY_SIGMA != 0;
+
+// Tile bytes per atom (position and charge, sigma) and the dynamic shared
+// memory the kernels may take: 227 KB per block less their static tables.
+constexpr size_t kTile32Bytes = 20, kTile64Bytes = 40;
+constexpr size_t kSmemPerBlock = 232448;
+constexpr size_t kReal32SmemMax = kSmemPerBlock - 4096;
+constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096 - sizeof(double) * kErfcPieces * kErfcCoef;
+
+int real_block_threads(int max_rows) {
+    int t = (kTPR * std::max(1, max_rows) + 31) / 32 * 32;
+    return std::min(kRealMaxThreads, std::max(64, t));
+}
+
+// Stage the tile of brick blockIdx.x: warp 0 builds the tile table, then the
+// warps copy the tile bricks (positions shifted by their periodic image, and
+// sigma) into tile[] / tsg[].  Returns the tile size, or -1 when it exceeds cap
+// (the whole block then skips the brick and raises kFlagTileOverflow).
+template <typename T4, typename T>
+__device__ __forceinline__ int stage_tile(const BrickGeom &g, const int32_t *__restrict__ cell_start,
+                                          const T4 *__restrict__ xq, const T *__restrict__ sg,
+                                          T Lx, T Ly, T Lz, int cap, T4 *tile, T *tsg, int *t_start,
+                                          int *t_base, int *t_code, int *t_total,
+                                          int32_t *__restrict__ flags) {
+    if (threadIdx.x < 32) tile_table(g, blockIdx.x, cell_start, t_start, t_base, t_code, t_total);
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / kTPR, sub = t % kTPR;
+    const int total = *t_total;
+    if (total > cap) {
+        if (threadIdx.x == 0) atomicExch(&flags[kFlagTileOverflow], 1);
+        return -1;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int rb = warp; rb < g.T; rb += nw) {
+        const int st = t_start[rb], off = st + t_base[rb];
+        const int end = rb + 1 < g.T ? t_start[rb + 1] + t_base[rb + 1] : total;
+        const int code = t_code[rb];
+        const T sx = (T)(code / 25 - 2) * Lx, sy = (T)((code / 5) % 5 - 2) * Ly,
+                sz = (T)(code % 5 - 2) * Lz;
+        for (int k = lane; k < end - off; k += 32) {
+            T4 x = xq[st + k];
+            x.x += sx;
+            x.y += sy;
+            x.z += sz;
+            tile[off + k] = x;
+            tsg[off + k] = sg[st + k];
+        }
+    }
+    __syncthreads();
+    return total;
+}
+
+// Tile slots of the rows of the block's brick: the brick is the tile's center.
+__device__ __forceinline__ void home_rows(const BrickGeom &g, const int *t_start, const int *t_base,
+                                          int total, int &i0, int &off, int &nrows) {
+    i0 = t_start[g.center];
+    off = i0 + t_base[g.center];
+    const int end = g.center + 1 < g.T ? t_start[g.center + 1] + t_base[g.center + 1] : total;
+    nrows = end - off;
+}
+
+// FP64 real space, one block per brick: the tile (double4 positions with q,
+// sigma) and the erfc table in shared memory (GTILE: the tile in the block's
+// slice of a global scratch buffer instead), kTPR lanes per row.
+template <bool FIELD, bool GTILE>
+__global__ void __launch_bounds__(kRealMaxThreads, 2)
+k_real64(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
+         const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+         const double4_32a *__restrict__ xq, const double *__restrict__ sg,
+         const double *__restrict__ erfc_tab, int cap, unsigned char *__restrict__ gtile,
+         int32_t *__restrict__ flags, double *__restrict__ v_s, double *__restrict__ E_s) {
+    extern __shared__ __align__(32) unsigned char smem_raw[];
+    __shared__ double tab[kErfcPieces * kErfcCoef];
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
+    unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile64Bytes : smem_raw;
+    double4_32a *tile = (double4_32a *)base;
+    double *tsg = (double *)(base + (size_t)cap * 32);
+    for (int t = threadIdx.x; t < kErfcPieces * kErfcCoef; t += blockDim.x) tab[t] = erfc_tab[t];
+    const int total = stage_tile<double4_32a, double>(g, cell_start, xq, sg, a.Lx, a.Ly, a.Lz, cap,
+                                                     tile, tsg, t_start, t_base, t_code, &t_total,
+                                                     flags);
+    if (total < 0) return;
+    int i0, offc, nrows;
+    home_rows(g, t_start, t_base, total, i0, offc, nrows);
     const double al = a.alpha;
-    double v = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    if (i < a.n) {
-        const double4_32a xi = xq[i];
-        const double si2 = sg[i] * sg[i];
-        const int c = cnt[i];
-        for (int k = sub; k < c; k += kTPR) {
-            const int32_t e = nbr[(size_t)k * a.n + i];
-            const int j = e & kIndexMask;
-            const double *sh = shift_tab[(uint32_t)e >> kIndexBits];
-            const double4_32a xj = xq[j];
-            const double dx = (xj.x - xi.x) + sh[0];
-            const double dy = (xj.y - xi.y) + sh[1];
-            const double dz = (xj.z - xi.z) + sh[2];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (!(r2 < a.rc2)) continue;
-            const double ir = rsqrt(r2);
-            const double r = r2 * ir;
-            double d1;
-            double f = erfc_pw(tab, al * r, d1) * ir;
-            double dfr = (al * d1 - f) * ir;  // d/dr [erfc(alpha r) / r]
-            const double g2 = si2 + sg[j] * sg[j];
-            // Gaussian correction; the table is exactly 0 beyond r / gamma = kErfcXMax
-            if (r2 < kErfcXMax * kErfcXMax * g2) {
-                const double ig = rsqrt(g2);
-                double d2;
-                const double fg = erfc_pw(tab, r * ig, d2) * ir;
-                f -= fg;
-                dfr -= (ig * d2 - fg) * ir;
-            }
-            v += xj.w * f;
-            if (FIELD) {
-                const double gq = xj.w * dfr * ir;
-                ex += gq * dx;
-                ey += gq * dy;
-                ez += gq * dz;
+    const int rpp = blockDim.x / kTPR;
+    for (int r0 = 0; r0 < nrows; r0 += rpp) {
+        const int r = r0 + threadIdx.x / kTPR, sub = threadIdx.x % kTPR;
+        const bool act = r < nrows;
+        double v = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+        if (act) {
+            const int i = i0 + r;
+            const double4_32a xi = tile[offc + r];
+            const double si2 = tsg[offc + r] * tsg[offc + r];
+            const int c = cnt[i];
+            for (int k = sub; k < c; k += kTPR) {
+                const int e = nbr[list_index(k, i, a.n)];
+                const double4_32a xj = tile[e];
+                const double dx = xj.x - xi.x;
+                const double dy = xj.y - xi.y;
+                const double dz = xj.z - xi.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < a.rc2)) continue;
+                const double ir = rsqrt(r2);
+                const double rr = r2 * ir;
+                double d1;
+                double f = erfc_pw(tab, al * rr, d1) * ir;
+                double dfr = (al * d1 - f) * ir;  // d/dr [erfc(alpha r) / r]
+                const double g2 = si2 + tsg[e] * tsg[e];
+                // Gaussian correction; the table is exactly 0 beyond r / gamma = kErfcXMax
+                if (r2 < kErfcXMax * kErfcXMax * g2) {
+                    const double ig = rsqrt(g2);
+                    double d2;
+                    const double fg = erfc_pw(tab, rr * ig, d2) * ir;
+                    f -= fg;
+                    dfr -= (ig * d2 - fg) * ir;
+                }
+                v += xj.w * f;
+                if (FIELD) {
+                    const double gq = xj.w * dfr * ir;
+                    ex += gq * dx;
+                    ey += gq * dy;
+                    ez += gq * dz;
+                }
             }
         }
-    }
 #pragma unroll
-    for (int o = 1; o < kTPR; o <<= 1) {
-        v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (FIELD) {
-            ex += __shfl_xor_sync(0xffffffffu, ex, o);
-            ey += __shfl_xor_sync(0xffffffffu, ey, o);
-            ez += __shfl_xor_sync(0xffffffffu, ez, o);
+        for (int o = 1; o < kTPR; o <<= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (FIELD) {
+                ex += __shfl_xor_sync(0xffffffffu, ex, o);
+                ey += __shfl_xor_sync(0xffffffffu, ey, o);
+                ez += __shfl_xor_sync(0xffffffffu, ez, o);
+            }
         }
-    }
-    if (sub == 0 && i < a.n) {
-        v_s[i] = a.ke * v;
-        if (FIELD) {
-            E_s[3 * (size_t)i] = a.ke * ex;
-            E_s[3 * (size_t)i + 1] = a.ke * ey;
-            E_s[3 * (size_t)i + 2] = a.ke * ez;
+        if (act && sub == 0) {
+            const int i = i0 + r;
+            v_s[i] = a.ke * v;
+            if (FIELD) {
+                E_s[3 * (size_t)i] = a.ke * ex;
+                E_s[3 * (size_t)i + 1] = a.ke * ey;
+                E_s[3 * (size_t)i + 2] = a.ke * ez;
+            }
         }
     }
 }
@@ -280,13 +343,12 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 // correction erfc(r / gamma_ij) / r, and (FIELD) the field coefficient, added to
 // the running chunk sums.  The correction is evaluated only when r^2 is below
 // the row's bound gpre = 25 (sigma_i^2 + max sigma^2) (x 1.0001 against
-// rounding), the only pairs where it can be kept.  c1 = -alpha^2 log2 e, so
-// exp(-alpha^2 r^2) = 2^(c1 r^2).
+// rounding), the only pairs where it can be kept; sigma_j is read there only.
+// c1 = -alpha^2 log2 e, so exp(-alpha^2 r^2) = 2^(c1 r^2).
 template <bool FIELD>
-__device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
-                                       const float *__restrict__ sgj, float si2, float gpre,
-                                       float pal, float c1, float rc2, float tspa, float &vf,
-                                       float &exf, float &eyf, float &ezf) {
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, const float *sgj,
+                                       float si2, float gpre, float pal, float c1, float rc2,
+                                       float tspa, float &vf, float &exf, float &eyf, float &ezf) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     if (r2 < rc2) {
         const float ir = rsqrt_ftz(r2);
@@ -296,7 +358,7 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
         float dfr = 0.f;
         if (FIELD) dfr = -fmaf(tspa, e1, f) * ir;
         if (r2 < gpre) {
-            const float sj = __ldg(sgj);
+            const float sj = *sgj;
             const float g2 = fmaf(sj, sj, si2);
             // Gaussian correction; beyond r / gamma = 5 it is below 2e-12 / r and
             // is dropped (FP32 cannot resolve it next to erfc(alpha r) / r)
@@ -319,96 +381,85 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj,
     }
 }
 
-// Loop shape of the FP32 real-space kernel.  Each lane walks its entries k =
-// sub, sub + kTPR, ... in chunks of 32 (FP32 sums, flushed with compensation).
-// The list entry two iterations ahead and x_j one iteration ahead are loaded
-// before the current pair is evaluated (software pipelining), so the
-// DRAM latency of the streamed list and the L1/L2 latency of the gathered
-// positions overlap the pair arithmetic.
+// Unroll of the FP32 real-space entry loop: four independent pair evaluations
+// in flight per lane hide the SFU and shared-memory latencies (0.243 ms against
+// 0.297 ms without unrolling, 300,000 atoms).
 #ifndef QEQ_REAL_UNROLL
-#define QEQ_REAL_UNROLL 1
+#define QEQ_REAL_UNROLL 4
 #endif
 
-// FP32 pair math with one exp per erfc shared with the field term, image shifts
-// from a shared table, kTPR lanes per row, FP32 chunk sums of 32 entries
-// accumulated with compensation, and an FP32 shuffle combine of the lanes (no
-// FP64 arithmetic before the final scaling).  smax_bits holds the float bits of
-// max |sigma| over the atoms (written by the gather of the same apply).
-template <bool FIELD>
-__global__ void __launch_bounds__(kRealThreads, QEQ_REAL_MIN_BLOCKS)
-k_real32(RealArgs a, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+// FP32 real space, one block per brick: the tile (float4 positions with q, and
+// sigma) in shared memory (GTILE: in the block's slice of a global scratch
+// buffer), kTPR lanes per row, FP32 pair math with one exp per erfc shared with
+// the field term, FP32 sums (each lane about r_list^3 rho / 4 terms) and an FP32
+// shuffle combine of the lanes (no FP64 arithmetic before the final scaling).  smax_bits holds the float bits of max |sigma| over the atoms
+// (written by the gather of the same apply).
+template <bool FIELD, bool GTILE>
+__global__ void __launch_bounds__(kRealMaxThreads, QEQ_REAL_MIN_BLOCKS)
+k_real32(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
+         const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const float4 *__restrict__ xq, const float *__restrict__ sg,
-         const int32_t *__restrict__ smax_bits, double *__restrict__ v_s,
-         double *__restrict__ E_s) {
-    __shared__ float4 shift_tab[128];
-    for (int t = threadIdx.x; t < 125; t += blockDim.x)
-        shift_tab[t] = make_float4((float)(t / 25 - 2) * a.Lx_f, (float)((t / 5) % 5 - 2) * a.Ly_f,
-                                   (float)(t % 5 - 2) * a.Lz_f, 0.f);
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / kTPR, sub = t % kTPR;
-    float sv = 0.f, cv = 0.f, sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f;
-    if (i < a.n) {
-        const float4 xi = xq[i];
-        const float si = sg[i];
-        const float si2 = si * si;
-        float gpre = 3.4e38f;  // every pair checks sigma_j when max |sigma| is unknown
-        if (kRealLazySigma) {
-            const float smax = __int_as_float(__ldg(smax_bits));
-            gpre = 25.0001f * fmaf(smax, smax, si2);
-        }
-        const int c = cnt[i];
-        const float pal = kAsP * a.alpha_f, c1 = a.c1_f, rc2 = a.rc2_f, tspa = a.tspa_f;
-        const size_t step = (size_t)kTPR * a.n;
-        // e0: entry of the current iteration, e1: the next one; x_j of the current
-        // entry is in xj.  Entries past the row end read as 0 (atom 0, image code 0:
-        // a valid address, never evaluated).
-        const int32_t *pk = nbr + i + (size_t)sub * a.n;
-        int32_t e0 = sub < c ? __ldg(pk) : 0;
-        int32_t e1 = sub + kTPR < c ? __ldg(pk + step) : 0;
-        float4 xj = __ldg(xq + (e0 & kIndexMask));
-        const int n_it = c > sub ? (c - sub + kTPR - 1) / kTPR : 0;
-        for (int base = 0; base < n_it; base += 32) {
-            const int lim = min(32, n_it - base);
-            float vf = 0.f, exf = 0.f, eyf = 0.f, ezf = 0.f;
+         const int32_t *__restrict__ smax_bits, int cap, unsigned char *__restrict__ gtile,
+         int32_t *__restrict__ flags, double *__restrict__ v_s, double *__restrict__ E_s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
+    unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile32Bytes : smem_raw;
+    float4 *tile = (float4 *)base;
+    float *tsg = (float *)(base + (size_t)cap * 16);
+    const int total = stage_tile<float4, float>(g, cell_start, xq, sg, a.Lx_f, a.Ly_f, a.Lz_f, cap,
+                                                tile, tsg, t_start, t_base, t_code, &t_total, flags);
+    if (total < 0) return;
+    int i0, offc, nrows;
+    home_rows(g, t_start, t_base, total, i0, offc, nrows);
+    const float smax = kRealLazySigma ? __int_as_float(__ldg(smax_bits)) : 0.f;
+    const size_t step = (size_t)kTPR * a.n;  // one list group further
+    const int rpp = blockDim.x / kTPR;
+    for (int r0 = 0; r0 < nrows; r0 += rpp) {
+        const int r = r0 + threadIdx.x / kTPR, sub = threadIdx.x % kTPR;
+        const bool act = r < nrows;
+        float tv = 0.f, tx = 0.f, ty = 0.f, tz = 0.f;
+        if (act) {
+            const int i = i0 + r;
+            const float4 xi = tile[offc + r];
+            const float si = tsg[offc + r];
+            const float si2 = si * si;
+            // every pair checks sigma_j when max |sigma| is unknown
+            const float gpre = kRealLazySigma ? 25.0001f * fmaf(smax, smax, si2) : 3.4e38f;
+            const int c = cnt[i];
+            // e1: entry of the current iteration, e2: the next one, loaded ahead
+            // so that the DRAM latency of the list stream overlaps the pair math.
+            // Entries past the row end read as 0 (tile slot 0: never evaluated).
+            const uint16_t *pk = nbr + list_index(sub, i, a.n);
+            int e1 = sub < c ? __ldg(pk) : 0;
+            int e2 = sub + kTPR < c ? __ldg(pk + step) : 0;
             QEQ_UNROLL(QEQ_REAL_UNROLL)
-            for (int it = 0; it < lim; ++it) {
-                const int k = sub + (base + it) * kTPR;
-                const int32_t e = e0;
-                const float4 xc = xj;
-                e0 = e1;
+            for (int k = sub; k < c; k += kTPR) {
+                const int e = e1;
+                e1 = e2;
                 pk += step;
-                e1 = k + 2 * kTPR < c ? __ldg(pk + step) : 0;
-                xj = __ldg(xq + (e0 & kIndexMask));
-                const float4 sh = shift_tab[(uint32_t)e >> kIndexBits];
-                pair32<FIELD>((xc.x - xi.x) + sh.x, (xc.y - xi.y) + sh.y, (xc.z - xi.z) + sh.z, xc.w,
-                              sg + (e & kIndexMask), si2, gpre, pal, c1, rc2, tspa, vf, exf, eyf,
-                              ezf);
-            }
-            kahan_add(sv, cv, vf);
-            if (FIELD) {
-                kahan_add(sx, cx, exf);
-                kahan_add(sy, cy, eyf);
-                kahan_add(sz, cz, ezf);
+                e2 = k + 2 * kTPR < c ? __ldg(pk + step) : 0;
+                const float4 xc = tile[e];
+                pair32<FIELD>(xc.x - xi.x, xc.y - xi.y, xc.z - xi.z, xc.w, tsg + e, si2, gpre,
+                              a.pal_f, a.c1_f, a.rc2_f, a.tspa_f, tv, tx, ty, tz);
             }
         }
-    }
-    float tv = sv - cv, tx = sx - cx, ty = sy - cy, tz = sz - cz;
 #pragma unroll
-    for (int o = 1; o < kTPR; o <<= 1) {
-        tv += __shfl_xor_sync(0xffffffffu, tv, o);
-        if (FIELD) {
-            tx += __shfl_xor_sync(0xffffffffu, tx, o);
-            ty += __shfl_xor_sync(0xffffffffu, ty, o);
-            tz += __shfl_xor_sync(0xffffffffu, tz, o);
+        for (int o = 1; o < kTPR; o <<= 1) {
+            tv += __shfl_xor_sync(0xffffffffu, tv, o);
+            if (FIELD) {
+                tx += __shfl_xor_sync(0xffffffffu, tx, o);
+                ty += __shfl_xor_sync(0xffffffffu, ty, o);
+                tz += __shfl_xor_sync(0xffffffffu, tz, o);
+            }
         }
-    }
-    if (sub == 0 && i < a.n) {
-        v_s[i] = a.ke * (double)tv;
-        if (FIELD) {
-            E_s[3 * (size_t)i] = a.ke * (double)tx;
-            E_s[3 * (size_t)i + 1] = a.ke * (double)ty;
-            E_s[3 * (size_t)i + 2] = a.ke * (double)tz;
+        if (act && sub == 0) {
+            const int i = i0 + r;
+            v_s[i] = a.ke * (double)tv;
+            if (FIELD) {
+                E_s[3 * (size_t)i] = a.ke * (double)tx;
+                E_s[3 * (size_t)i + 1] = a.ke * (double)ty;
+                E_s[3 * (size_t)i + 2] = a.ke * (double)tz;
+            }
         }
     }
 }
@@ -760,6 +811,27 @@ void dispatch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const v
     }
 }
 
+// Launch shape of the brick-tiled real-space kernels for the current list: one
+// block per brick, kTPR lanes per row of the largest brick, the tile capacity
+// ctx->tile_cap (atoms) in shared memory, or in the global tile scratch when it
+// does not fit (boxes of a few hundred atoms whose tile repeats the box).
+struct RealLaunch {
+    int threads;
+    int cap;
+    size_t smem;
+    bool gtile;
+};
+
+RealLaunch real_launch(const qeq_ctx *ctx, bool f64) {
+    RealLaunch L;
+    L.threads = real_block_threads(ctx->rows_cap);
+    L.cap = ctx->tile_cap;
+    const size_t bytes = (size_t)L.cap * (f64 ? kTile64Bytes : kTile32Bytes);
+    L.gtile = bytes > (f64 ? kReal64SmemMax : kReal32SmemMax);
+    L.smem = L.gtile ? 0 : bytes;
+    return L;
+}
+
 template <typename T>
 int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma, double *v,
             double *E, double *F, double *energy4, bool need_field, cudaStream_t s) {
@@ -789,26 +861,40 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.rc2_f = (float)ra.rc2;
     ra.tspa_f = (float)(kTwoOverSqrtPi * ra.alpha);
     ra.c1_f = (float)(-ra.alpha * ra.alpha * 1.4426950408889634);
+    ra.pal_f = (float)(0.3275911 * ra.alpha);
     ra.Lx_f = (float)ra.Lx;
     ra.Ly_f = (float)ra.Ly;
     ra.Lz_f = (float)ra.Lz;
     prof_begin(ctx, kPhReal, s);
-    if (f64) {
-        if (need_field)
-            k_real64<true><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
-                                                            (double *)sg, ctx->erfc_tab64, ctx->v_s, ctx->E_s);
-        else
-            k_real64<false><<<grid_for((int64_t)n * kTPR), kThreads, 0, s>>>(ra, ctx->nbr, ctx->cnt, (double4_32a *)xq,
-                                                             (double *)sg, ctx->erfc_tab64, ctx->v_s, ctx->E_s);
-    } else {
-        if (need_field)
-            k_real32<true><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(
-                ra, ctx->nbr, ctx->cnt, (float4 *)xq, (float *)sg, ctx->d_flags + kFlagSigmaMax, ctx->v_s,
-                ctx->E_s);
-        else
-            k_real32<false><<<grid_for((int64_t)n * kTPR, kRealThreads), kRealThreads, 0, s>>>(
-                ra, ctx->nbr, ctx->cnt, (float4 *)xq, (float *)sg, ctx->d_flags + kFlagSigmaMax, ctx->v_s,
-                ctx->E_s);
+    {
+        const RealLaunch L = real_launch(ctx, f64);
+        const dim3 grid((unsigned)ctx->geom.nbricks);
+        int32_t *fl = ctx->d_flags;
+        unsigned char *gt = ctx->tile_scratch;
+        if (f64) {
+            auto *x4 = (const double4_32a *)xq;
+            auto *s1 = (const double *)sg;
+            if (need_field && !L.gtile)
+                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+            else if (need_field)
+                k_real64<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+            else if (!L.gtile)
+                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+            else
+                k_real64<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+        } else {
+            auto *x4 = (const float4 *)xq;
+            auto *s1 = (const float *)sg;
+            const int32_t *sm = ctx->d_flags + kFlagSigmaMax;
+            if (need_field && !L.gtile)
+                k_real32<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+            else if (need_field)
+                k_real32<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+            else if (!L.gtile)
+                k_real32<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+            else
+                k_real32<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+        }
     }
 
     prof_end(ctx, s);
@@ -961,6 +1047,24 @@ int coulomb_alloc(qeq_ctx *ctx) {
         if (rc) return rc;
     }
 
+    // dynamic shared memory of the tiled real-space kernels (up to 227 KB a block)
+    {
+        cudaError_t ea = cudaFuncSetAttribute(k_real32<true, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kReal32SmemMax);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_real32<false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal32SmemMax);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_real64<true, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal64SmemMax);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_real64<false, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal64SmemMax);
+        const int rca = cuda_check(ctx, ea, "real-space shared memory attribute");
+        if (rca) return rca;
+    }
+
     // piecewise erfc table of the FP64 real-space kernel
     {
         std::vector<double> tab = erfc_table();
@@ -996,6 +1100,20 @@ int coulomb_alloc(qeq_ctx *ctx) {
     return QEQ_OK;
 }
 
+int real_tile_reserve(qeq_ctx *ctx) {
+    const RealLaunch L = real_launch(ctx, !ctx->fp32);
+    if (!L.gtile) return QEQ_OK;
+    const size_t need = (size_t)ctx->geom.nbricks * L.cap * (ctx->fp32 ? kTile32Bytes : kTile64Bytes);
+    if (need <= ctx->tile_scratch_bytes) return QEQ_OK;
+    dev_free(ctx, ctx->tile_scratch);
+    ctx->tile_scratch = nullptr;
+    ctx->tile_scratch_bytes = 0;
+    const int rc = dev_alloc(ctx, (void **)&ctx->tile_scratch, need);
+    if (rc) return rc;
+    ctx->tile_scratch_bytes = need;
+    return QEQ_OK;
+}
+
 void coulomb_free(qeq_ctx *ctx) {
     if (ctx->have_plans) {
         cufftDestroy(ctx->plan_r2c);
@@ -1003,7 +1121,7 @@ void coulomb_free(qeq_ctx *ctx) {
     }
     void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
                     ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
-                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64};
+                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->tile_scratch};
     for (void *p : ptrs) dev_free(ctx, p);
     ewald_free(ctx);
     delete[] ctx->h_scal;

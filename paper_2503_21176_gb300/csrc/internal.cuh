@@ -39,8 +39,9 @@ constexpr int kMaxRedSlots = 72;
 static_assert(kMaxRank * (kMaxRank + 1) / 2 + kMaxRank <= kMaxRedSlots, "reduction slots");
 static_assert(kMaxGmresRestart + 1 <= kMaxRedSlots, "reduction slots");
 constexpr int kMaxHist = 8;
-// A neighbour entry packs the sorted atom index (low 24 bits) and the image
-// code (high 8 bits): code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2), |s| <= 2.
+// An entry of the allocation-free list packs the atom index (low 24 bits) and
+// the image code (high 8 bits): code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2),
+// |s| <= 2.  The atom count is limited to the 24-bit index range.
 constexpr int kIndexBits = 24;
 constexpr int32_t kIndexMask = (1 << kIndexBits) - 1;
 constexpr int kMaxWidthLimit = 1 << 16;
@@ -51,7 +52,155 @@ constexpr double kPi = 3.14159265358979323846;
 
 // Device-side status words (int32).
 // kFlagSigmaMax: float bits of max |sigma| of the last FP32 apply's inputs.
-enum Flag { kFlagMaxRow = 0, kFlagNonFinite = 1, kFlagSigmaMax = 2, kNumFlags = 4 };
+// kFlagMaxTile / kFlagMaxRows: largest tile (atoms) and brick (rows) of the last build.
+// kFlagTileOverflow: a real-space block met a tile larger than its capacity
+// (cannot happen for a list built by this context; the block then skips its brick).
+enum Flag {
+    kFlagMaxRow = 0,
+    kFlagNonFinite = 1,
+    kFlagSigmaMax = 2,
+    kFlagMaxTile = 3,
+    kFlagMaxRows = 4,
+    kFlagTileOverflow = 5,
+    kNumFlags = 8
+};
+
+// ---------------------------------------------------------------------------
+// Brick tiling of the cell grid.
+//
+// Cells are at least r_list / 2 wide, so a pair inside r_list lies at most
+// reach <= 2 cells apart per axis.  Cells are grouped into bricks of B x B x B
+// cells (B = 2 per axis, or 1 on an axis with a single cell).  The tile of a
+// brick is the (2 br + 1)^3 block of bricks around it, br = ceil(reach / B),
+// each with its periodic image shift; it holds every atom that a row of the
+// brick can pair with (27 bricks, about 2,000 atoms, for water at r_list 9 A).
+// Atoms are sorted brick-major (brick, then cell inside the brick, then atom
+// id), so a brick's atoms are one contiguous range.  Neighbour entries are
+// 16-bit indices into the tile of the row's brick: the tile is the
+// concatenation of its bricks in tile order (oz fastest), so the entry of
+// sorted atom j of tile brick rb is off[rb] + (j - start[rb]).
+// ---------------------------------------------------------------------------
+constexpr int kMaxTileBricks = 125;   // (2 br + 1)^3 with br <= 2
+constexpr int kMaxTileAtoms = 65535;  // 16-bit entries
+
+struct BrickGeom {
+    int nc[3];    // cells per axis
+    int B[3];     // cells per brick per axis (1 or 2)
+    int nb[3];    // bricks per axis
+    int br[3];    // tile radius in bricks per axis
+    int td[3];    // tile extent in bricks, 2 br + 1
+    int T;        // bricks in a tile
+    int bvol;     // cells per brick
+    int center;   // tile index of the brick itself
+    int64_t nbricks;
+};
+
+__host__ __device__ __forceinline__ int floor_div(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+__host__ __device__ __forceinline__ int64_t brick_index(const BrickGeom &g, int bx, int by, int bz) {
+    return ((int64_t)bx * g.nb[1] + by) * g.nb[2] + bz;
+}
+
+// Brick-major index of cell (cx, cy, cz), 0 <= c < nc.
+__host__ __device__ __forceinline__ int cell_index(const BrickGeom &g, int cx, int cy, int cz) {
+    const int bx = cx / g.B[0], by = cy / g.B[1], bz = cz / g.B[2];
+    const int lx = cx - bx * g.B[0], ly = cy - by * g.B[1], lz = cz - bz * g.B[2];
+    return (int)(brick_index(g, bx, by, bz) * g.bvol + (lx * g.B[1] + ly) * g.B[2] + lz);
+}
+
+__host__ __device__ __forceinline__ void cell_coords(const BrickGeom &g, int c, int &cx, int &cy,
+                                                     int &cz) {
+    const int b = c / g.bvol, l = c - b * g.bvol;
+    const int bz = b % g.nb[2], by = (b / g.nb[2]) % g.nb[1], bx = b / (g.nb[2] * g.nb[1]);
+    const int lz = l % g.B[2], ly = (l / g.B[2]) % g.B[1], lx = l / (g.B[2] * g.B[1]);
+    cx = bx * g.B[0] + lx;
+    cy = by * g.B[1] + ly;
+    cz = bz * g.B[2] + lz;
+}
+
+// Tile brick rb of brick b: the wrapped brick index and the image shift s per axis.
+__host__ __device__ __forceinline__ int64_t tile_brick(const BrickGeom &g, int64_t b, int rb, int s[3]) {
+    const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
+    const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
+    const int o[3] = {rb / (g.td[2] * g.td[1]) - g.br[0], (rb / g.td[2]) % g.td[1] - g.br[1],
+                      rb % g.td[2] - g.br[2]};
+    const int u[3] = {bx + o[0], by + o[1], bz + o[2]};
+    int w[3];
+    for (int d = 0; d < 3; ++d) {
+        s[d] = floor_div(u[d], g.nb[d]);
+        w[d] = u[d] - s[d] * g.nb[d];
+    }
+    return brick_index(g, w[0], w[1], w[2]);
+}
+
+// List layout: row i (sorted) keeps its entry k at list_index(k, i, n).  Entries
+// come in groups of kListGroup per row, rows interleaved group by group
+// ([width / 4][N][4]), so the 4 lanes that share a row in the real-space kernel
+// read 4 adjacent entries and a warp's 8 rows one contiguous 64-byte span.
+constexpr int kListGroup = 4;
+__host__ __device__ __forceinline__ size_t list_index(int k, int64_t i, int64_t n) {
+    return (((size_t)(k / kListGroup) * n + i) * kListGroup) + (k % kListGroup);
+}
+
+// Tile table of brick b, built by one warp (all 32 lanes): for every tile brick
+// rb the first sorted atom of its (wrapped) brick in start[rb], base[rb] =
+// off[rb] - start[rb] (a sorted atom j of rb has tile index j + base[rb]), the
+// image shift code (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2) in code[rb] (when
+// code is not null), and the tile size in *total.  off[rb] is the exclusive
+// prefix sum of the brick counts in tile order: T <= 125 = 4 bricks a lane and
+// one warp scan.
+__device__ __forceinline__ void tile_table(const BrickGeom &g, int64_t b,
+                                           const int32_t *__restrict__ cell_start, int *start,
+                                           int *base, int *code, int *total) {
+    const int lane = threadIdx.x & 31;
+    int cn[4], st[4], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int rb = lane * 4 + k;
+        cn[k] = 0;
+        st[k] = 0;
+        if (rb < g.T) {
+            int s[3];
+            const int64_t wb = tile_brick(g, b, rb, s);
+            st[k] = cell_start[wb * g.bvol];
+            cn[k] = cell_start[(wb + 1) * g.bvol] - st[k];
+            if (code) code[rb] = (s[0] + 2) * 25 + (s[1] + 2) * 5 + (s[2] + 2);
+        }
+        sum += cn[k];
+    }
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    int run = x - sum;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int rb = lane * 4 + k;
+        if (rb < g.T) {
+            start[rb] = st[k];
+            base[rb] = run - st[k];
+        }
+        run += cn[k];
+    }
+    if (lane == 31) *total = x;
+}
+
+// Tile index -> (tile brick, sorted atom): the last rb with off[rb] <= e, where
+// off[rb] = start[rb] + base[rb] is non-decreasing in rb.
+__device__ __forceinline__ int tile_locate(int e, int T, const int *start, const int *base) {
+    int lo = 0, hi = T - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] + base[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 // Device scalar table (double).  Slot 4 holds the last max displacement^2;
 // shadow.cu uses slots 32..127 for its reductions.
@@ -98,7 +247,7 @@ struct qeq_ctx {
 
     // ---- cell grid (Sec. 3.1) ----
     int nc[3] = {1, 1, 1};
-    int reach[3] = {1, 1, 1};
+    int reach[3] = {1, 1, 1};  // cells per axis a list pair can span
     int64_t ncell = 1;
     double cw[3] = {0, 0, 0};
     double rl = 0, rl2 = 0;
@@ -116,9 +265,18 @@ struct qeq_ctx {
     double *R_build = nullptr;      // [N][3] positions at the last build
     double4_32a *xs64 = nullptr;        // [N] wrapped positions at build (sorted)
     float4 *xs32 = nullptr;         // [N] FP32 copy
-    int32_t *nbr = nullptr;         // [width][N] packed entries, column-major
+    uint16_t *nbr = nullptr;        // [width][N] tile-local entries, column-major
     int32_t *cnt = nullptr;         // [N] entries per sorted row
     int width = 0;
+    qeq::BrickGeom geom{};
+    int max_tile = 0;               // largest brick tile of the current list (atoms)
+    int max_rows = 0;               // largest brick (rows) of the current list
+    // Launch capacities of the real-space kernels: grown (never shrunk) past the
+    // largest tile / brick seen, in steps, so that rebuilds rarely change the
+    // launch shape of a captured graph.
+    int tile_cap = 0, rows_cap = 0;
+    unsigned char *tile_scratch = nullptr;  // [nbricks][tile_cap] tiles when shared memory is too small
+    size_t tile_scratch_bytes = 0;
     int32_t *d_flags = nullptr;     // [kNumFlags]
     int32_t *h_flags = nullptr;     // pinned host mirror
     bool list_valid = false;
@@ -179,6 +337,7 @@ struct qeq_ctx {
     cudaGraphExec_t step_exec = nullptr;
     const void *graph_key[14] = {};  // state / parameter / list pointers it was captured with
     int graph_width = 0;
+    int graph_tile = 0, graph_rows = 0;  // launch geometry of the real-space kernel at capture
     int64_t graph_launches = 0;      // this library's kernels inside the graph
     bool use_graphs = true;
 
@@ -212,6 +371,9 @@ void nl_free(qeq_ctx *ctx);
 
 // ---- Coulomb operator (coulomb.cu) ----
 int coulomb_alloc(qeq_ctx *ctx);
+// Global tile scratch of the real-space kernels when the tile capacity exceeds
+// shared memory (after each neighbour build; allocates only when it must grow).
+int real_tile_reserve(qeq_ctx *ctx);
 void coulomb_free(qeq_ctx *ctx);
 // v, E, F in original numbering; E / F / energy4 may be null; need_field=false
 // skips every field computation (potential-only apply).

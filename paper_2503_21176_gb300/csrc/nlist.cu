@@ -3,14 +3,17 @@
 // The paper gathers a [N, 27, C_max] candidate tensor and filters it (Alg. 1).
 // Its Triton variant instead loops over neighbouring cells per atom, writing a
 // buffer sized by a neighbour-count estimate.  Here:
-//   1. wrap + bin            one thread per atom: wrap offsets, cell index, cell histogram
+//   1. wrap + bin            one thread per atom: wrap offsets, brick-major cell index,
+//                            cell histogram
 //   2. scan                  one block, exclusive scan of the cell histogram
 //   3. scatter               one thread per atom: slot in its cell (atomic)
 //   4. cell sort             one warp per cell: rank by atom id, so the order in a cell
 //                            is ascending atom id whatever order step 3 gave
-//   5. pair emit             one thread per sorted atom sweeps the (2r+1)^3 cell images;
-//                            FP32 distance prefilter, FP64 decision inside a band
-//                            around the list radius; ELLPACK rows, column-major
+//   5. pair emit             one block per brick: the tile table of the brick (the
+//                            bricks around it and their offsets), then one thread per
+//                            row sweeps the (2 reach + 1)^3 cell images; FP32 distance
+//                            prefilter, FP64 decision inside a band around the list
+//                            radius; 16-bit tile-local entries, column-major rows
 // The FP64 decision is d = (xw_j - xw_i) + s * L per axis, then
 // d2 = (dx*dx + dy*dy) + dz*dz < r_list^2, every operation explicitly rounded
 // (no fused multiply-add), so the emitted set is exactly the geometric one.
@@ -26,14 +29,8 @@ namespace qeq {
 
 namespace {
 
-__device__ __forceinline__ int floor_div(int a, int b) {
-    int q = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-    return q;
-}
-
 __global__ void k_wrap_bin(int n, const double *__restrict__ R, double Lx, double Ly, double Lz,
-                           double cwx, double cwy, double cwz, int ncx, int ncy, int ncz,
+                           double cwx, double cwy, double cwz, BrickGeom g,
                            int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_count,
                            double *__restrict__ wrap_off, double *__restrict__ R_build,
                            int32_t *__restrict__ flags) {
@@ -41,7 +38,7 @@ __global__ void k_wrap_bin(int n, const double *__restrict__ R, double Lx, doubl
     if (i >= n) return;
     const double L[3] = {Lx, Ly, Lz};
     const double cw[3] = {cwx, cwy, cwz};
-    const int nc[3] = {ncx, ncy, ncz};
+    const int nc[3] = {g.nc[0], g.nc[1], g.nc[2]};
     int c[3];
     bool finite = true;
 #pragma unroll
@@ -58,7 +55,7 @@ __global__ void k_wrap_bin(int n, const double *__restrict__ R, double Lx, doubl
         c[d] = min(max(cc, 0), nc[d] - 1);
     }
     if (!finite) atomicExch(&flags[kFlagNonFinite], 1);
-    const int cell = (c[0] * ncy + c[1]) * ncz + c[2];
+    const int cell = cell_index(g, c[0], c[1], c[2]);
     cell_of[i] = cell;
     atomicAdd(&cell_count[cell], 1);
 }
@@ -170,15 +167,13 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t *__restrict__ start,
 
 // Cells per list radius.  With cells r_list / 2 wide the emit visits 125 cells
 // holding about 1.16 (4 pi / 3)^-1 x 125 / 8 = 4.6x the atoms of the list ball,
-// against 27 cells and 6.4x with cells r_list wide.
-#ifndef QEQ_NL_CELL_DIV
-#define QEQ_NL_CELL_DIV 2
-#endif
-constexpr int kCellDiv = QEQ_NL_CELL_DIV;
+// against 27 cells and 6.4x with cells r_list wide.  The brick tiling needs it.
+constexpr int kCellDiv = 2;
 // Unroll of the candidate loop of the emit (independent candidate loads in flight).
 #ifndef QEQ_NL_UNROLL
 #define QEQ_NL_UNROLL 1
 #endif
+constexpr int kEmitThreads = 128;
 
 // s L for an image index s in [-2, 2]: exact in FP64 (a multiple of L by 0, 1 or
 // 2), selected without an FP64 multiply.
@@ -208,28 +203,33 @@ struct EmitArgs {
 constexpr int kShells = 8;
 
 template <bool PLACE>
-__device__ __forceinline__ void emit_sweep(const EmitArgs &a, int i, int cx, int cy, int cz,
-                                           const double4_32a &xi, const float4 &xf,
+__device__ __forceinline__ void emit_sweep(const EmitArgs &a, const BrickGeom &g, int i, int cx,
+                                           int cy, int cz, const double4_32a &xi, const float4 &xf,
                                            const double4_32a *__restrict__ xs64,
                                            const float4 *__restrict__ xs32,
-                                           const int32_t *__restrict__ cell_start, int (&cnt)[kShells],
-                                           int32_t *__restrict__ nbr) {
+                                           const int32_t *__restrict__ cell_start,
+                                           const int *__restrict__ t_base, int (&cnt)[kShells],
+                                           uint16_t *__restrict__ nbr) {
     const float inv_rl2 = (float)(kShells / a.rl2);
+    const int bx = cx / g.B[0], by = cy / g.B[1], bz = cz / g.B[2];
     for (int ox = -a.rx; ox <= a.rx; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
+        const int tx = floor_div(ux, g.B[0]) - bx + g.br[0];
         const double shx = image_shift(sx, a.Lx, a.L2x);
         const float shxf = (float)sx * a.Lfx;
         for (int oy = -a.ry; oy <= a.ry; ++oy) {
             const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
+            const int ty = floor_div(uy, g.B[1]) - by + g.br[1];
             const double shy = image_shift(sy, a.Ly, a.L2y);
             const float shyf = (float)sy * a.Lfy;
             for (int oz = -a.rz; oz <= a.rz; ++oz) {
                 const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
+                const int tz = floor_div(uz, g.B[2]) - bz + g.br[2];
                 const double shz = image_shift(sz, a.Lz, a.L2z);
                 const float shzf = (float)sz * a.Lfz;
-                const int cn = (wx * a.ncy + wy) * a.ncz + wz;
+                const int cn = cell_index(g, wx, wy, wz);
                 const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
-                const int32_t code = ((sx + 2) * 25 + (sy + 2) * 5 + (sz + 2)) << kIndexBits;
+                const int base = t_base[(tx * g.td[1] + ty) * g.td[2] + tz];
                 const int jb = cell_start[cn], je = cell_start[cn + 1];
                 QEQ_UNROLL(QEQ_NL_UNROLL)
                 for (int j = jb; j < je; ++j) {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void emit_sweep(const EmitArgs &a, int i, int cx, int
                         const int shell = min(kShells - 1, max(0, (int)(d2f * inv_rl2)));
                         if (PLACE) {
                             const int slot = cnt[shell]++;
-                            if (slot < a.width) nbr[(size_t)slot * a.n + i] = j | code;
+                            if (slot < a.width) nbr[list_index(slot, i, a.n)] = (uint16_t)(j + base);
                         } else {
                             ++cnt[shell];
                         }
@@ -268,49 +268,74 @@ __device__ __forceinline__ void emit_sweep(const EmitArgs &a, int i, int cx, int
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_emit(EmitArgs a, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
+// One block per brick.  Warp 0 builds the tile table; the threads then take the
+// brick's rows.  The block also records the largest tile and brick for the
+// real-space launch, and writes no entry when the tile exceeds 16-bit indices.
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
        const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
-       int32_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int c = cell_s[i];
-    const int cx = c / (a.ncy * a.ncz), cy = (c / a.ncz) % a.ncy, cz = c % a.ncz;
-    const double4_32a xi = xs64[i];
-    const float4 xf = xs32[i];
-    int shell[kShells];
-#pragma unroll
-    for (int b = 0; b < kShells; ++b) shell[b] = 0;
-    emit_sweep<false>(a, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, shell, nbr);
-    // shell counts -> first slot of each shell
-    int count = 0;
-#pragma unroll
-    for (int b = 0; b < kShells; ++b) {
-        const int c_b = shell[b];
-        shell[b] = count;
-        count += c_b;
+       uint16_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_total;
+    const int64_t b = blockIdx.x;
+    if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, nullptr, &t_total);
+    __syncthreads();
+    const int i0 = t_start[g.center], i1 = cell_start[(b + 1) * g.bvol];
+    if (threadIdx.x == 0) {
+        atomicMax(&flags[kFlagMaxTile], t_total);
+        atomicMax(&flags[kFlagMaxRows], i1 - i0);
     }
-    emit_sweep<true>(a, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, shell, nbr);
-    cnt[i] = min(count, a.width);
-    if (count > a.width) atomicMax(&flags[kFlagMaxRow], count);
+    const bool fits = t_total <= kMaxTileAtoms;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        if (!fits) {
+            cnt[i] = 0;
+            continue;
+        }
+        int cx, cy, cz;
+        cell_coords(g, cell_s[i], cx, cy, cz);
+        const double4_32a xi = xs64[i];
+        const float4 xf = xs32[i];
+        int shell[kShells];
+#pragma unroll
+        for (int k = 0; k < kShells; ++k) shell[k] = 0;
+        emit_sweep<false>(a, g, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, t_base, shell, nbr);
+        // shell counts -> first slot of each shell
+        int count = 0;
+#pragma unroll
+        for (int k = 0; k < kShells; ++k) {
+            const int c_k = shell[k];
+            shell[k] = count;
+            count += c_k;
+        }
+        emit_sweep<true>(a, g, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, t_base, shell, nbr);
+        cnt[i] = min(count, a.width);
+        if (count > a.width) atomicMax(&flags[kFlagMaxRow], count);
+    }
 }
 
-// COO scatter: sorted row i with entries k < cnt[i] goes to slots offset[i] + k as
-// (original i, original j, image code), so the pair order is the list's.
-__global__ void k_coo_scatter(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ nbr,
-                              const int32_t *__restrict__ cnt, const int32_t *__restrict__ offset,
-                              int32_t *__restrict__ coo_i, int32_t *__restrict__ coo_j,
-                              int8_t *__restrict__ coo_code) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = cnt[i];
-    const int base = offset[i];
-    const int ai = perm[i];
-    for (int k = 0; k < c; ++k) {
-        const int32_t e = nbr[(size_t)k * n + i];
-        coo_i[base + k] = ai;
-        coo_j[base + k] = perm[e & kIndexMask];
-        coo_code[base + k] = (int8_t)((uint32_t)e >> kIndexBits);
+// COO scatter, one block per brick: sorted row i with entries k < cnt[i] goes to
+// slots offset[i] + k as (original i, original j, image code), so the pair order
+// is the list's.
+__global__ void __launch_bounds__(kEmitThreads)
+k_coo_scatter(int n, BrickGeom g, const int32_t *__restrict__ cell_start,
+              const int32_t *__restrict__ perm, const uint16_t *__restrict__ nbr,
+              const int32_t *__restrict__ cnt, const int32_t *__restrict__ offset,
+              int32_t *__restrict__ coo_i, int32_t *__restrict__ coo_j, int8_t *__restrict__ coo_code) {
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
+    const int64_t b = blockIdx.x;
+    if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, t_code, &t_total);
+    __syncthreads();
+    const int i0 = t_start[g.center], i1 = cell_start[(b + 1) * g.bvol];
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int c = cnt[i];
+        const int off = offset[i];
+        const int ai = perm[i];
+        for (int k = 0; k < c; ++k) {
+            const int e = nbr[list_index(k, i, n)];
+            const int rb = tile_locate(e, g.T, t_start, t_base);
+            coo_i[off + k] = ai;
+            coo_j[off + k] = perm[e - t_base[rb]];
+            coo_code[off + k] = (int8_t)t_code[rb];
+        }
     }
 }
 
@@ -357,25 +382,42 @@ int nl_configure(qeq_ctx *ctx) {
     ctx->rl = p.r_cut + p.skin;
     ctx->rl2 = ctx->rl * ctx->rl;
     double lmax = 0.0;
+    BrickGeom &g = ctx->geom;
+    g.T = 1;
+    g.bvol = 1;
     for (int d = 0; d < 3; ++d) {
         const double L = p.box[d];
         lmax = std::max(lmax, L);
         // cells at least r_list / kCellDiv wide (with a relative margin so that
         // rounding in the cell index cannot move an atom by more than one cell);
-        // the emit then visits (2 reach + 1)^3 cells
+        // the emit then visits (2 reach + 1)^3 cells.  With four or more cells the
+        // count is made even and cells pair into bricks of 2; with fewer, a brick
+        // is one cell.
         int nc = (int)std::floor(L / (ctx->rl / kCellDiv * (1.0 + 1e-9)));
         if (nc < 1) nc = 1;
         if (nc > 1024) nc = 1024;
+        if (nc >= 4) nc &= ~1;
         ctx->nc[d] = nc;
         ctx->cw[d] = L / nc;
         ctx->reach[d] = (int)std::ceil(ctx->rl * (1.0 + 1e-9) / ctx->cw[d]);
-        // image index |s| <= ceil(reach / nc) must fit the 8-bit image code (|s| <= 2)
+        // image index |s| <= ceil(reach / nc) must stay within [-2, 2]
         const int smax = (ctx->reach[d] + nc - 1) / nc;
         if (smax > 2)
             return set_error(ctx, QEQ_ERR_UNSUPPORTED,
                              "box edge %d (%.6g) is shorter than half the list radius %.6g", d, L,
                              ctx->rl);
+        g.nc[d] = nc;
+        g.B[d] = nc >= 4 ? 2 : 1;
+        g.nb[d] = nc / g.B[d];
+        g.br[d] = (ctx->reach[d] + g.B[d] - 1) / g.B[d];
+        g.td[d] = 2 * g.br[d] + 1;
+        g.T *= g.td[d];
+        g.bvol *= g.B[d];
     }
+    if (g.T > kMaxTileBricks)
+        return set_error(ctx, QEQ_ERR_UNSUPPORTED, "tile of %d bricks exceeds %d", g.T, kMaxTileBricks);
+    g.center = (g.br[0] * g.td[1] + g.br[1]) * g.td[2] + g.br[2];
+    g.nbricks = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
     ctx->ncell = (int64_t)ctx->nc[0] * ctx->nc[1] * ctx->nc[2];
     // FP32 prefilter band: |d2_fp32 - d2_exact| is bounded by a few ulp of the
     // coordinates times the list radius; 4e-5 * rl * (Lmax + rl) is >10x that bound.
@@ -391,7 +433,7 @@ int nl_alloc_list(qeq_ctx *ctx, int width) {
                          width, kMaxWidthLimit);
     dev_free(ctx, ctx->nbr);
     ctx->nbr = nullptr;
-    int rc = dev_alloc(ctx, (void **)&ctx->nbr, sizeof(int32_t) * (size_t)width * ctx->n);
+    int rc = dev_alloc(ctx, (void **)&ctx->nbr, sizeof(uint16_t) * (size_t)width * ctx->n);
     if (rc) return rc;
     ctx->width = width;
     return QEQ_OK;
@@ -453,8 +495,9 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     a.lo = ctx->rl2f_lo;
     a.hi = ctx->rl2f_hi;
     a.width = ctx->width;
-    k_emit<<<grid_for(ctx->n), kThreads, 0, s>>>(a, ctx->xs64, ctx->xs32, ctx->cell_s,
-                                                 ctx->cell_start, ctx->nbr, ctx->cnt, ctx->d_flags);
+    k_emit<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
+        a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr, ctx->cnt,
+        ctx->d_flags);
 }
 
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
@@ -465,8 +508,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
     cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
     k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(
         n, R, ctx->p.box[0], ctx->p.box[1], ctx->p.box[2], ctx->cw[0], ctx->cw[1], ctx->cw[2],
-        ctx->nc[0], ctx->nc[1], ctx->nc[2], ctx->cell_of, ctx->cell_count, ctx->wrap_off,
-        ctx->R_build, ctx->d_flags);
+        ctx->geom, ctx->cell_of, ctx->cell_count, ctx->wrap_off, ctx->R_build, ctx->d_flags);
     k_scan<<<1, kScanThreads, 0, s>>>(ctx->ncell, ctx->cell_count, ctx->cell_start, ctx->cell_fill);
     k_scatter<<<grid_for(n), kThreads, 0, s>>>(n, ctx->cell_of, ctx->cell_start, ctx->cell_fill,
                                                ctx->tmp_list);
@@ -484,6 +526,14 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
             ctx->list_valid = false;
             return set_error(ctx, QEQ_ERR_NONFINITE, "non-finite position in neighbor_build");
         }
+        if (ctx->h_flags[kFlagMaxTile] > kMaxTileAtoms) {
+            ctx->list_valid = false;
+            return set_error(ctx, QEQ_ERR_CAPACITY,
+                             "a brick tile holds %d atoms, more than the %d of 16-bit entries",
+                             ctx->h_flags[kFlagMaxTile], kMaxTileAtoms);
+        }
+        ctx->max_tile = ctx->h_flags[kFlagMaxTile];
+        ctx->max_rows = ctx->h_flags[kFlagMaxRows];
         const int need = ctx->h_flags[kFlagMaxRow];
         if (need <= ctx->width) break;
         // grow (the paper's estimate-plus-buffer, Sec. 3.1) and emit again
@@ -497,6 +547,16 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
         launch_emit(ctx, s);
         prof_end(ctx, s);
         ctx->launches++;
+    }
+    // launch capacities of the real-space kernels (grown in steps, never shrunk)
+    const int tcap = (ctx->max_tile + 32 + 63) / 64 * 64;
+    const int rcap = (ctx->max_rows + 7) / 8 * 8;
+    ctx->tile_cap = std::max(ctx->tile_cap, tcap);
+    ctx->rows_cap = std::max(ctx->rows_cap, rcap);
+    int rc = real_tile_reserve(ctx);
+    if (rc) {
+        ctx->list_valid = false;
+        return rc;
     }
     ctx->list_valid = true;
     ctx->n_builds++;
@@ -538,8 +598,9 @@ int nl_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *coo_i, int32_t *coo_j
             rc = set_error(ctx, QEQ_ERR_CAPACITY, "COO needs %d pairs, capacity is %lld", total,
                            (long long)capacity);
         } else {
-            k_coo_scatter<<<grid_for(n), kThreads, 0, s>>>(n, ctx->perm, ctx->nbr, ctx->cnt, scan_out,
-                                                          coo_i, coo_j, coo_code);
+            k_coo_scatter<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
+                n, ctx->geom, ctx->cell_start, ctx->perm, ctx->nbr, ctx->cnt, scan_out, coo_i,
+                coo_j, coo_code);
             ctx->launches += 2;
             rc = cuda_check(ctx, cudaGetLastError(), "coo scatter");
         }
@@ -552,7 +613,9 @@ int nl_export_coo(qeq_ctx *ctx, int64_t capacity, int32_t *coo_i, int32_t *coo_j
 int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr_out, int8_t *shift_out) {
     const int64_t n = ctx->n;
     const int w = ctx->width;
-    std::vector<int32_t> perm(n), cnt(n), nbr((size_t)w * n);
+    const BrickGeom &g = ctx->geom;
+    std::vector<int32_t> perm(n), cnt(n), cell_start(ctx->ncell + 1);
+    std::vector<uint16_t> nbr((size_t)w * n);
     int rc = cuda_check(ctx, ctx->async_alloc ? cudaStreamSynchronize(ctx->alloc_stream)
                                               : cudaDeviceSynchronize(), "export sync");
     if (rc) return rc;
@@ -562,22 +625,36 @@ int nl_export(qeq_ctx *ctx, int32_t *counts, int32_t *nbr_out, int8_t *shift_out
     rc = cuda_check(ctx, cudaMemcpy(cnt.data(), ctx->cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost),
                     "export counts");
     if (rc) return rc;
-    rc = cuda_check(ctx, cudaMemcpy(nbr.data(), ctx->nbr, sizeof(int32_t) * (size_t)w * n,
+    rc = cuda_check(ctx, cudaMemcpy(cell_start.data(), ctx->cell_start,
+                                    sizeof(int32_t) * (ctx->ncell + 1), cudaMemcpyDeviceToHost),
+                    "export cells");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpy(nbr.data(), ctx->nbr, sizeof(uint16_t) * (size_t)w * n,
                                     cudaMemcpyDeviceToHost),
                     "export list");
     if (rc) return rc;
-    for (int64_t si = 0; si < n; ++si) {
-        const int64_t atom = perm[si];
-        if (counts) counts[atom] = cnt[si];
-        for (int k = 0; k < cnt[si]; ++k) {
-            const int32_t e = nbr[(size_t)k * n + si];
-            const int32_t j = e & kIndexMask;
-            const int code = (int)((uint32_t)e >> kIndexBits);
-            if (nbr_out) nbr_out[atom * w + k] = perm[j];
-            if (shift_out) {
-                shift_out[(atom * w + k) * 3 + 0] = (int8_t)(code / 25 - 2);
-                shift_out[(atom * w + k) * 3 + 1] = (int8_t)((code / 5) % 5 - 2);
-                shift_out[(atom * w + k) * 3 + 2] = (int8_t)(code % 5 - 2);
+    // per brick: the tile table (first tile index, first sorted atom, image shift
+    // of each tile brick), then every row of the brick decoded through it
+    std::vector<int> off(g.T + 1), start(g.T), shift(3 * g.T);
+    for (int64_t b = 0; b < g.nbricks; ++b) {
+        off[0] = 0;
+        for (int rb = 0; rb < g.T; ++rb) {
+            int s[3];
+            const int64_t wb = tile_brick(g, b, rb, s);
+            start[rb] = cell_start[wb * g.bvol];
+            off[rb + 1] = off[rb] + cell_start[(wb + 1) * g.bvol] - start[rb];
+            for (int d = 0; d < 3; ++d) shift[3 * rb + d] = s[d];
+        }
+        for (int64_t si = cell_start[b * g.bvol]; si < cell_start[(b + 1) * g.bvol]; ++si) {
+            const int64_t atom = perm[si];
+            if (counts) counts[atom] = cnt[si];
+            for (int k = 0; k < cnt[si]; ++k) {
+                const int e = nbr[list_index(k, si, n)];
+                const int rb = (int)(std::upper_bound(off.begin(), off.end(), e) - off.begin()) - 1;
+                const int32_t j = start[rb] + (e - off[rb]);
+                if (nbr_out) nbr_out[atom * w + k] = perm[j];
+                if (shift_out)
+                    for (int d = 0; d < 3; ++d) shift_out[(atom * w + k) * 3 + d] = (int8_t)shift[3 * rb + d];
             }
         }
     }
@@ -773,9 +850,16 @@ QEQ_API int qeq_neighbor_build_noalloc(const double *R, int64_t n_atoms, const d
     const int n = (int)n_atoms;
     cudaMemsetAsync(S->cell_count, 0, sizeof(int32_t) * ncell, s);
     cudaMemsetAsync(S->flags, 0, sizeof(int32_t) * kNumFlags, s);
+    // one cell per brick: the cell index is the plain (cx * ncy + cy) * ncz + cz
+    BrickGeom g{};
+    for (int d = 0; d < 3; ++d) {
+        g.nc[d] = g.nb[d] = nc[d];
+        g.B[d] = 1;
+    }
+    g.bvol = 1;
     k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(n, R, box[0], box[1], box[2], cw[0], cw[1], cw[2],
-                                                nc[0], nc[1], nc[2], S->cell_of, S->cell_count,
-                                                S->wrap_off, S->R_build, S->flags);
+                                                g, S->cell_of, S->cell_count, S->wrap_off,
+                                                S->R_build, S->flags);
     k_scan<<<1, kScanThreads, 0, s>>>(ncell, S->cell_count, S->cell_start, S->cell_fill);
     k_scatter<<<grid_for(n), kThreads, 0, s>>>(n, S->cell_of, S->cell_start, S->cell_fill,
                                                S->tmp_list);

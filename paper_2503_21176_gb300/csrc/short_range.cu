@@ -71,43 +71,55 @@ __global__ void k_water_intra(int n_mol, const double *__restrict__ R, double Lx
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
 }
 
-// O-O Lennard-Jones over the list: sorted atom i is an O when perm[i] % 3 == 0.
-__global__ void k_water_lj(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ nbr,
-                           const int32_t *__restrict__ cnt, const double *__restrict__ R,
-                           const double *__restrict__ wrap_off, double Lx, double Ly, double Lz,
-                           double rc2, double *__restrict__ F, double *__restrict__ part) {
+// O-O Lennard-Jones over the list, one block per brick: sorted atom i is an O
+// when perm[i] % 3 == 0; an entry e of row i is decoded through the brick's tile
+// table into the sorted atom j and its image shift.
+__global__ void __launch_bounds__(kThreads)
+k_water_lj(int n, BrickGeom g, const int32_t *__restrict__ cell_start,
+           const int32_t *__restrict__ perm, const uint16_t *__restrict__ nbr,
+           const int32_t *__restrict__ cnt, const double *__restrict__ R,
+           const double *__restrict__ wrap_off, double Lx, double Ly, double Lz, double rc2,
+           double *__restrict__ F, double *__restrict__ part) {
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     double e = 0.0;
     const double s6 = kLjSigma * kLjSigma * kLjSigma * kLjSigma * kLjSigma * kLjSigma;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int ai = perm[i];
-        if (ai % 3 != 0) continue;
-        const double xi = R[3 * (size_t)ai] + wrap_off[3 * (size_t)ai];
-        const double yi = R[3 * (size_t)ai + 1] + wrap_off[3 * (size_t)ai + 1];
-        const double zi = R[3 * (size_t)ai + 2] + wrap_off[3 * (size_t)ai + 2];
-        double fx = 0.0, fy = 0.0, fz = 0.0;
-        const int c = cnt[i];
-        for (int k = 0; k < c; ++k) {
-            const int32_t en = nbr[(size_t)k * n + i];
-            const int aj = perm[en & kIndexMask];
-            if (aj % 3 != 0) continue;
-            const int code = (int)((uint32_t)en >> kIndexBits);
-            const double dx = (R[3 * (size_t)aj] + wrap_off[3 * (size_t)aj] - xi) + (code / 25 - 2) * Lx;
-            const double dy = (R[3 * (size_t)aj + 1] + wrap_off[3 * (size_t)aj + 1] - yi) +
-                              ((code / 5) % 5 - 2) * Ly;
-            const double dz = (R[3 * (size_t)aj + 2] + wrap_off[3 * (size_t)aj + 2] - zi) +
-                              (code % 5 - 2) * Lz;
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (!(r2 < rc2)) continue;
-            const double inv6 = s6 / (r2 * r2 * r2);
-            e += 0.5 * 4.0 * kLjEps * (inv6 * inv6 - inv6);
-            const double g = 4.0 * kLjEps * (-12.0 * inv6 * inv6 + 6.0 * inv6) / r2;
-            fx += g * dx;
-            fy += g * dy;
-            fz += g * dz;
+    for (int64_t b = blockIdx.x; b < g.nbricks; b += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, t_code, &t_total);
+        __syncthreads();
+        const int i0 = t_start[g.center], i1 = cell_start[(b + 1) * g.bvol];
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int ai = perm[i];
+            if (ai % 3 != 0) continue;
+            const double xi = R[3 * (size_t)ai] + wrap_off[3 * (size_t)ai];
+            const double yi = R[3 * (size_t)ai + 1] + wrap_off[3 * (size_t)ai + 1];
+            const double zi = R[3 * (size_t)ai + 2] + wrap_off[3 * (size_t)ai + 2];
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            const int c = cnt[i];
+            for (int k = 0; k < c; ++k) {
+                const int en = nbr[list_index(k, i, n)];
+                const int rb = tile_locate(en, g.T, t_start, t_base);
+                const int aj = perm[en - t_base[rb]];
+                if (aj % 3 != 0) continue;
+                const int code = t_code[rb];
+                const double dx = (R[3 * (size_t)aj] + wrap_off[3 * (size_t)aj] - xi) + (code / 25 - 2) * Lx;
+                const double dy = (R[3 * (size_t)aj + 1] + wrap_off[3 * (size_t)aj + 1] - yi) +
+                                  ((code / 5) % 5 - 2) * Ly;
+                const double dz = (R[3 * (size_t)aj + 2] + wrap_off[3 * (size_t)aj + 2] - zi) +
+                                  (code % 5 - 2) * Lz;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2)) continue;
+                const double inv6 = s6 / (r2 * r2 * r2);
+                e += 0.5 * 4.0 * kLjEps * (inv6 * inv6 - inv6);
+                const double gg = 4.0 * kLjEps * (-12.0 * inv6 * inv6 + 6.0 * inv6) / r2;
+                fx += gg * dx;
+                fy += gg * dy;
+                fz += gg * dz;
+            }
+            F[3 * (size_t)ai] += fx;
+            F[3 * (size_t)ai + 1] += fy;
+            F[3 * (size_t)ai + 2] += fz;
         }
-        F[3 * (size_t)ai] += fx;
-        F[3 * (size_t)ai + 1] += fy;
-        F[3 * (size_t)ai + 2] += fz;
     }
     double vals[1] = {e};
     block_sum<1>(vals);
@@ -124,9 +136,9 @@ int short_range_forces(qeq_ctx *ctx, const double *R, const double *, double *F_
     const qeq_params &p = ctx->p;
     k_water_intra<<<kRedBlocks, kThreads, 0, s>>>(n / 3, R, p.box[0], p.box[1], p.box[2], F_short,
                                                   ctx->part);
-    k_water_lj<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->perm, ctx->nbr, ctx->cnt, R, ctx->wrap_off,
-                                               p.box[0], p.box[1], p.box[2], p.r_cut * p.r_cut,
-                                               F_short, ctx->part);
+    k_water_lj<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->geom, ctx->cell_start, ctx->perm, ctx->nbr,
+                                               ctx->cnt, R, ctx->wrap_off, p.box[0], p.box[1],
+                                               p.box[2], p.r_cut * p.r_cut, F_short, ctx->part);
     launch_finalize(ctx->part, 2, e_slot, s);
     ctx->launches += 3;
     return cuda_check(ctx, cudaGetLastError(), "short-range launch");
