@@ -201,81 +201,112 @@ struct EmitArgs {
 // distance branches (cutoff test, Gaussian correction) agree across the warp.
 // Pass 0 counts each shell, pass 1 places the entries.
 constexpr int kShells = 8;
+// Lanes per row in the emit: lane s of a row tests candidates s, s + 4, ... of
+// the row's candidate stream (its cell's (2 reach + 1)^3 neighbour cells,
+// concatenated).  Rows of one cell have the same stream, so the 8 rows of a warp
+// (mostly one cell of about 9 atoms) walk it in lockstep.
+constexpr int kEmitLanes = 4;
+constexpr int kMaxBrickCells = 8;
+constexpr int kCenterCode = 62;  // image code of the zero shift
 
+// Per-lane shell counters, 16 bits a shell, shells 0-3 in lo and 4-7 in hi
+// (register-resident; a row holds at most 65535 entries, the tile limit).
+struct ShellCount {
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(int shell) {
+        const unsigned long long inc = 1ull << (16 * (shell & 3));
+        lo += shell < 4 ? inc : 0ull;
+        hi += shell < 4 ? 0ull : inc;
+    }
+    __device__ __forceinline__ int get(int shell) const {
+        return (int)(((shell < 4 ? lo : hi) >> (16 * (shell & 3))) & 0xffffu);
+    }
+};
+
+// The candidate stream of one lane: cell k of the table, candidate j in it.
+struct Cursor {
+    int k, j;
+    int4 ct;  // (first sorted atom, end, tile base, image code) of cell k
+};
+
+__device__ __forceinline__ bool cursor_fix(Cursor &c, const int4 *__restrict__ tab, int ncand) {
+    while (c.j >= c.ct.y) {
+        const int over = c.j - c.ct.y;
+        if (++c.k >= ncand) return false;
+        c.ct = tab[c.k];
+        c.j = c.ct.x + over;
+    }
+    return true;
+}
+
+// One pass over a row's candidate stream.  PLACE = false counts the kept
+// entries per shell; PLACE = true writes each at the next slot of its shell
+// (start holds the lane's first slot per shell).  The FP64 decision is taken
+// only inside the band [lo, hi] of the FP32 distance.
 template <bool PLACE>
-__device__ __forceinline__ void emit_sweep(const EmitArgs &a, const BrickGeom &g, int i, int cx,
-                                           int cy, int cz, const double4_32a &xi, const float4 &xf,
-                                           const double4_32a *__restrict__ xs64,
-                                           const float4 *__restrict__ xs32,
-                                           const int32_t *__restrict__ cell_start,
-                                           const int *__restrict__ t_base, int (&cnt)[kShells],
-                                           uint16_t *__restrict__ nbr) {
+__device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, const int4 *__restrict__ tab,
+                                            int ncand, const double4_32a &xi, const float4 &xf,
+                                            const double4_32a *__restrict__ xs64,
+                                            const float4 *__restrict__ xs32, ShellCount &sc,
+                                            uint16_t *__restrict__ nbr) {
     const float inv_rl2 = (float)(kShells / a.rl2);
-    const int bx = cx / g.B[0], by = cy / g.B[1], bz = cz / g.B[2];
-    for (int ox = -a.rx; ox <= a.rx; ++ox) {
-        const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
-        const int tx = floor_div(ux, g.B[0]) - bx + g.br[0];
-        const double shx = image_shift(sx, a.Lx, a.L2x);
-        const float shxf = (float)sx * a.Lfx;
-        for (int oy = -a.ry; oy <= a.ry; ++oy) {
-            const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
-            const int ty = floor_div(uy, g.B[1]) - by + g.br[1];
-            const double shy = image_shift(sy, a.Ly, a.L2y);
-            const float shyf = (float)sy * a.Lfy;
-            for (int oz = -a.rz; oz <= a.rz; ++oz) {
-                const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
-                const int tz = floor_div(uz, g.B[2]) - bz + g.br[2];
-                const double shz = image_shift(sz, a.Lz, a.L2z);
-                const float shzf = (float)sz * a.Lfz;
-                const int cn = cell_index(g, wx, wy, wz);
-                const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
-                const int base = t_base[(tx * g.td[1] + ty) * g.td[2] + tz];
-                const int jb = cell_start[cn], je = cell_start[cn + 1];
-                QEQ_UNROLL(QEQ_NL_UNROLL)
-                for (int j = jb; j < je; ++j) {
-                    if (self_img && j == i) continue;
-                    const float4 xj = xs32[j];
-                    const float dxf = (xj.x - xf.x) + shxf;
-                    const float dyf = (xj.y - xf.y) + shyf;
-                    const float dzf = (xj.z - xf.z) + shzf;
-                    const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-                    bool keep;
-                    if (d2f < a.lo) {
-                        keep = true;
-                    } else if (d2f > a.hi) {
-                        keep = false;
-                    } else {
-                        const double4_32a xj64 = xs64[j];
-                        const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), shx);
-                        const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), shy);
-                        const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), shz);
-                        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                                                    __dmul_rn(dz, dz));
-                        keep = d2 < a.rl2;
-                    }
-                    if (keep) {
-                        const int shell = min(kShells - 1, max(0, (int)(d2f * inv_rl2)));
-                        if (PLACE) {
-                            const int slot = cnt[shell]++;
-                            if (slot < a.width) nbr[list_index(slot, i, a.n)] = (uint16_t)(j + base);
-                        } else {
-                            ++cnt[shell];
-                        }
-                    }
-                }
+    Cursor c;
+    c.k = 0;
+    c.ct = tab[0];
+    c.j = c.ct.x + s;
+    int code = -1;
+    float shx = 0.f, shy = 0.f, shz = 0.f;
+    while (cursor_fix(c, tab, ncand)) {
+        if (c.ct.w != code) {
+            code = c.ct.w;
+            shx = (float)(code / 25 - 2) * a.Lfx;
+            shy = (float)((code / 5) % 5 - 2) * a.Lfy;
+            shz = (float)(code % 5 - 2) * a.Lfz;
+        }
+        const int j = c.j;
+        c.j += kEmitLanes;
+        if (code == kCenterCode && j == i) continue;
+        const float4 xj = xs32[j];
+        const float dxf = (xj.x - xf.x) + shx;
+        const float dyf = (xj.y - xf.y) + shy;
+        const float dzf = (xj.z - xf.z) + shz;
+        const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+        bool keep;
+        if (d2f < a.lo) {
+            keep = true;
+        } else if (d2f > a.hi) {
+            keep = false;
+        } else {
+            const double4_32a xj64 = xs64[j];
+            const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), image_shift(code / 25 - 2, a.Lx, a.L2x));
+            const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), image_shift((code / 5) % 5 - 2, a.Ly, a.L2y));
+            const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), image_shift(code % 5 - 2, a.Lz, a.L2z));
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            keep = d2 < a.rl2;
+        }
+        if (keep) {
+            const int shell = min(kShells - 1, max(0, (int)(d2f * inv_rl2)));
+            if (PLACE) {
+                const int slot = sc.get(shell);
+                if (slot < a.width) nbr[list_index(slot, i, a.n)] = (uint16_t)(j + c.ct.z);
             }
+            sc.add(shell);
         }
     }
 }
 
-// One block per brick.  Warp 0 builds the tile table; the threads then take the
-// brick's rows.  The block also records the largest tile and brick for the
-// real-space launch, and writes no entry when the tile exceeds 16-bit indices.
+// One block per brick.  Warp 0 builds the tile table, then the block builds the
+// candidate-cell table of each cell of the brick (first / end sorted atom, tile
+// base and image code of each of its (2 reach + 1)^3 neighbour cells).  Warps
+// take the brick's rows 8 at a time, kEmitLanes lanes a row.  The block also
+// records the largest tile and brick for the real-space launch, and writes no
+// entry when the tile exceeds 16-bit indices.
 __global__ void __launch_bounds__(kEmitThreads)
 k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
        const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
        uint16_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_total;
+    __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
     const int64_t b = blockIdx.x;
     if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, nullptr, &t_total);
     __syncthreads();
@@ -284,31 +315,76 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
         atomicMax(&flags[kFlagMaxTile], t_total);
         atomicMax(&flags[kFlagMaxRows], i1 - i0);
     }
-    const bool fits = t_total <= kMaxTileAtoms;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        if (!fits) {
-            cnt[i] = 0;
-            continue;
-        }
-        int cx, cy, cz;
-        cell_coords(g, cell_s[i], cx, cy, cz);
+    const int dx = 2 * a.rx + 1, dy = 2 * a.ry + 1, dz = 2 * a.rz + 1;
+    const int ncand = dx * dy * dz;
+    const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
+    const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
+    for (int t = threadIdx.x; t < g.bvol * ncand; t += blockDim.x) {
+        const int lc = t / ncand, kk = t - lc * ncand;
+        const int lz = lc % g.B[2], ly = (lc / g.B[2]) % g.B[1], lx = lc / (g.B[2] * g.B[1]);
+        const int cx = bx * g.B[0] + lx, cy = by * g.B[1] + ly, cz = bz * g.B[2] + lz;
+        const int ox = kk / (dy * dz) - a.rx, oy = (kk / dz) % dy - a.ry, oz = kk % dz - a.rz;
+        const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
+        const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
+        const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
+        const int tx = floor_div(ux, g.B[0]) - bx + g.br[0];
+        const int ty = floor_div(uy, g.B[1]) - by + g.br[1];
+        const int tz = floor_div(uz, g.B[2]) - bz + g.br[2];
+        const int cn = cell_index(g, wx, wy, wz);
+        ctab[lc][kk] = make_int4(cell_start[cn], cell_start[cn + 1],
+                                 t_base[(tx * g.td[1] + ty) * g.td[2] + tz],
+                                 (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2));
+    }
+    __syncthreads();
+    if (t_total > kMaxTileAtoms) {
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) cnt[i] = 0;
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int s = lane % kEmitLanes;
+    const int nrows = i1 - i0;
+    const int rows_per_warp = 32 / kEmitLanes;
+    for (int r0 = warp * rows_per_warp; r0 < nrows; r0 += nw * rows_per_warp) {
+        const int r = r0 + lane / kEmitLanes;
+        const bool act = r < nrows;
+        const int i = i0 + (act ? r : 0);
+        const int4 *tab = ctab[act ? cell_s[i] - (int)(b * g.bvol) : 0];
         const double4_32a xi = xs64[i];
         const float4 xf = xs32[i];
-        int shell[kShells];
+        ShellCount sc;
+        if (act) emit_stream<false>(a, i, s, tab, ncand, xi, xf, xs64, xs32, sc, nbr);
+        // row totals per shell and this lane's first slot in each shell
+        unsigned long long plo = sc.lo, phi = sc.hi;  // inclusive prefix over the row's lanes
 #pragma unroll
-        for (int k = 0; k < kShells; ++k) shell[k] = 0;
-        emit_sweep<false>(a, g, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, t_base, shell, nbr);
-        // shell counts -> first slot of each shell
-        int count = 0;
+        for (int o = 1; o < kEmitLanes; o <<= 1) {
+            const unsigned long long ylo = __shfl_up_sync(0xffffffffu, plo, o);
+            const unsigned long long yhi = __shfl_up_sync(0xffffffffu, phi, o);
+            if (s >= o) {
+                plo += ylo;
+                phi += yhi;
+            }
+        }
+        const int last = (lane / kEmitLanes) * kEmitLanes + kEmitLanes - 1;
+        ShellCount tot;
+        tot.lo = __shfl_sync(0xffffffffu, plo, last);
+        tot.hi = __shfl_sync(0xffffffffu, phi, last);
+        ShellCount start;
+        int base = 0;
 #pragma unroll
         for (int k = 0; k < kShells; ++k) {
-            const int c_k = shell[k];
-            shell[k] = count;
-            count += c_k;
+            const int mine = sc.get(k);
+            const int before = (int)((((k < 4 ? plo : phi) >> (16 * (k & 3))) & 0xffffu)) - mine;
+            const unsigned long long v = (unsigned long long)(base + before) << (16 * (k & 3));
+            if (k < 4) start.lo |= v; else start.hi |= v;
+            base += tot.get(k);
         }
-        emit_sweep<true>(a, g, i, cx, cy, cz, xi, xf, xs64, xs32, cell_start, t_base, shell, nbr);
-        cnt[i] = min(count, a.width);
-        if (count > a.width) atomicMax(&flags[kFlagMaxRow], count);
+        if (act) {
+            emit_stream<true>(a, i, s, tab, ncand, xi, xf, xs64, xs32, start, nbr);
+            if (s == 0) {
+                cnt[i] = min(base, a.width);
+                if (base > a.width) atomicMax(&flags[kFlagMaxRow], base);
+            }
+        }
     }
 }
 
