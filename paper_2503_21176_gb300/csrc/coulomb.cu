@@ -141,6 +141,10 @@ constexpr size_t kSmemPerBlock = 232448;
 constexpr size_t kReal32SmemMax = kSmemPerBlock - 4096;
 constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096 - sizeof(double) * kErfcPieces * kErfcCoef;
 
+// Brick spreading: block size and the largest shared-memory window it takes.
+constexpr int kSpreadThreads = 128;
+constexpr size_t kSpreadSmemMax = 48 * 1024;
+
 int real_block_threads(int max_rows) {
     int t = (kTPR * std::max(1, max_rows) + 31) / 32 * 32;
     return std::min(kRealMaxThreads, std::max(64, t));
@@ -567,6 +571,109 @@ k_spread(int n, const int4 *__restrict__ sbase, const typename V4<T>::type *__re
     }
 }
 
+// Vector reduction of four adjacent floats (sm_90+): one L2 atomic for 16 bytes.
+// p must be 16-byte aligned.
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+                 "f"(d)
+                 : "memory");
+}
+
+// Brick-window spreading.  One block per brick: the brick's atoms add their
+// p^3 weights into a shared-memory window of the mesh that covers the brick
+// plus the spline support (atomics in shared memory), and the block then adds
+// the window into the global mesh, four z-points per vector reduction where
+// the row is 16-byte aligned and does not wrap.  The window origin of brick
+// (bx, by, bz) is floor(b_d X_d) - P per axis, X_d = B_d cw_d K_d / L_d (one
+// mesh point of margin below and above against rounding of floor(K x / L));
+// z is rounded down to a multiple of 4.  An atom whose support leaves the
+// window (not expected) adds straight into the global mesh.
+struct SpreadWin {
+    int K0, K1, K2;
+    int E0, E1, E2;      // window extent (E2 a multiple of 4)
+    double X0, X1, X2;   // mesh points per brick and axis
+    int vec;             // K2 % 4 == 0: vector flush allowed
+};
+
+template <typename T, int P>
+__device__ __forceinline__ void spread_atom_global(const int4 &b, const T (&Mx)[P], const T (&My)[P],
+                                                   const T (&Mz)[P], T q, const SpreadWin &w,
+                                                   T *__restrict__ mesh) {
+    for (int aa = 0; aa < P; ++aa) {
+        const int ix = wrap_index(b.x - aa, w.K0);
+        for (int bb = 0; bb < P; ++bb) {
+            const int iy = wrap_index(b.y - bb, w.K1);
+            T *row = mesh + ((size_t)ix * w.K1 + iy) * w.K2;
+            for (int c = 0; c < P; ++c) atomicAdd(row + wrap_index(b.z - c, w.K2), q * Mx[aa] * My[bb] * Mz[c]);
+        }
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
+               const int4 *__restrict__ sbase, const typename V4<T>::type *__restrict__ sfrac,
+               T *__restrict__ mesh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *win = (T *)smem_raw;
+    const int64_t b = blockIdx.x;
+    const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
+    const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
+    const int lo0 = (int)floor(bx * w.X0) - P, lo1 = (int)floor(by * w.X1) - P;
+    const int lo2 = ((int)floor(bz * w.X2) - P) & ~3;
+    const int nwin = w.E0 * w.E1 * w.E2;
+    for (int t = threadIdx.x; t < nwin; t += blockDim.x) win[t] = T(0);
+    __syncthreads();
+    const int a0 = cell_start[b * g.bvol], a1 = cell_start[(b + 1) * g.bvol];
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+        const int4 bs = sbase[i];
+        const auto f = sfrac[i];
+        T Mx[P], My[P], Mz[P], dummy[P];
+        bspline<T, P, false>(f.x, Mx, dummy);
+        bspline<T, P, false>(f.y, My, dummy);
+        bspline<T, P, false>(f.z, Mz, dummy);
+        const int lx = bs.x - lo0, ly = bs.y - lo1, lz = bs.z - lo2;
+        if (lx < P - 1 || lx >= w.E0 || ly < P - 1 || ly >= w.E1 || lz < P - 1 || lz >= w.E2) {
+            spread_atom_global<T, P>(bs, Mx, My, Mz, f.w, w, mesh);
+            continue;
+        }
+#pragma unroll
+        for (int aa = 0; aa < P; ++aa) {
+            const T qa = f.w * Mx[aa];
+#pragma unroll
+            for (int bb = 0; bb < P; ++bb) {
+                const T qab = qa * My[bb];
+                T *row = win + ((lx - aa) * w.E1 + (ly - bb)) * w.E2 + lz;
+#pragma unroll
+                for (int c = 0; c < P; ++c) atomicAdd(row - c, qab * Mz[c]);
+            }
+        }
+    }
+    __syncthreads();
+    // flush: chunks of 4 z-points of each window row
+    const int nq = w.E2 / 4;
+    for (int t = threadIdx.x; t < w.E0 * w.E1 * nq; t += blockDim.x) {
+        const int k = t % nq, row = t / nq;
+        const int iy = row % w.E1, ix = row / w.E1;
+        const T *src = win + (size_t)row * w.E2 + 4 * k;
+        const T v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
+        if (v0 == T(0) && v1 == T(0) && v2 == T(0) && v3 == T(0)) continue;
+        const int mx = wrap_index(lo0 + ix, w.K0), my = wrap_index(lo1 + iy, w.K1);
+        const int mz = lo2 + 4 * k;
+        T *dst = mesh + ((size_t)mx * w.K1 + my) * w.K2;
+        if constexpr (std::is_same<T, float>::value) {
+            if (w.vec && mz >= 0 && mz + 4 <= w.K2) {
+                red_add_v4(dst + mz, v0, v1, v2, v3);
+                continue;
+            }
+        }
+        const T vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (vv[c] != T(0)) atomicAdd(dst + wrap_index(mz + c, w.K2), vv[c]);
+    }
+}
+
 // Q^ *= G on the half spectrum; partial sums of the mesh energy 1/2 sum_full G |Q^|^2,
 // where every half-spectrum point stands for itself and its mirror except on the
 // planes m3 = 0 and (K3 even) m3 = K3/2.  Grid-stride over the flat half spectrum;
@@ -771,8 +878,41 @@ std::vector<double> erfc_table() {
     return out;
 }
 
+// Shared-memory window of the brick spreading, or nbytes = 0 when it exceeds
+// kSpreadSmemMax (a box of very few bricks against a fine mesh): then the
+// one-thread-per-atom global spreading runs instead.
+SpreadWin spread_window(const qeq_ctx *ctx, int P, size_t elem, size_t *nbytes) {
+    SpreadWin w;
+    w.K0 = ctx->K[0];
+    w.K1 = ctx->K[1];
+    w.K2 = ctx->K[2];
+    const BrickGeom &g = ctx->geom;
+    const double X[3] = {g.B[0] * ctx->cw[0] * ctx->K[0] / ctx->p.box[0],
+                         g.B[1] * ctx->cw[1] * ctx->K[1] / ctx->p.box[1],
+                         g.B[2] * ctx->cw[2] * ctx->K[2] / ctx->p.box[2]};
+    w.X0 = X[0];
+    w.X1 = X[1];
+    w.X2 = X[2];
+    // floor((b + 1) X) - floor(b X) <= ceil(X); P - 1 support points below, one
+    // margin point on each side, and up to 3 more below z from the alignment
+    w.E0 = (int)std::ceil(X[0]) + P + 2;
+    w.E1 = (int)std::ceil(X[1]) + P + 2;
+    w.E2 = ((int)std::ceil(X[2]) + P + 2 + 3 + 3) / 4 * 4;
+    w.vec = ctx->K[2] % 4 == 0;
+    const size_t bytes = elem * w.E0 * w.E1 * w.E2;
+    *nbytes = bytes <= kSpreadSmemMax ? bytes : 0;
+    return w;
+}
+
 template <typename T, int P>
 void launch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s) {
+    size_t bytes = 0;
+    const SpreadWin w = spread_window(ctx, P, sizeof(T), &bytes);
+    if (bytes) {
+        k_spread_brick<T, P><<<(unsigned)ctx->geom.nbricks, kSpreadThreads, bytes, s>>>(
+            w, ctx->geom, ctx->cell_start, sb, (const typename V4<T>::type *)sf, (T *)ctx->mesh);
+        return;
+    }
     k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
         (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
         (T *)ctx->mesh);

@@ -196,3 +196,56 @@ def test_fp64_explicit_ewald_matches_oracle(n_mol, box_scale):
     s.close()
     with pytest.raises(qg.QeqError):
         qg.System(qg.make_params(w.n_atoms, w.box, recip="ewald", precision="fp32_mixed"))
+
+
+def _dense_small_box(seed):
+    """1000 atoms on a jittered 10^3 lattice in an 8 A cube (about 20x water density)."""
+    from workloads import simple_cubic_lattice
+
+    rng = np.random.default_rng(seed)
+    R, L = simple_cubic_lattice(10, 0.8)
+    R = R + rng.uniform(-0.1, 0.1, size=R.shape)
+
+    class W:
+        pass
+
+    w = W()
+    w.R, w.box, w.n_atoms = R, np.array([L, L, L]), len(R)
+    w.sigma = np.where(np.arange(len(R)) % 3 == 0, 0.7, 0.45)
+    return w
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_dense_small_box_global_tiles(precision):
+    """Tiles larger than shared memory: the real-space kernels stage them in global scratch.
+
+    r_list 5.6 in an 8 A box gives 2 cells of 4 A per axis, bricks of one cell
+    and a tile of 5^3 cell images: 125 x 1000 / 8 = 15,625 atoms, beyond the
+    5,200 (FP64) and 11,400 (FP32) atoms that shared memory holds.  The
+    neighbour set is also compared exactly with the brute-force search.
+    """
+    from gpu_util import canonical_rows_gpu, canonical_rows_oracle
+    from oracle import neighbors
+
+    qg = cuda_or_skip()
+    w = _dense_small_box(12)
+    q = random_neutral_charges(w.n_atoms, seed=4, scale=0.3)
+    mesh = (16, 16, 16)
+    p = qg.make_params(w.n_atoms, w.box, alpha=0.5, r_cut=5.0, skin=0.6, mesh=mesh, order=4,
+                       precision=precision)
+    s = qg.System(p)
+    R = dev_tensor(w.R)
+    s.neighbor_build(R)
+    counts, nbr, shift = s.neighbor_export()
+    off, j, sh = neighbors.brute_force_pairs(w.R, w.box, 5.6)
+    assert canonical_rows_gpu(counts, nbr, shift) == canonical_rows_oracle(off, j, sh)
+    v, E, F, en = s.apply(R, dev_tensor(q), dev_tensor(w.sigma))
+    g = {"v": v.cpu().numpy().copy(), "E": E.cpu().numpy().copy(), "F": F.cpu().numpy().copy(),
+         "energy": en.cpu().numpy().copy()}
+    s.close()
+    o = _oracle(w, q, 0.5, 5.0, mesh, 4)
+    if precision == "fp64":
+        _check64(g, o)
+    else:
+        assert np.sqrt(np.mean((g["F"] - o["F"]) ** 2) / np.mean(o["F"] ** 2)) < 1e-4
+        assert rel_max(g["v"], o["v"]) < 1e-5
