@@ -581,18 +581,27 @@ __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, 
 
 // Brick-window spreading.  One block per brick: the brick's atoms add their
 // p^3 weights into a shared-memory window of the mesh that covers the brick
-// plus the spline support (atomics in shared memory), and the block then adds
-// the window into the global mesh, four z-points per vector reduction where
-// the row is 16-byte aligned and does not wrap.  The window origin of brick
-// (bx, by, bz) is floor(b_d X_d) - P per axis, X_d = B_d cw_d K_d / L_d (one
-// mesh point of margin below and above against rounding of floor(K x / L));
-// z is rounded down to a multiple of 4.  An atom whose support leaves the
-// window (not expected) adds straight into the global mesh.
+// plus the spline support, and the block then adds the window into the global
+// mesh, four z-points per vector reduction where the row is 16-byte aligned and
+// does not wrap.  The window accumulates in 32-bit fixed point: integer shared
+// atomics are native, and ran the 300,000-atom spread in 46 us against 66 us
+// with float shared atomics (64-bit integers: 101 us).  A contribution
+// q Mx My Mz becomes round(scale q Mx My Mz), scale = 2^k the largest power of
+// two with scale wmax sum_brick |q| < 2^30, where wmax >= Mx My Mz is the
+// largest weight of one mesh point: no window point can overflow.  The sums are
+// exact and independent of the atomic order; the resolution is
+// wmax sum |q| / 2^30 (about 7e-9 e for a 73-atom water brick with charges of
+// 0.3 e).  The window origin of brick (bx, by, bz) is floor(b_d X_d) - P per
+// axis, X_d = B_d cw_d K_d / L_d (one mesh point of margin below and above
+// against rounding of floor(K x / L)); z is rounded down to a multiple of 4.
+// An atom whose support leaves the window (not expected) adds straight into
+// the global mesh.
 struct SpreadWin {
     int K0, K1, K2;
     int E0, E1, E2;      // window extent (E2 a multiple of 4)
     double X0, X1, X2;   // mesh points per brick and axis
     int vec;             // K2 % 4 == 0: vector flush allowed
+    float wmax;          // upper bound of one atom's weight at one mesh point
 };
 
 template <typename T, int P>
@@ -609,68 +618,81 @@ __device__ __forceinline__ void spread_atom_global(const int4 &b, const T (&Mx)[
     }
 }
 
-template <typename T, int P>
+template <int P>
 __global__ void __launch_bounds__(kSpreadThreads)
 k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
-               const int4 *__restrict__ sbase, const typename V4<T>::type *__restrict__ sfrac,
-               T *__restrict__ mesh) {
+               const int4 *__restrict__ sbase, const float4 *__restrict__ sfrac,
+               float *__restrict__ mesh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *win = (T *)smem_raw;
+    int *win = (int *)smem_raw;
+    __shared__ float qsum_w[kSpreadThreads / 32];
     const int64_t b = blockIdx.x;
     const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
     const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
     const int lo0 = (int)floor(bx * w.X0) - P, lo1 = (int)floor(by * w.X1) - P;
     const int lo2 = ((int)floor(bz * w.X2) - P) & ~3;
     const int nwin = w.E0 * w.E1 * w.E2;
-    for (int t = threadIdx.x; t < nwin; t += blockDim.x) win[t] = T(0);
-    __syncthreads();
     const int a0 = cell_start[b * g.bvol], a1 = cell_start[(b + 1) * g.bvol];
+    float qs = 0.f;
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) qs += fabsf(sfrac[i].w);
+    for (int t = threadIdx.x; t < nwin; t += blockDim.x) win[t] = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
+    if ((threadIdx.x & 31) == 0) qsum_w[threadIdx.x >> 5] = qs;
+    __syncthreads();
+    float qsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSpreadThreads / 32; ++k) qsum += qsum_w[k];
+    // scale = 2^(30 - e) with wmax qsum < 2^e (rounded up by 1e-5 relative)
+    int e2;
+    frexpf(fmaxf(qsum * w.wmax * 1.00001f, 1e-30f), &e2);
+    const int sh = min(126, 30 - e2);
+    const float scale = ldexpf(1.f, sh);
     for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
         const int4 bs = sbase[i];
-        const auto f = sfrac[i];
-        T Mx[P], My[P], Mz[P], dummy[P];
-        bspline<T, P, false>(f.x, Mx, dummy);
-        bspline<T, P, false>(f.y, My, dummy);
-        bspline<T, P, false>(f.z, Mz, dummy);
+        const float4 f = sfrac[i];
+        float Mx[P], My[P], Mz[P], dummy[P];
+        bspline<float, P, false>(f.x, Mx, dummy);
+        bspline<float, P, false>(f.y, My, dummy);
+        bspline<float, P, false>(f.z, Mz, dummy);
         const int lx = bs.x - lo0, ly = bs.y - lo1, lz = bs.z - lo2;
         if (lx < P - 1 || lx >= w.E0 || ly < P - 1 || ly >= w.E1 || lz < P - 1 || lz >= w.E2) {
-            spread_atom_global<T, P>(bs, Mx, My, Mz, f.w, w, mesh);
+            spread_atom_global<float, P>(bs, Mx, My, Mz, f.w, w, mesh);
             continue;
         }
+        const float qsc = f.w * scale;
 #pragma unroll
         for (int aa = 0; aa < P; ++aa) {
-            const T qa = f.w * Mx[aa];
+            const float qa = qsc * Mx[aa];
 #pragma unroll
             for (int bb = 0; bb < P; ++bb) {
-                const T qab = qa * My[bb];
-                T *row = win + ((lx - aa) * w.E1 + (ly - bb)) * w.E2 + lz;
+                const float qab = qa * My[bb];
+                int *row = win + ((lx - aa) * w.E1 + (ly - bb)) * w.E2 + lz;
 #pragma unroll
-                for (int c = 0; c < P; ++c) atomicAdd(row - c, qab * Mz[c]);
+                for (int c = 0; c < P; ++c) atomicAdd(row - c, __float2int_rn(qab * Mz[c]));
             }
         }
     }
     __syncthreads();
-    // flush: chunks of 4 z-points of each window row
+    // flush: chunks of 4 z-points of each window row, back to FP32 (x 2^-sh)
     const int nq = w.E2 / 4;
     for (int t = threadIdx.x; t < w.E0 * w.E1 * nq; t += blockDim.x) {
         const int k = t % nq, row = t / nq;
         const int iy = row % w.E1, ix = row / w.E1;
-        const T *src = win + (size_t)row * w.E2 + 4 * k;
-        const T v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
-        if (v0 == T(0) && v1 == T(0) && v2 == T(0) && v3 == T(0)) continue;
+        const int4 iv = *(const int4 *)(win + (size_t)row * w.E2 + 4 * k);
+        if ((iv.x | iv.y | iv.z | iv.w) == 0) continue;
+        const float vv[4] = {ldexpf((float)iv.x, -sh), ldexpf((float)iv.y, -sh),
+                             ldexpf((float)iv.z, -sh), ldexpf((float)iv.w, -sh)};
         const int mx = wrap_index(lo0 + ix, w.K0), my = wrap_index(lo1 + iy, w.K1);
         const int mz = lo2 + 4 * k;
-        T *dst = mesh + ((size_t)mx * w.K1 + my) * w.K2;
-        if constexpr (std::is_same<T, float>::value) {
-            if (w.vec && mz >= 0 && mz + 4 <= w.K2) {
-                red_add_v4(dst + mz, v0, v1, v2, v3);
-                continue;
-            }
+        float *dst = mesh + ((size_t)mx * w.K1 + my) * w.K2;
+        if (w.vec && mz >= 0 && mz + 4 <= w.K2) {
+            red_add_v4(dst + mz, vv[0], vv[1], vv[2], vv[3]);
+            continue;
         }
-        const T vv[4] = {v0, v1, v2, v3};
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (vv[c] != T(0)) atomicAdd(dst + wrap_index(mz + c, w.K2), vv[c]);
+            if (vv[c] != 0.f) atomicAdd(dst + wrap_index(mz + c, w.K2), vv[c]);
     }
 }
 
@@ -878,6 +900,25 @@ std::vector<double> erfc_table() {
     return out;
 }
 
+// M_P(P / 2), the peak of the cardinal B-spline of order P, by the same order
+// recursion as bspline_mod2 (evaluated at the midpoint).
+double bspline_peak(int P) {
+    std::vector<double> M(P + 1, 0.0);  // M[j] = M_n(j + f) for the fraction f
+    const double f = (P % 2 == 0) ? 0.0 : 0.5;  // P / 2 = j + f
+    M[0] = f;
+    M[1] = 1.0 - f;
+    for (int n = 3; n <= P; ++n) {
+        for (int j = n - 1; j >= 0; --j) {
+            const double left = (j < n - 1) ? M[j] : 0.0;
+            const double right = (j >= 1) ? M[j - 1] : 0.0;
+            M[j] = ((f + j) * left + (n - f - j) * right) / (n - 1);
+        }
+    }
+    double peak = 0.0;
+    for (int j = 0; j < P; ++j) peak = std::max(peak, M[j]);
+    return peak * (1.0 + 1e-6);
+}
+
 // Shared-memory window of the brick spreading, or nbytes = 0 when it exceeds
 // kSpreadSmemMax (a box of very few bricks against a fine mesh): then the
 // one-thread-per-atom global spreading runs instead.
@@ -899,6 +940,8 @@ SpreadWin spread_window(const qeq_ctx *ctx, int P, size_t elem, size_t *nbytes) 
     w.E1 = (int)std::ceil(X[1]) + P + 2;
     w.E2 = ((int)std::ceil(X[2]) + P + 2 + 3 + 3) / 4 * 4;
     w.vec = ctx->K[2] % 4 == 0;
+    // largest cardinal B-spline value M_P(P / 2), cubed: one atom's largest weight
+    w.wmax = (float)std::pow(bspline_peak(P), 3);
     const size_t bytes = elem * w.E0 * w.E1 * w.E2;
     *nbytes = bytes <= kSpreadSmemMax ? bytes : 0;
     return w;
@@ -906,12 +949,14 @@ SpreadWin spread_window(const qeq_ctx *ctx, int P, size_t elem, size_t *nbytes) 
 
 template <typename T, int P>
 void launch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s) {
-    size_t bytes = 0;
-    const SpreadWin w = spread_window(ctx, P, sizeof(T), &bytes);
-    if (bytes) {
-        k_spread_brick<T, P><<<(unsigned)ctx->geom.nbricks, kSpreadThreads, bytes, s>>>(
-            w, ctx->geom, ctx->cell_start, sb, (const typename V4<T>::type *)sf, (T *)ctx->mesh);
-        return;
+    if constexpr (std::is_same<T, float>::value) {
+        size_t bytes = 0;
+        const SpreadWin w = spread_window(ctx, P, sizeof(int), &bytes);
+        if (bytes) {
+            k_spread_brick<P><<<(unsigned)ctx->geom.nbricks, kSpreadThreads, bytes, s>>>(
+                w, ctx->geom, ctx->cell_start, sb, (const float4 *)sf, (float *)ctx->mesh);
+            return;
+        }
     }
     k_spread<T, P><<<grid_for(ctx->n), kThreads, 0, s>>>(
         (int)ctx->n, sb, (const typename V4<T>::type *)sf, ctx->K[0], ctx->K[1], ctx->K[2],
