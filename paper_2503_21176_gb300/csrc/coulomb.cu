@@ -117,7 +117,7 @@ __device__ __forceinline__ double erfc_pw(const double *__restrict__ tab, double
 // Lanes per neighbour row.  kTPR consecutive lanes share one row: lane s takes
 // the row's entries s, s + kTPR, ..., which the list stores next to each other
 // (kListGroup), and their partial sums are combined with warp shuffles.
-constexpr int kTPR = kListGroup;
+constexpr int kTPR = kListLanes;
 // One block per brick; its blockDim is kTPR x (largest brick, rounded to warps),
 // at most kRealMaxThreads.  Larger bricks take several passes.
 constexpr int kRealMaxThreads = 512;
@@ -150,17 +150,25 @@ int real_block_threads(int max_rows) {
     return std::min(kRealMaxThreads, std::max(64, t));
 }
 
-// Stage the tile of brick blockIdx.x: warp 0 builds the tile table, then the
-// warps copy the tile bricks (positions shifted by their periodic image, and
-// sigma) into tile[] / tsg[].  Returns the tile size, or -1 when it exceeds cap
-// (the whole block then skips the brick and raises kFlagTileOverflow).
+// Stage the tile of brick blockIdx.x: load its tile table (written by the
+// neighbour build), then the warps copy the tile bricks (positions shifted by
+// their periodic image, and sigma) into tile[] / tsg[].  Returns the tile size,
+// or -1 when it exceeds cap (the whole block then skips the brick and raises
+// kFlagTileOverflow).
 template <typename T4, typename T>
-__device__ __forceinline__ int stage_tile(const BrickGeom &g, const int32_t *__restrict__ cell_start,
+__device__ __forceinline__ int stage_tile(const BrickGeom &g, const int4 *__restrict__ tile_tab,
+                                          const int32_t *__restrict__ tile_tot,
                                           const T4 *__restrict__ xq, const T *__restrict__ sg,
                                           T Lx, T Ly, T Lz, int cap, T4 *tile, T *tsg, int *t_start,
                                           int *t_base, int *t_code, int *t_total,
                                           int32_t *__restrict__ flags) {
-    if (threadIdx.x < 32) tile_table(g, blockIdx.x, cell_start, t_start, t_base, t_code, t_total);
+    for (int rb = threadIdx.x; rb < g.T; rb += blockDim.x) {
+        const int4 e = tile_tab[(int64_t)blockIdx.x * g.T + rb];
+        t_start[rb] = e.x;
+        t_base[rb] = e.y;
+        t_code[rb] = e.z;
+    }
+    if (threadIdx.x == 0) *t_total = tile_tot[blockIdx.x];
     __syncthreads();
     const int total = *t_total;
     if (total > cap) {
@@ -201,7 +209,7 @@ __device__ __forceinline__ void home_rows(const BrickGeom &g, const int *t_start
 // slice of a global scratch buffer instead), kTPR lanes per row.
 template <bool FIELD, bool GTILE>
 __global__ void __launch_bounds__(kRealMaxThreads, 2)
-k_real64(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
+k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32_t *__restrict__ tile_tot,
          const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const double4_32a *__restrict__ xq, const double *__restrict__ sg,
          const double *__restrict__ erfc_tab, int cap, unsigned char *__restrict__ gtile,
@@ -213,7 +221,7 @@ k_real64(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
     double4_32a *tile = (double4_32a *)base;
     double *tsg = (double *)(base + (size_t)cap * 32);
     for (int t = threadIdx.x; t < kErfcPieces * kErfcCoef; t += blockDim.x) tab[t] = erfc_tab[t];
-    const int total = stage_tile<double4_32a, double>(g, cell_start, xq, sg, a.Lx, a.Ly, a.Lz, cap,
+    const int total = stage_tile<double4_32a, double>(g, tile_tab, tile_tot, xq, sg, a.Lx, a.Ly, a.Lz, cap,
                                                      tile, tsg, t_start, t_base, t_code, &t_total,
                                                      flags);
     if (total < 0) return;
@@ -385,12 +393,6 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, c
     }
 }
 
-// Unroll of the FP32 real-space entry loop: four independent pair evaluations
-// in flight per lane hide the SFU and shared-memory latencies (0.243 ms against
-// 0.297 ms without unrolling, 300,000 atoms).
-#ifndef QEQ_REAL_UNROLL
-#define QEQ_REAL_UNROLL 4
-#endif
 
 // FP32 real space, one block per brick: the tile (float4 positions with q, and
 // sigma) in shared memory (GTILE: in the block's slice of a global scratch
@@ -400,7 +402,7 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, c
 // (written by the gather of the same apply).
 template <bool FIELD, bool GTILE>
 __global__ void __launch_bounds__(kRealMaxThreads, QEQ_REAL_MIN_BLOCKS)
-k_real32(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
+k_real32(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32_t *__restrict__ tile_tot,
          const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const float4 *__restrict__ xq, const float *__restrict__ sg,
          const int32_t *__restrict__ smax_bits, int cap, unsigned char *__restrict__ gtile,
@@ -410,13 +412,13 @@ k_real32(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
     unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile32Bytes : smem_raw;
     float4 *tile = (float4 *)base;
     float *tsg = (float *)(base + (size_t)cap * 16);
-    const int total = stage_tile<float4, float>(g, cell_start, xq, sg, a.Lx_f, a.Ly_f, a.Lz_f, cap,
+    const int total = stage_tile<float4, float>(g, tile_tab, tile_tot, xq, sg, a.Lx_f, a.Ly_f, a.Lz_f, cap,
                                                 tile, tsg, t_start, t_base, t_code, &t_total, flags);
     if (total < 0) return;
     int i0, offc, nrows;
     home_rows(g, t_start, t_base, total, i0, offc, nrows);
     const float smax = kRealLazySigma ? __int_as_float(__ldg(smax_bits)) : 0.f;
-    const size_t step = (size_t)kTPR * a.n;  // one list group further
+    const size_t wstep = (size_t)kListStripe / 4 * a.n;  // one stripe further, in 8-byte words
     const int rpp = blockDim.x / kTPR;
     for (int r0 = 0; r0 < nrows; r0 += rpp) {
         const int r = r0 + threadIdx.x / kTPR, sub = threadIdx.x % kTPR;
@@ -430,21 +432,29 @@ k_real32(RealArgs a, BrickGeom g, const int32_t *__restrict__ cell_start,
             // every pair checks sigma_j when max |sigma| is unknown
             const float gpre = kRealLazySigma ? 25.0001f * fmaf(smax, smax, si2) : 3.4e38f;
             const int c = cnt[i];
-            // e1: entry of the current iteration, e2: the next one, loaded ahead
-            // so that the DRAM latency of the list stream overlaps the pair math.
-            // Entries past the row end read as 0 (tile slot 0: never evaluated).
-            const uint16_t *pk = nbr + list_index(sub, i, a.n);
-            int e1 = sub < c ? __ldg(pk) : 0;
-            int e2 = sub + kTPR < c ? __ldg(pk + step) : 0;
-            QEQ_UNROLL(QEQ_REAL_UNROLL)
-            for (int k = sub; k < c; k += kTPR) {
-                const int e = e1;
-                e1 = e2;
-                pk += step;
-                e2 = k + 2 * kTPR < c ? __ldg(pk + step) : 0;
-                const float4 xc = tile[e];
-                pair32<FIELD>(xc.x - xi.x, xc.y - xi.y, xc.z - xi.z, xc.w, tsg + e, si2, gpre,
-                              a.pal_f, a.c1_f, a.rc2_f, a.tspa_f, tv, tx, ty, tz);
+            // This lane's entries come 4 to an 8-byte word, one word per list
+            // stripe; w0 holds the current word and w1 the next, loaded ahead so
+            // that the DRAM latency of the list stream overlaps the pair math.
+            const int cl = c > sub ? (c - sub + kTPR - 1) / kTPR : 0;
+            const uint2 *pw = (const uint2 *)(nbr + list_index(sub, i, a.n));
+            uint2 w0 = cl > 0 ? __ldg(pw) : make_uint2(0u, 0u);
+            uint2 w1 = cl > 4 ? __ldg(pw + wstep) : make_uint2(0u, 0u);
+            for (int t = 0; t < cl; t += 4) {
+                const uint2 cur = w0;
+                w0 = w1;
+                pw += wstep;
+                w1 = t + 8 < cl ? __ldg(pw + wstep) : make_uint2(0u, 0u);
+                const int ev[4] = {(int)(cur.x & 0xffffu), (int)(cur.x >> 16), (int)(cur.y & 0xffffu),
+                                   (int)(cur.y >> 16)};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (t + u < cl) {
+                        const int e = ev[u];
+                        const float4 xc = tile[e];
+                        pair32<FIELD>(xc.x - xi.x, xc.y - xi.y, xc.z - xi.z, xc.w, tsg + e, si2,
+                                      gpre, a.pal_f, a.c1_f, a.rc2_f, a.tspa_f, tv, tx, ty, tz);
+                    }
+                }
             }
         }
 #pragma unroll
@@ -1060,25 +1070,25 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
             auto *x4 = (const double4_32a *)xq;
             auto *s1 = (const double *)sg;
             if (need_field && !L.gtile)
-                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (need_field)
-                k_real64<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (!L.gtile)
-                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else
-                k_real64<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
         } else {
             auto *x4 = (const float4 *)xq;
             auto *s1 = (const float *)sg;
             const int32_t *sm = ctx->d_flags + kFlagSigmaMax;
             if (need_field && !L.gtile)
-                k_real32<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (need_field)
-                k_real32<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (!L.gtile)
-                k_real32<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else
-                k_real32<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->cell_start, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
         }
     }
 

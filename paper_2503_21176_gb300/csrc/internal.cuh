@@ -137,13 +137,17 @@ __host__ __device__ __forceinline__ int64_t tile_brick(const BrickGeom &g, int64
     return brick_index(g, w[0], w[1], w[2]);
 }
 
-// List layout: row i (sorted) keeps its entry k at list_index(k, i, n).  Entries
-// come in groups of kListGroup per row, rows interleaved group by group
-// ([width / 4][N][4]), so the 4 lanes that share a row in the real-space kernel
-// read 4 adjacent entries and a warp's 8 rows one contiguous 64-byte span.
-constexpr int kListGroup = 4;
+// List layout: row i (sorted) keeps its entry k at list_index(k, i, n).  The
+// real-space kernels give a row kListLanes lanes, lane s taking the entries
+// k = s, s + 4, s + 8, ...  Rows are stored in stripes of kListStripe = 16
+// entries ([width / 16][N][16]); inside a stripe, lane s's 4 entries are
+// adjacent (one 8-byte load), and a warp's 8 rows read one contiguous 256-byte
+// span per stripe.  The width is a multiple of 16.
+constexpr int kListLanes = 4;
+constexpr int kListStripe = 16;
 __host__ __device__ __forceinline__ size_t list_index(int k, int64_t i, int64_t n) {
-    return (((size_t)(k / kListGroup) * n + i) * kListGroup) + (k % kListGroup);
+    return ((size_t)(k / kListStripe) * n + i) * kListStripe + (k % kListLanes) * 4 +
+           (k / kListLanes) % 4;
 }
 
 // Tile table of brick b, built by one warp (all 32 lanes): for every tile brick
@@ -275,6 +279,8 @@ struct qeq_ctx {
     // largest tile / brick seen, in steps, so that rebuilds rarely change the
     // launch shape of a captured graph.
     int tile_cap = 0, rows_cap = 0;
+    int4 *tile_tab = nullptr;       // [nbricks][T] (first sorted atom, tile base, image code, 0)
+    int32_t *tile_tot = nullptr;    // [nbricks] tile size
     unsigned char *tile_scratch = nullptr;  // [nbricks][tile_cap] tiles when shared memory is too small
     size_t tile_scratch_bytes = 0;
     int32_t *d_flags = nullptr;     // [kNumFlags]

@@ -304,12 +304,17 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
 __global__ void __launch_bounds__(kEmitThreads)
 k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
        const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
-       uint16_t *__restrict__ nbr, int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
-    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_total;
+       uint16_t *__restrict__ nbr, int32_t *__restrict__ cnt, int4 *__restrict__ tile_tab,
+       int32_t *__restrict__ tile_tot, int32_t *__restrict__ flags) {
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
     const int64_t b = blockIdx.x;
-    if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, nullptr, &t_total);
+    if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, t_code, &t_total);
     __syncthreads();
+    // the tile table of the brick, for the real-space kernels of this list
+    for (int rb = threadIdx.x; rb < g.T; rb += blockDim.x)
+        tile_tab[b * g.T + rb] = make_int4(t_start[rb], t_base[rb], t_code[rb], 0);
+    if (threadIdx.x == 0) tile_tot[b] = t_total;
     const int i0 = t_start[g.center], i1 = cell_start[(b + 1) * g.bvol];
     if (threadIdx.x == 0) {
         atomicMax(&flags[kFlagMaxTile], t_total);
@@ -534,6 +539,8 @@ int nl_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->xs32, sizeof(float4) * n},
         {(void **)&ctx->cnt, sizeof(int32_t) * n},
         {(void **)&ctx->d_flags, sizeof(int32_t) * kNumFlags},
+        {(void **)&ctx->tile_tab, sizeof(int4) * ctx->geom.nbricks * ctx->geom.T},
+        {(void **)&ctx->tile_tot, sizeof(int32_t) * ctx->geom.nbricks},
     };
     for (auto &b : bufs) {
         int rc = dev_alloc(ctx, b.ptr, b.bytes);
@@ -547,14 +554,15 @@ int nl_alloc(qeq_ctx *ctx) {
         const double mean = 4.0 / 3.0 * kPi * ctx->rl2 * ctx->rl * (double)n / V;
         width = (int)std::ceil(1.2 * mean + 32.0);
     }
-    width = std::max(8, (width + 7) / 8 * 8);
+    width = std::max(kListStripe, (width + kListStripe - 1) / kListStripe * kListStripe);
     return nl_alloc_list(ctx, width);
 }
 
 void nl_free(qeq_ctx *ctx) {
     void *ptrs[] = {ctx->cell_of, ctx->cell_count, ctx->cell_start, ctx->cell_fill, ctx->tmp_list,
                     ctx->perm,    ctx->cell_s,     ctx->wrap_off,   ctx->R_build,   ctx->xs64,
-                    ctx->xs32,    ctx->nbr,        ctx->cnt,        ctx->d_flags};
+                    ctx->xs32,    ctx->nbr,        ctx->cnt,        ctx->d_flags,
+                    ctx->tile_tab, ctx->tile_tot};
     for (void *p : ptrs) dev_free(ctx, p);
     delete[] ctx->h_flags;
 }
@@ -573,7 +581,7 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     a.width = ctx->width;
     k_emit<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
         a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr, ctx->cnt,
-        ctx->d_flags);
+        ctx->tile_tab, ctx->tile_tot, ctx->d_flags);
 }
 
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
@@ -613,7 +621,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
         const int need = ctx->h_flags[kFlagMaxRow];
         if (need <= ctx->width) break;
         // grow (the paper's estimate-plus-buffer, Sec. 3.1) and emit again
-        rc = nl_alloc_list(ctx, (int)std::ceil(need * 1.1 / 8.0) * 8 + 8);
+        rc = nl_alloc_list(ctx, (int)std::ceil(need * 1.1 / kListStripe) * kListStripe + kListStripe);
         if (rc) {
             ctx->list_valid = false;
             return rc;
