@@ -67,6 +67,19 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
     sfrac[i] = {(T)(ux - fx), (T)(uy - fy), (T)(uz - fz), (T)qa};
 }
 
+// Charges only, for an apply at the positions of the previous one: the sorted
+// copies keep their positions, sigma and spline bases.
+template <typename T>
+__global__ void k_gather_q(int n, const int32_t *__restrict__ perm, const double *__restrict__ q,
+                           typename V4<T>::type *__restrict__ xq,
+                           typename V4<T>::type *__restrict__ sfrac) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T qa = (T)q[perm[i]];
+    xq[i].w = qa;
+    sfrac[i].w = qa;
+}
+
 // ---------------------------------------------------------------------------
 // real space (Eq. ewald_real, Gaussian-charge correction)
 // ---------------------------------------------------------------------------
@@ -1029,7 +1042,7 @@ RealLaunch real_launch(const qeq_ctx *ctx, bool f64) {
 
 template <typename T>
 int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma, double *v,
-            double *E, double *F, double *energy4, bool need_field, cudaStream_t s) {
+            double *E, double *F, double *energy4, bool need_field, bool q_only, cudaStream_t s) {
     const int n = (int)ctx->n;
     using T4 = typename V4<T>::type;
     constexpr bool f64 = std::is_same<T, double>::value;
@@ -1038,11 +1051,16 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     const qeq_params &p = ctx->p;
     ctx->applies++;
     prof_begin(ctx, kPhGatherIn, s);
-    int32_t *smax_bits = (!f64 && kRealLazySigma) ? ctx->d_flags + kFlagSigmaMax : nullptr;
-    if (smax_bits) cudaMemsetAsync(smax_bits, 0, sizeof(int32_t), s);
-    k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
-        n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
-        ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac, smax_bits);
+    if (q_only) {
+        k_gather_q<T><<<grid_for(n), kThreads, 0, s>>>(n, ctx->perm, q, xq, (T4 *)ctx->sfrac);
+    } else {
+        int32_t *smax_bits = (!f64 && kRealLazySigma) ? ctx->d_flags + kFlagSigmaMax : nullptr;
+        if (smax_bits) cudaMemsetAsync(smax_bits, 0, sizeof(int32_t), s);
+        k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
+            n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
+            ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac, smax_bits);
+        ctx->gathered = true;
+    }
     prof_end(ctx, s);
     ctx->launches++;
 
@@ -1335,10 +1353,11 @@ int erfc64_selftest(qeq_ctx *ctx, const double *x, double *out, double *dout, in
 
 int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                        double *v, double *E, double *F, double *energy4, bool need_field,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool same_R) {
     if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "coulomb_apply before neighbor_build");
-    if (ctx->fp32) return apply_t<float>(ctx, R, q, sigma, v, E, F, energy4, need_field, s);
-    return apply_t<double>(ctx, R, q, sigma, v, E, F, energy4, need_field, s);
+    const bool q_only = same_R && ctx->gathered;
+    if (ctx->fp32) return apply_t<float>(ctx, R, q, sigma, v, E, F, energy4, need_field, q_only, s);
+    return apply_t<double>(ctx, R, q, sigma, v, E, F, energy4, need_field, q_only, s);
 }
 
 }  // namespace qeq

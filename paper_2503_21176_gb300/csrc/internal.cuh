@@ -293,6 +293,7 @@ struct qeq_ctx {
     double *sg64 = nullptr;    // [N] sigma
     float4 *xq32 = nullptr;    // [N] FP32 copies
     float *sg32 = nullptr;
+    bool gathered = false;     // sorted positions / sigma / spline bases current (cleared by a build)
     double *v_s = nullptr;     // [N] real-space potential (sorted)
     double *E_s = nullptr;     // [N][3] real-space field (sorted)
     int4 *sbase = nullptr;     // [N] B-spline base mesh index floor(K x / L) (sorted)
@@ -383,9 +384,11 @@ int real_tile_reserve(qeq_ctx *ctx);
 void coulomb_free(qeq_ctx *ctx);
 // v, E, F in original numbering; E / F / energy4 may be null; need_field=false
 // skips every field computation (potential-only apply).
+// same_R: R and sigma are those of the previous apply of this context (no
+// neighbour build since), so only the charges are gathered again.
 int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                        double *v, double *E, double *F, double *energy4, bool need_field,
-                       cudaStream_t s);
+                       cudaStream_t s, bool same_R = false);
 
 // ---- explicit k-vector Ewald (ewald.cu) ----
 int ewald_alloc(qeq_ctx *ctx);

@@ -192,15 +192,17 @@ struct EmitArgs {
     float Lfx, Lfy, Lfz;
     double rl2;
     float lo, hi;
+    float t_near, t_cut;  // class thresholds on the FP32 d^2
     int width;
 };
 
-// Rows are written in 8 shells of equal volume (equal steps of d^2 / r_list^2), so
-// that the entries of a row go roughly from near to far.  Lanes that run the same
-// iteration then hold neighbours at similar distances, and the real-space kernel's
-// distance branches (cutoff test, Gaussian correction) agree across the warp.
-// Pass 0 counts each shell, pass 1 places the entries.
-constexpr int kShells = 8;
+// Rows are written in three distance classes: near (d^2 < r_list^2 / 3, where
+// the Gaussian-charge correction of the real-space sum lives for water-like
+// widths), inside the cutoff (d^2 < r_cut^2) and the skin beyond it.  Lanes that
+// run the same iteration of the real-space kernel then hold neighbours of the
+// same class, so its distance branches (cutoff test, Gaussian correction) agree
+// across the warp.  Pass 0 counts each class, pass 1 places the entries.
+constexpr int kClasses = 3;
 // Lanes per row in the emit: lane s of a row tests candidates s, s + 4, ... of
 // the row's candidate stream (its cell's (2 reach + 1)^3 neighbour cells,
 // concatenated).  Rows of one cell have the same stream, so the 8 rows of a warp
@@ -209,18 +211,14 @@ constexpr int kEmitLanes = 4;
 constexpr int kMaxBrickCells = 8;
 constexpr int kCenterCode = 62;  // image code of the zero shift
 
-// Per-lane shell counters, 16 bits a shell, shells 0-3 in lo and 4-7 in hi
-// (register-resident; a row holds at most 65535 entries, the tile limit).
-struct ShellCount {
-    unsigned long long lo = 0, hi = 0;
-    __device__ __forceinline__ void add(int shell) {
-        const unsigned long long inc = 1ull << (16 * (shell & 3));
-        lo += shell < 4 ? inc : 0ull;
-        hi += shell < 4 ? 0ull : inc;
+// Per-lane class counters, 16 bits a class in one 64-bit word (register
+// resident; a row holds at most 65535 entries, the tile limit).
+struct ClassCount {
+    unsigned long long v = 0;
+    __device__ __forceinline__ void add(int cls) {
+        v += cls == 0 ? 1ull : (cls == 1 ? (1ull << 16) : (1ull << 32));
     }
-    __device__ __forceinline__ int get(int shell) const {
-        return (int)(((shell < 4 ? lo : hi) >> (16 * (shell & 3))) & 0xffffu);
-    }
+    __device__ __forceinline__ int get(int cls) const { return (int)((v >> (16 * cls)) & 0xffffu); }
 };
 
 // The candidate stream of one lane: cell k of the table, candidate j in it.
@@ -247,9 +245,8 @@ template <bool PLACE>
 __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, const int4 *__restrict__ tab,
                                             int ncand, const double4_32a &xi, const float4 &xf,
                                             const double4_32a *__restrict__ xs64,
-                                            const float4 *__restrict__ xs32, ShellCount &sc,
+                                            const float4 *__restrict__ xs32, ClassCount &sc,
                                             uint16_t *__restrict__ nbr) {
-    const float inv_rl2 = (float)(kShells / a.rl2);
     Cursor c;
     c.k = 0;
     c.ct = tab[0];
@@ -285,12 +282,12 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
             keep = d2 < a.rl2;
         }
         if (keep) {
-            const int shell = min(kShells - 1, max(0, (int)(d2f * inv_rl2)));
+            const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
             if (PLACE) {
-                const int slot = sc.get(shell);
+                const int slot = sc.get(cls);
                 if (slot < a.width) nbr[list_index(slot, i, a.n)] = (uint16_t)(j + c.ct.z);
             }
-            sc.add(shell);
+            sc.add(cls);
         }
     }
 }
@@ -356,31 +353,24 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
         const int4 *tab = ctab[act ? cell_s[i] - (int)(b * g.bvol) : 0];
         const double4_32a xi = xs64[i];
         const float4 xf = xs32[i];
-        ShellCount sc;
+        ClassCount sc;
         if (act) emit_stream<false>(a, i, s, tab, ncand, xi, xf, xs64, xs32, sc, nbr);
-        // row totals per shell and this lane's first slot in each shell
-        unsigned long long plo = sc.lo, phi = sc.hi;  // inclusive prefix over the row's lanes
+        // row totals per class and this lane's first slot in each class
+        ClassCount incl = sc;  // inclusive prefix over the row's lanes
 #pragma unroll
         for (int o = 1; o < kEmitLanes; o <<= 1) {
-            const unsigned long long ylo = __shfl_up_sync(0xffffffffu, plo, o);
-            const unsigned long long yhi = __shfl_up_sync(0xffffffffu, phi, o);
-            if (s >= o) {
-                plo += ylo;
-                phi += yhi;
-            }
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl.v, o);
+            if (s >= o) incl.v += y;
         }
         const int last = (lane / kEmitLanes) * kEmitLanes + kEmitLanes - 1;
-        ShellCount tot;
-        tot.lo = __shfl_sync(0xffffffffu, plo, last);
-        tot.hi = __shfl_sync(0xffffffffu, phi, last);
-        ShellCount start;
+        ClassCount tot;
+        tot.v = __shfl_sync(0xffffffffu, incl.v, last);
+        ClassCount start;
         int base = 0;
 #pragma unroll
-        for (int k = 0; k < kShells; ++k) {
-            const int mine = sc.get(k);
-            const int before = (int)((((k < 4 ? plo : phi) >> (16 * (k & 3))) & 0xffffu)) - mine;
-            const unsigned long long v = (unsigned long long)(base + before) << (16 * (k & 3));
-            if (k < 4) start.lo |= v; else start.hi |= v;
+        for (int k = 0; k < kClasses; ++k) {
+            const int before = incl.get(k) - sc.get(k);
+            start.v |= (unsigned long long)(base + before) << (16 * k);
             base += tot.get(k);
         }
         if (act) {
@@ -578,6 +568,8 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     a.rl2 = ctx->rl2;
     a.lo = ctx->rl2f_lo;
     a.hi = ctx->rl2f_hi;
+    a.t_near = (float)(ctx->rl2 / 3.0);
+    a.t_cut = (float)(ctx->p.r_cut * ctx->p.r_cut);
     a.width = ctx->width;
     k_emit<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
         a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr, ctx->cnt,
@@ -586,6 +578,7 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
 
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
     const int n = (int)ctx->n;
+    ctx->gathered = false;  // the sorted order changes
     prof_begin(ctx, kPhNeighbor, s);
     ctx->launches += 5;
     cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s);

@@ -446,7 +446,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     prof_end(ctx, s);
     // 3. Phi f, E[f]
     rc = coulomb_apply_impl(ctx, st->R, ctx->fvec, prm->sigma, ctx->phi, ctx->E_f, nullptr, nullptr,
-                            true, s);
+                            true, s, true);
     if (rc) return rc;
     // 4. forces, w_1, r_1 (and, when m > 1, the start of w_2)
     const bool adaptive = ctx->p.krylov_tol > 0.0;
@@ -508,7 +508,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         ctx->launches++;
         prof_end(ctx, s);
         rc = coulomb_apply_impl(ctx, st->R, Wk, prm->sigma, ctx->phi, nullptr, nullptr, nullptr,
-                                false, s);
+                                false, s, true);
         if (rc) return rc;
         prof_begin(ctx, kPhShadow, s);
         k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->inv_u, part);

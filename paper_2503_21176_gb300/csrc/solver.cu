@@ -221,12 +221,13 @@ int cgs2(qeq_ctx *ctx, int n1, int nv, double *w, std::vector<double> &h, double
 
 // y = A M^{-1} x  (one potential-only Coulomb apply)
 int precond_apply(qeq_ctx *ctx, const double *R, const double *u, const double *sigma,
-                  const double *x, double *y, cudaStream_t s) {
+                  const double *x, double *y, cudaStream_t s, bool same_R) {
     const int n = (int)ctx->n;
     double *z = ctx->gmZ;
     k_precond<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->gmDinv, x, z);
     ctx->launches++;
-    int rc = coulomb_apply_impl(ctx, R, z, sigma, ctx->phi, nullptr, nullptr, nullptr, false, s);
+    int rc = coulomb_apply_impl(ctx, R, z, sigma, ctx->phi, nullptr, nullptr, nullptr, false, s,
+                                same_R);
     if (rc) return rc;
     k_bordered_apply<<<kRedBlocks, kThreads, 0, s>>>(n, u, ctx->phi, z, y, ctx->part);
     launch_finalize(ctx->part, 1, ctx->gmH + 2 * (kMaxDots + 2) + 1, s);
@@ -237,9 +238,10 @@ int precond_apply(qeq_ctx *ctx, const double *R, const double *u, const double *
 
 // A x without preconditioning (x in gmZ already as a plain vector)
 int plain_apply(qeq_ctx *ctx, const double *R, const double *u, const double *sigma,
-                const double *x, double *y, cudaStream_t s) {
+                const double *x, double *y, cudaStream_t s, bool same_R) {
     const int n = (int)ctx->n;
-    int rc = coulomb_apply_impl(ctx, R, x, sigma, ctx->phi, nullptr, nullptr, nullptr, false, s);
+    int rc = coulomb_apply_impl(ctx, R, x, sigma, ctx->phi, nullptr, nullptr, nullptr, false, s,
+                                same_R);
     if (rc) return rc;
     k_bordered_apply<<<kRedBlocks, kThreads, 0, s>>>(n, u, ctx->phi, x, y, ctx->part);
     launch_finalize(ctx->part, 1, ctx->gmH + 2 * (kMaxDots + 2) + 1, s);
@@ -289,7 +291,7 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
     std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), h;
     while (true) {
         // r = b - A z
-        rc = plain_apply(ctx, R, u, sigma, z, w, s);
+        rc = plain_apply(ctx, R, u, sigma, z, w, s, applies > 0);
         if (rc) return rc;
         ++applies;
         k_residual<<<kRedBlocks, kThreads, 0, s>>>(n, p.q_tot, chi, w, w);
@@ -306,7 +308,7 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
         for (; j < restart && iters < max_iter; ++j) {
             double *vj = ctx->gmV + (size_t)j * n1;
             double *vnext = ctx->gmV + (size_t)(j + 1) * n1;
-            rc = precond_apply(ctx, R, u, sigma, vj, vnext, s);
+            rc = precond_apply(ctx, R, u, sigma, vj, vnext, s, applies > 0);
             if (rc) return rc;
             ++applies;
             ++iters;
@@ -357,7 +359,7 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
         if ((relres <= tol || iters >= max_iter) && !final_check) break;
         if (relres <= tol || iters >= max_iter) {
             // true residual of the final iterate (one more apply)
-            rc = plain_apply(ctx, R, u, sigma, z, w, s);
+            rc = plain_apply(ctx, R, u, sigma, z, w, s, applies > 0);
             if (rc) return rc;
             ++applies;
             k_residual<<<kRedBlocks, kThreads, 0, s>>>(n, p.q_tot, chi, w, w);
@@ -442,8 +444,9 @@ int bomd_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, doub
     } else {
         cudaMemsetAsync(scal + 126, 0, 2 * sizeof(double), s);
     }
+    // the solve applied the operator at these positions already
     rc = coulomb_apply_impl(ctx, st->R, st->q, prm->sigma, ctx->v_n, ctx->E_n, nullptr, nullptr,
-                            true, s);
+                            true, s, true);
     if (rc) return rc;
     local.applies += 1;
     k_bo_forces<<<kRedBlocks, kThreads, 0, s>>>(
