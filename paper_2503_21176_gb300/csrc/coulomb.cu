@@ -420,7 +420,7 @@ k_real32(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
          const float4 *__restrict__ xq, const float *__restrict__ sg,
          const int32_t *__restrict__ smax_bits, int cap, unsigned char *__restrict__ gtile,
          int32_t *__restrict__ flags, double *__restrict__ v_s, double *__restrict__ E_s) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile32Bytes : smem_raw;
     float4 *tile = (float4 *)base;
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(kSpreadThreads)
 k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
                const int4 *__restrict__ sbase, const float4 *__restrict__ sfrac,
                float *__restrict__ mesh) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     int *win = (int *)smem_raw;
     __shared__ float qsum_w[kSpreadThreads / 32];
     const int64_t b = blockIdx.x;
@@ -725,7 +725,7 @@ k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
 // m3 = t mod K2h is carried incrementally (stride_mod = stride mod K2h), so the
 // loop has no integer division.  FP32 mode sums each thread's terms in FP32 with
 // compensation; the block partials are FP64.
-template <typename T>
+template <typename T, bool ENERGY>
 __global__ void __launch_bounds__(kThreads)
 k_influence(int nc, int K2h, int K2, int stride_mod, typename C2<T>::type *__restrict__ meshc,
             const T *__restrict__ G, double *__restrict__ part) {
@@ -734,14 +734,16 @@ k_influence(int nc, int K2h, int K2, int stride_mod, typename C2<T>::type *__res
     int m3 = t % K2h;
     T s = T(0), comp = T(0);
     for (; t < nc; t += stride) {
-        const T wgt = (m3 == 0 || 2 * m3 == K2) ? T(0.5) : T(1);
         auto z = meshc[t];
         const T g = G[t];
-        const T term = wgt * g * (z.x * z.x + z.y * z.y);
-        if constexpr (std::is_same<T, float>::value) {
-            kahan_add(s, comp, term);
-        } else {
-            s += term;
+        if (ENERGY) {
+            const T wgt = (m3 == 0 || 2 * m3 == K2) ? T(0.5) : T(1);
+            const T term = wgt * g * (z.x * z.x + z.y * z.y);
+            if constexpr (std::is_same<T, float>::value) {
+                kahan_add(s, comp, term);
+            } else {
+                s += term;
+            }
         }
         z.x *= g;
         z.y *= g;
@@ -749,9 +751,11 @@ k_influence(int nc, int K2h, int K2, int stride_mod, typename C2<T>::type *__res
         m3 += stride_mod;
         if (m3 >= K2h) m3 -= K2h;
     }
-    double vals[1] = {(double)s - (double)comp};
-    block_sum<1>(vals);
-    if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    if (ENERGY) {
+        double vals[1] = {(double)s - (double)comp};
+        block_sum<1>(vals);
+        if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    }
 }
 
 struct GatherArgs {
@@ -762,14 +766,20 @@ struct GatherArgs {
     double gauss_coef;  // k_e * sqrt(2 / pi) when the Gaussian self-energy is on, else 0
 };
 
-template <typename T, int P, bool FIELD>
+// ENERGY: accumulate the energy partial sums (only when the caller asked for
+// the energy parts).  The Gaussian self term k_e sqrt(2/pi) q / sigma takes 1 /
+// sigma in FP64 in FP64 mode, and from the sorted FP32 sigma (correctly rounded
+// reciprocal, relative error below 6e-8) in FP32-mixed mode: an FP64 divide per
+// atom is about 30 operations of GB300's 1/64-rate FP64 pipe, which bounded this
+// kernel.
+template <typename T, int P, bool FIELD, bool ENERGY>
 __global__ void __launch_bounds__(kThreads)
 k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restrict__ sbase,
              const typename V4<T>::type *__restrict__ sfrac, const T *__restrict__ phi,
              const double *__restrict__ v_s, const double *__restrict__ E_s,
              const double *__restrict__ q, const double *__restrict__ sigma,
-             double *__restrict__ v_out, double *__restrict__ E_out, double *__restrict__ F_out,
-             double *__restrict__ part) {
+             const T *__restrict__ sg_sorted, double *__restrict__ v_out, double *__restrict__ E_out,
+             double *__restrict__ F_out, double *__restrict__ part) {
     double e_tot = 0.0, e_real = 0.0, e_self = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const int4 b = sbase[i];
@@ -807,7 +817,12 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
         const int atom = perm[i];
         const double qa = q[atom];
         double sc = a.self_coef;
-        if (a.gauss_coef != 0.0) sc += a.gauss_coef / sigma[atom];
+        if (a.gauss_coef != 0.0) {
+            if constexpr (std::is_same<T, float>::value)
+                sc += a.gauss_coef * (double)__frcp_rn(sg_sorted[i]);
+            else
+                sc += a.gauss_coef / sigma[atom];
+        }
         const double vs = v_s[i];
         const double vself = sc * qa;
         const double v = vs + (double)vr + vself;
@@ -827,16 +842,20 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
                 F_out[3 * (size_t)atom + 2] = qa * Ez;
             }
         }
-        e_tot += 0.5 * qa * v;
-        e_real += 0.5 * qa * vs;
-        e_self += 0.5 * qa * vself;
+        if (ENERGY) {
+            e_tot += 0.5 * qa * v;
+            e_real += 0.5 * qa * vs;
+            e_self += 0.5 * qa * vself;
+        }
     }
-    double vals[3] = {e_tot, e_real, e_self};
-    block_sum<3>(vals);
-    if (threadIdx.x == 0) {
-        part[0 * kRedBlocks + blockIdx.x] = vals[0];
-        part[1 * kRedBlocks + blockIdx.x] = vals[1];
-        part[3 * kRedBlocks + blockIdx.x] = vals[2];
+    if (ENERGY) {
+        double vals[3] = {e_tot, e_real, e_self};
+        block_sum<3>(vals);
+        if (threadIdx.x == 0) {
+            part[0 * kRedBlocks + blockIdx.x] = vals[0];
+            part[1 * kRedBlocks + blockIdx.x] = vals[1];
+            part[3 * kRedBlocks + blockIdx.x] = vals[2];
+        }
     }
 }
 
@@ -989,10 +1008,16 @@ void launch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t s)
 template <typename T, int P, bool FIELD>
 void launch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const void *sf,
                    const double *q, const double *sigma, double *v, double *E, double *F,
-                   cudaStream_t s) {
-    k_gather_out<T, P, FIELD><<<kRedBlocks, kThreads, 0, s>>>(
-        ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
-        ctx->E_s, q, sigma, v, E, F, ctx->part);
+                   bool energy, cudaStream_t s) {
+    const T *sgs = std::is_same<T, float>::value ? (const T *)ctx->sg32 : (const T *)ctx->sg64;
+    if (energy)
+        k_gather_out<T, P, FIELD, true><<<kRedBlocks, kThreads, 0, s>>>(
+            ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
+            ctx->E_s, q, sigma, sgs, v, E, F, ctx->part);
+    else
+        k_gather_out<T, P, FIELD, false><<<kRedBlocks, kThreads, 0, s>>>(
+            ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
+            ctx->E_s, q, sigma, sgs, v, E, F, ctx->part);
 }
 
 template <typename T>
@@ -1009,13 +1034,13 @@ void dispatch_spread(qeq_ctx *ctx, const int4 *sb, const void *sf, cudaStream_t 
 template <typename T, bool FIELD>
 void dispatch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const void *sf,
                      const double *q, const double *sigma, double *v, double *E, double *F,
-                     cudaStream_t s) {
+                     bool energy, cudaStream_t s) {
     switch (ctx->p.order) {
-        case 4: launch_gather<T, 4, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
-        case 5: launch_gather<T, 5, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
-        case 6: launch_gather<T, 6, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
-        case 7: launch_gather<T, 7, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
-        default: launch_gather<T, 8, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, s); break;
+        case 4: launch_gather<T, 4, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, energy, s); break;
+        case 5: launch_gather<T, 5, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, energy, s); break;
+        case 6: launch_gather<T, 6, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, energy, s); break;
+        case 7: launch_gather<T, 7, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, energy, s); break;
+        default: launch_gather<T, 8, FIELD>(ctx, ga, sb, sf, q, sigma, v, E, F, energy, s); break;
     }
 }
 
@@ -1141,9 +1166,14 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     prof_begin(ctx, kPhInfluence, s);
     {
         const int K2h = ctx->K[2] / 2 + 1;
-        k_influence<T><<<kRedBlocks, kThreads, 0, s>>>(
-            (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
-            (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+        if (energy4)
+            k_influence<T, true><<<kRedBlocks, kThreads, 0, s>>>(
+                (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
+                (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+        else
+            k_influence<T, false><<<kRedBlocks, kThreads, 0, s>>>(
+                (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
+                (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, nullptr);
     }
     prof_end(ctx, s);
     ctx->launches++;
@@ -1165,10 +1195,12 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ga.self_coef = p.k_e * (-kTwoOverSqrtPi * p.alpha);
     ga.gauss_coef = p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0;
     prof_begin(ctx, kPhGatherOut, s);
+    const bool energy = energy4 != nullptr;
     if (need_field)
-        dispatch_gather<T, true>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, E, F, s);
+        dispatch_gather<T, true>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, E, F, energy, s);
     else
-        dispatch_gather<T, false>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, nullptr, nullptr, s);
+        dispatch_gather<T, false>(ctx, ga, ctx->sbase, ctx->sfrac, q, sigma, v, nullptr, nullptr,
+                                  energy, s);
     prof_end(ctx, s);
     ctx->launches++;
     if (energy4) {
