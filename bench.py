@@ -42,6 +42,12 @@ ALPHA, R_CUT, SKIN, MESH, ORDER, RANK, KD, DT = 0.34, 8.0, 1.0, 144, 4, 2, 5, 0.
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # algorithmic work per directed real-space pair inside r_c (FMA-pipe operations)
 PAIR_OPS = 40
+# DRAM bytes (read + write) per launch of the FP32 real-space kernel (potential
+# and field): ncu --set full of k_real32<1,0> on the 120,000-atom water box
+# (profiles/ncu_kernels_fp32_water120k.md: 78.71 MB read + 1.79 MB written),
+# scaled to the 300,000-atom box by the list entries processed (x 2.5).  Valid
+# for the kernel version that capture was taken of.
+REAL32_TRAFFIC_BYTES = (78.71e6 + 1.79e6) * 2.5
 SM_COUNT, FP32_LANES, FP64_LANES = 152, 128, 2
 T_EV = 0.025852  # k_B * 300 K in eV
 
@@ -325,7 +331,9 @@ def roofline(res, precision, n_pairs_rc, peaks):
         achieved = n_pairs_rc * PAIR_OPS / (avg_ms * 1e-3) / 1e12
         out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-               "traffic": None, "peak_source": f"{SM_COUNT} SMs x {lanes} lanes x 2.07 GHz",
+               "traffic": REAL32_TRAFFIC_BYTES if precision == "fp32_mixed" else None,
+               "traffic_unit": "DRAM bytes per launch (ncu, scaled from 120k atoms)",
+               "peak_source": f"{SM_COUNT} SMs x {lanes} lanes x 2.07 GHz",
                "pairs_per_s": round(n_pairs_rc / (avg_ms * 1e-3), 1)}
     else:
         gbs = peaks.get("hbm_gbs", 6800.0)
