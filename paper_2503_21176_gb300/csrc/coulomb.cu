@@ -1014,8 +1014,8 @@ void launch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const voi
         k_gather_out<T, P, FIELD, true><<<kRedBlocks, kThreads, 0, s>>>(
             ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
             ctx->E_s, q, sigma, sgs, v, E, F, ctx->part);
-    else
-        k_gather_out<T, P, FIELD, false><<<kRedBlocks, kThreads, 0, s>>>(
+    else  // no partials: one thread per atom, every atom in flight at once
+        k_gather_out<T, P, FIELD, false><<<grid_for(ctx->n), kThreads, 0, s>>>(
             ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
             ctx->E_s, q, sigma, sgs, v, E, F, ctx->part);
 }
@@ -1240,6 +1240,7 @@ int coulomb_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->part, sizeof(double) * kMaxRedSlots * kRedBlocks},
         {(void **)&ctx->scal, sizeof(double) * kNumScal},
         {(void **)&ctx->energy4, sizeof(double) * 4},
+        {(void **)&ctx->ticket, sizeof(unsigned int) * 4},
     };
     for (auto &b : bufs) {
         int rc = dev_alloc(ctx, b.ptr, b.bytes);
@@ -1249,6 +1250,7 @@ int coulomb_alloc(qeq_ctx *ctx) {
     if (!ctx->h_scal) return set_error(ctx, QEQ_ERR_NOMEM, "host allocation failed");
     cudaMemsetAsync(ctx->scal, 0, sizeof(double) * kNumScal, ctx->alloc_stream);
     cudaMemsetAsync(ctx->part, 0, sizeof(double) * kMaxRedSlots * kRedBlocks, ctx->alloc_stream);
+    cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int) * 4, ctx->alloc_stream);
 
     // influence function G(m) = k_e (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2 * B(m) on the
     // half spectrum [K0][K1][K2/2+1], G(0) = 0 (Eq. ewald_rec with the smooth-PME B factor)
@@ -1366,7 +1368,8 @@ void coulomb_free(qeq_ctx *ctx) {
     }
     void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
                     ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
-                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->tile_scratch};
+                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->tile_scratch,
+                    ctx->ticket};
     for (void *p : ptrs) dev_free(ctx, p);
     ewald_free(ctx);
     delete[] ctx->h_scal;

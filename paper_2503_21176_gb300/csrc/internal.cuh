@@ -318,6 +318,7 @@ struct qeq_ctx {
 
     // ---- reductions ----
     double *part = nullptr;    // [kMaxRedSlots][kRedBlocks]
+    unsigned int *ticket = nullptr;  // last-block counter of finalize_last_block (0 between kernels)
     double *scal = nullptr;    // [kNumScal]
     double *h_scal = nullptr;  // pinned host mirror
 
@@ -450,6 +451,38 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
         }
     }
     __syncthreads();
+}
+
+// Grid reduction without a second launch.  Every block has written its NV
+// partial sums to part[k * kRedBlocks + blockIdx.x]; the last block to arrive
+// (ticket counter, then reset to 0 for the next kernel) sums them in the fixed
+// order of k_finalize into out[0..NV).  Returns true in all threads of that
+// block; out is written by its thread 0 before the block's final barrier.
+template <int NV>
+__device__ __forceinline__ bool finalize_last_block(const double *part, double *out,
+                                                    unsigned int *ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        v[k] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            v[k] += __ldcg(part + (size_t)k * kRedBlocks + b);
+    }
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = v[k];
+        *ticket = 0u;
+    }
+    __syncthreads();
+    return true;
 }
 
 // Record the start / end event of a profiled phase on stream s (no-op when off).

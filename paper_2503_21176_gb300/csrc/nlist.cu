@@ -410,8 +410,11 @@ k_coo_scatter(int n, BrickGeom g, const int32_t *__restrict__ cell_start,
     }
 }
 
+// Max squared displacement since the last build: block maxima, and the last
+// block to finish (ticket counter, reset to 0) reduces them into *out.
 __global__ void k_max_disp2(int n, const double *__restrict__ R, const double *__restrict__ R0,
-                            double *__restrict__ part) {
+                            double *__restrict__ part, double *__restrict__ out,
+                            unsigned int *__restrict__ ticket) {
     double m = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double dx = R[3 * (size_t)i] - R0[3 * (size_t)i];
@@ -422,6 +425,7 @@ __global__ void k_max_disp2(int n, const double *__restrict__ R, const double *_
         m = fmax(m, d2);
     }
     __shared__ double sh[kThreads / 32];
+    __shared__ bool is_last;
     m = warp_max(m);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -430,19 +434,25 @@ __global__ void k_max_disp2(int n, const double *__restrict__ R, const double *_
         t = warp_max(t);
         if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
-}
-
-__global__ void k_max_final(int nb, const double *__restrict__ part, double *__restrict__ out) {
-    double m = 0.0;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) m = fmax(m, part[k]);
-    __shared__ double sh[kThreads / 32];
-    m = warp_max(m);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) v = fmax(v, __ldcg(part + k));
+    v = warp_max(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x < 32) {
         double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
         t = warp_max(t);
-        if (threadIdx.x == 0) *out = t;
+        if (threadIdx.x == 0) {
+            *out = t;
+            *ticket = 0u;
+        }
     }
 }
 
@@ -642,10 +652,10 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
 
 int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_disp2) {
     prof_begin(ctx, kPhIntegrate, s);
-    k_max_disp2<<<kRedBlocks, kThreads, 0, s>>>((int)ctx->n, R, ctx->R_build, ctx->part);
-    k_max_final<<<1, kThreads, 0, s>>>(kRedBlocks, ctx->part, ctx->scal + kScMaxDisp2);
+    k_max_disp2<<<kRedBlocks, kThreads, 0, s>>>((int)ctx->n, R, ctx->R_build, ctx->part,
+                                                ctx->scal + kScMaxDisp2, ctx->ticket);
     prof_end(ctx, s);
-    ctx->launches += 2;
+    ctx->launches += 1;
     if (max_disp2) {
         cudaMemcpyAsync(ctx->h_scal + kScMaxDisp2, ctx->scal + kScMaxDisp2, sizeof(double),
                         cudaMemcpyDeviceToHost, s);

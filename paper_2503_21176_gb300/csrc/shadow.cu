@@ -40,7 +40,8 @@ constexpr int S_SHORT = 126;  // short-range energy: intramolecular, Lennard-Jon
 
 __global__ void k_lambda_part(int n, const double *__restrict__ chi, const double *__restrict__ u,
                               const double *__restrict__ v, double *__restrict__ inv_u,
-                              double *__restrict__ part) {
+                              double *__restrict__ part, double *__restrict__ out,
+                              unsigned int *__restrict__ ticket) {
     double s1 = 0.0, s2 = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double iu = 1.0 / u[i];
@@ -54,13 +55,15 @@ __global__ void k_lambda_part(int n, const double *__restrict__ chi, const doubl
         part[blockIdx.x] = vals[0];
         part[kRedBlocks + blockIdx.x] = vals[1];
     }
+    finalize_last_block<2>(part, out, ticket);
 }
 
 __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
                           const double *__restrict__ u, const double *__restrict__ inv_u,
                           const double *__restrict__ v,
                           const double *__restrict__ nn, const double *__restrict__ scal,
-                          double *__restrict__ q, double *__restrict__ f, double *__restrict__ part) {
+                          double *__restrict__ q, double *__restrict__ f, double *__restrict__ part,
+                          double *__restrict__ out, unsigned int *__restrict__ ticket) {
     const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
     double a[6] = {0, 0, 0, 0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -78,6 +81,7 @@ __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
     block_sum<6>(a);
     if (threadIdx.x == 0)
         for (int k = 0; k < 6; ++k) part[k * kRedBlocks + blockIdx.x] = a[k];
+    finalize_last_block<6>(part, out, ticket);
 }
 
 // F = q E[n] + n E[f] (+ F_short); w_1 = f / |f|; Phi w_1 = Phi f / |f| (in place);
@@ -87,7 +91,8 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
                             const double *__restrict__ Fs, const double *__restrict__ f,
                             const double *__restrict__ inv_u, const double *__restrict__ scal,
                             double *__restrict__ F, double *__restrict__ w1,
-                            double *__restrict__ phi, double *__restrict__ part) {
+                            double *__restrict__ phi, double *__restrict__ part,
+                            double *__restrict__ out, unsigned int *__restrict__ ticket) {
     const double nf = sqrt(scal[S_CHG]);
     const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
     double s = 0.0;
@@ -106,16 +111,19 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    finalize_last_block<1>(part, out, ticket);
 }
 
 __global__ void k_mu_part(int n, const double *__restrict__ phi, const double *__restrict__ inv_u,
-                          double *__restrict__ part) {
+                          double *__restrict__ part, double *__restrict__ out,
+                          unsigned int *__restrict__ ticket) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         s += phi[i] * inv_u[i];
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    finalize_last_block<1>(part, out, ticket);
 }
 
 // r = J w = -(Phi w + mu) / u - w with mu = -(sum Phi w / u) / sum 1 / u.
@@ -124,7 +132,8 @@ __global__ void k_mu_part(int n, const double *__restrict__ phi, const double *_
 __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *__restrict__ w,
                            const double *__restrict__ inv_u, const double *__restrict__ scal,
                            double *__restrict__ r, double *__restrict__ wnext,
-                           const double *__restrict__ w0, double *__restrict__ part) {
+                           const double *__restrict__ w0, double *__restrict__ part,
+                           double *__restrict__ out, unsigned int *__restrict__ ticket) {
     const double mu = -scal[S_MU] / scal[S_LAM + 1];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -139,12 +148,14 @@ __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *
         double vals[1] = {s};
         block_sum<1>(vals);
         if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+        finalize_last_block<1>(part, out, ticket);
     }
 }
 
 // x -= scal[S_DOT] * y, then partial of <z, x> (z may alias x for the norm)
 __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double *__restrict__ y,
-                           double *x, const double *z, double *__restrict__ part) {
+                           double *x, const double *z, double *__restrict__ part,
+                           double *__restrict__ out, unsigned int *__restrict__ ticket) {
     const double a = scal[S_DOT];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -155,6 +166,7 @@ __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double 
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    finalize_last_block<1>(part, out, ticket);
 }
 
 __global__ void k_normalize(int n, const double *__restrict__ scal, double *__restrict__ x) {
@@ -264,7 +276,8 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
 // |f|^2 - c.R^T f cancels catastrophically once the residual is small)
 __global__ void k_ls_residual(int n, int m, const double *__restrict__ Rb,
                               const double *__restrict__ f, const double *__restrict__ scal,
-                              double *__restrict__ part) {
+                              double *__restrict__ part, double *__restrict__ out,
+                              unsigned int *__restrict__ ticket) {
     const double *c = scal + S_OM + kMaxRank * kMaxRank;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -275,6 +288,7 @@ __global__ void k_ls_residual(int n, int m, const double *__restrict__ Rb,
     double vals[1] = {acc};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
+    finalize_last_block<1>(part, out, ticket);
 }
 
 __global__ void k_kf(int n, int m, const double *__restrict__ Wb, const double *__restrict__ scal,
@@ -344,7 +358,8 @@ __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
 __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
                          const double *__restrict__ mass, const double *__restrict__ inv_m,
                          const double *__restrict__ F, double *__restrict__ V,
-                         double *__restrict__ part) {
+                         double *__restrict__ part, double *__restrict__ scal,
+                         double *__restrict__ energies, unsigned int *__restrict__ ticket) {
     double ke = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double mi = mass[i] * mass_unit;
@@ -363,11 +378,11 @@ __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
     double vals[1] = {ke};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
-}
-
-__global__ void k_total_energy(const double *__restrict__ scal, double *__restrict__ energies) {
-    energies[0] = scal[S_KE];
-    energies[2] = scal[S_KE] + energies[1];
+    // the last block also writes the kinetic and total energies
+    if (finalize_last_block<1>(part, scal + S_KE, ticket) && threadIdx.x == 0) {
+        energies[0] = scal[S_KE];
+        energies[2] = scal[S_KE] + energies[1];
+    }
 }
 
 }  // namespace
@@ -417,10 +432,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     double *part = ctx->part;
     double *scal = ctx->scal;
     const int G = kRedBlocks;
-    auto fin = [&](int nslots, int slot0) {
-        launch_finalize(part, nslots, scal + slot0, s);
-        ctx->launches += 2;  // the partial kernel before it, and the finalize
-    };
+    unsigned int *tk = ctx->ticket;
+    auto fin = [&]() { ctx->launches += 1; };  // a reducing kernel (its last block finalizes)
 
     // short-range stand-in (or zero)
     prof_begin(ctx, kPhShadow, s);
@@ -438,11 +451,11 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     if (rc) return rc;
     // 2. lambda and q[n] (Eq. diag_linear_qeq); 1/u kept for the rest of the evaluation
     prof_begin(ctx, kPhShadow, s);
-    k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, ctx->inv_u, part);
-    fin(2, S_LAM);
+    k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, ctx->inv_u, part, scal + S_LAM, tk);
+    fin();
     k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn, scal,
-                                     st->q, ctx->fvec, part);
-    fin(6, S_CHG);
+                                     st->q, ctx->fvec, part, scal + S_CHG, tk);
+    fin();
     prof_end(ctx, s);
     // 3. Phi f, E[f]
     rc = coulomb_apply_impl(ctx, st->R, ctx->fvec, prm->sigma, ctx->phi, ctx->E_f, nullptr, nullptr,
@@ -453,15 +466,13 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     prof_begin(ctx, kPhShadow, s);
     k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
                                        ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr,
-                                       ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb, ctx->phi, part);
-    fin(1, S_MU);
+                                       ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb, ctx->phi, part,
+                                       scal + S_MU, tk);
+    fin();
     k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
-                                      m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part);
+                                      m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part,
+                                      scal + S_DOT, tk);
     ctx->launches++;
-    if (m > 1) {
-        launch_finalize(part, 1, scal + S_DOT, s);
-        ctx->launches++;
-    }
     prof_end(ctx, s);
     // normal equations, m x m solve and energies for rank k; with a tolerance, the
     // host reads the least-squares residual and stops adding vectors when it is met
@@ -475,8 +486,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         (void)nO;
         *done = true;
         if (!adaptive || k == m) return QEQ_OK;
-        k_ls_residual<<<G, kThreads, 0, s>>>(n, k, ctx->Rb, ctx->fvec, scal, part);
-        fin(1, S_RES);
+        k_ls_residual<<<G, kThreads, 0, s>>>(n, k, ctx->Rb, ctx->fvec, scal, part, scal + S_RES, tk);
+        fin();
         double hv[2] = {0.0, 0.0};  // |R c - f|^2 and |f|^2
         cudaError_t e = cudaMemcpyAsync(&hv[0], scal + S_RES, sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
@@ -501,8 +512,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
-            k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, part);
-            fin(1, S_DOT);
+            k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, part, scal + S_DOT, tk);
+            fin();
         }
         k_normalize<<<G, kThreads, 0, s>>>(n, scal, Wk);
         ctx->launches++;
@@ -511,17 +522,13 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
                                 false, s, true);
         if (rc) return rc;
         prof_begin(ctx, kPhShadow, s);
-        k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->inv_u, part);
-        fin(1, S_MU);
+        k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->inv_u, part, scal + S_MU, tk);
+        fin();
         const bool more = k + 1 < m;
         k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, Wk, ctx->inv_u, scal, ctx->Rb + (size_t)k * n,
                                           more ? ctx->Wb + (size_t)(k + 1) * n : nullptr, ctx->Wb,
-                                          part);
+                                          part, scal + S_DOT, tk);
         ctx->launches++;
-        if (more) {
-            launch_finalize(part, 1, scal + S_DOT, s);
-            ctx->launches++;
-        }
         prof_end(ctx, s);
         m_used = k + 1;
         if (adaptive) {
@@ -566,11 +573,10 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
     k_finish<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
-                                             ctx->inv_m, st->F, st->V, ctx->part);
-    launch_finalize(ctx->part, 1, ctx->scal + S_KE, s);
-    k_total_energy<<<1, 1, 0, s>>>(ctx->scal, st->energies);
+                                             ctx->inv_m, st->F, st->V, ctx->part, ctx->scal,
+                                             st->energies, ctx->ticket);
     prof_end(ctx, s);
-    ctx->launches += 3;
+    ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "shadow finish launch");
 }
 
