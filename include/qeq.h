@@ -139,8 +139,11 @@ int qeq_create(const qeq_params *p, qeq_ctx **out);
 
 /* Same as qeq_create, but every device buffer, including the cuFFT work
  * area, comes from the device's default stream-ordered memory pool
- * (cudaMallocAsync on `stream`).  Uploads and memsets are ordered on `stream`,
- * and the call synchronises only `stream`, never the whole device.
+ * (cudaMallocAsync on `stream`).  The set-up kernels, uploads and memsets are
+ * ordered on `stream`, and the call returns without waiting for them (it never
+ * synchronises the device; only the explicit k-vector Ewald set-up waits for
+ * `stream`).  cuFFT plans come from a process-wide pool keyed by device, mesh
+ * and transform: qeq_destroy of any context returns its plans there.
  * qeq_destroy then frees with cudaFreeAsync on that stream.  Creating and
  * destroying contexts this way does not stall work on other streams.  The
  * serving loop relies on that to admit and retire requests while others run.
@@ -149,8 +152,9 @@ int qeq_create(const qeq_params *p, qeq_ctx **out);
  * work before qeq_destroy. */
 int qeq_create_async(const qeq_params *p, void *stream, qeq_ctx **out);
 
-/* Free everything qeq_create allocated.  NULL is ignored.  Synchronises the
- * device (contexts from qeq_create_async: stream-ordered frees, no sync). */
+/* Free everything qeq_create allocated (its cuFFT plans go back to the plan
+ * pool).  NULL is ignored.  Synchronises the device (contexts from
+ * qeq_create_async: stream-ordered frees, no sync). */
 void qeq_destroy(qeq_ctx *ctx);
 
 /* Message for the last failing call on ctx ("" when none).  ctx may be NULL,

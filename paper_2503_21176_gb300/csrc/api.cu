@@ -165,9 +165,11 @@ int create(const qeq_params *p, cudaStream_t stream, bool async_alloc, qeq_ctx *
     if (!rc) rc = nl_alloc(ctx);
     if (!rc) rc = coulomb_alloc(ctx);
     if (!rc) rc = shadow_alloc(ctx);
+    // stream-ordered creation returns without waiting: the set-up kernels and copies
+    // (from process-lifetime host tables only) are ordered before the caller's work
+    // on the same stream
     if (!rc)
-        rc = cuda_check(ctx, async_alloc ? cudaStreamSynchronize(stream) : cudaDeviceSynchronize(),
-                        "create");
+        rc = cuda_check(ctx, async_alloc ? cudaGetLastError() : cudaDeviceSynchronize(), "create");
     if (rc) {
         g_create_error = ctx->err;
         destroy(ctx);

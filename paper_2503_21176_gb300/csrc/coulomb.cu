@@ -17,6 +17,9 @@
 // spreading, the FFT and the gather in float.  It accumulates rows in float
 // chunks of 32 flushed into double, and keeps the energies and outputs in double.
 #include <cmath>
+#include <tuple>
+#include <map>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -614,11 +617,10 @@ __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, 
 // largest weight of one mesh point: no window point can overflow.  The sums are
 // exact and independent of the atomic order; the resolution is
 // wmax sum |q| / 2^30 (about 7e-9 e for a 73-atom water brick with charges of
-// 0.3 e).  The window origin of brick (bx, by, bz) is floor(b_d X_d) - P per
-// axis, X_d = B_d cw_d K_d / L_d (one mesh point of margin below and above
-// against rounding of floor(K x / L)); z is rounded down to a multiple of 4.
-// An atom whose support leaves the window (not expected) adds straight into
-// the global mesh.
+// 0.3 e).  The window origin of brick (bx, by, bz) is floor(b_d X_d) - (P - 1)
+// per axis, X_d = B_d cw_d K_d / L_d; z is rounded down to a multiple of 4.
+// An atom whose support leaves the window (possible only through rounding of
+// floor(K x / L) at a brick face) adds straight into the global mesh.
 struct SpreadWin {
     int K0, K1, K2;
     int E0, E1, E2;      // window extent (E2 a multiple of 4)
@@ -652,8 +654,8 @@ k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
     const int64_t b = blockIdx.x;
     const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
     const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
-    const int lo0 = (int)floor(bx * w.X0) - P, lo1 = (int)floor(by * w.X1) - P;
-    const int lo2 = ((int)floor(bz * w.X2) - P) & ~3;
+    const int lo0 = (int)floor(bx * w.X0) - (P - 1), lo1 = (int)floor(by * w.X1) - (P - 1);
+    const int lo2 = ((int)floor(bz * w.X2) - (P - 1)) & ~3;
     const int nwin = w.E0 * w.E1 * w.E2;
     const int a0 = cell_start[b * g.bvol], a1 = cell_start[(b + 1) * g.bvol];
     float qs = 0.f;
@@ -868,6 +870,47 @@ __global__ void k_finalize(const double *__restrict__ part, double *__restrict__
     if (threadIdx.x == 0) out[blockIdx.x] = vals[0];
 }
 
+// |b(m)|^2 of smooth PME for one axis (K points): b(m) = e^{2 pi i (p-1) m / K} /
+// sum_{k=0}^{p-2} M_p(k+1) e^{2 pi i m k / K}; a vanishing denominator (odd p at
+// m = K/2) gives 0.  Mk holds M_p(k + 1), k = 0..p-2.
+struct SplineInts {
+    double Mk[8];
+    int p;
+};
+
+__global__ void k_bspline_mod2(int K, SplineInts s, double *__restrict__ out) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= K) return;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k <= s.p - 2; ++k) {
+        double sn, cs;
+        sincospi(2.0 * (double)(((long long)m * k) % K) / K, &sn, &cs);
+        re += s.Mk[k] * cs;
+        im += s.Mk[k] * sn;
+    }
+    const double d2 = re * re + im * im;
+    out[m] = d2 > 1e-10 ? 1.0 / d2 : 0.0;
+}
+
+// Influence function G(m) = k_e (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2 * B(m) on
+// the half spectrum [K0][K1][K2/2+1], G(0) = 0 (Eq. ewald_rec with the smooth-PME
+// B factor), one thread per point, from the per-axis |b|^2 tables b0, b1, b2.
+template <typename T>
+__global__ void k_influence_table(int K0, int K1, int K2, double Lx, double Ly, double Lz,
+                                  double pref, double inv4a2, const double *__restrict__ b0,
+                                  const double *__restrict__ b1, const double *__restrict__ b2,
+                                  T *__restrict__ G) {
+    const int K2h = K2 / 2 + 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)K0 * K1 * K2h) return;
+    const int m2 = (int)(t % K2h), m1 = (int)((t / K2h) % K1), m0 = (int)(t / ((int64_t)K2h * K1));
+    const int c0 = m0 <= K0 / 2 ? m0 : m0 - K0;
+    const int c1 = m1 <= K1 / 2 ? m1 : m1 - K1;
+    const double kx = 2.0 * kPi * c0 / Lx, ky = 2.0 * kPi * c1 / Ly, kz = 2.0 * kPi * m2 / Lz;
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    G[t] = k2 > 0.0 ? (T)(pref * exp(-k2 * inv4a2) / k2 * b0[m0] * b1[m1] * b2[m2]) : T(0);
+}
+
 // ---------------------------------------------------------------------------
 // host-side tables
 // ---------------------------------------------------------------------------
@@ -976,11 +1019,13 @@ SpreadWin spread_window(const qeq_ctx *ctx, int P, size_t elem, size_t *nbytes) 
     w.X0 = X[0];
     w.X1 = X[1];
     w.X2 = X[2];
-    // floor((b + 1) X) - floor(b X) <= ceil(X); P - 1 support points below, one
-    // margin point on each side, and up to 3 more below z from the alignment
-    w.E0 = (int)std::ceil(X[0]) + P + 2;
-    w.E1 = (int)std::ceil(X[1]) + P + 2;
-    w.E2 = ((int)std::ceil(X[2]) + P + 2 + 3 + 3) / 4 * 4;
+    // base = floor(K x / L) of the brick's atoms lies in [floor(b X), floor((b + 1) X)],
+    // floor((b + 1) X) - floor(b X) <= ceil(X), and the support reaches P - 1
+    // points below: ceil(X) + P points per axis, up to 3 more below z from the
+    // alignment.  An atom that rounding puts outside takes the global path.
+    w.E0 = (int)std::ceil(X[0]) + P;
+    w.E1 = (int)std::ceil(X[1]) + P;
+    w.E2 = ((int)std::ceil(X[2]) + P + 3 + 3) / 4 * 4;
     w.vec = ctx->K[2] % 4 == 0;
     // largest cardinal B-spline value M_P(P / 2), cubed: one atom's largest weight
     w.wmax = (float)std::pow(bspline_peak(P), 3);
@@ -1252,42 +1297,44 @@ int coulomb_alloc(qeq_ctx *ctx) {
     cudaMemsetAsync(ctx->part, 0, sizeof(double) * kMaxRedSlots * kRedBlocks, ctx->alloc_stream);
     cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int) * 4, ctx->alloc_stream);
 
-    // influence function G(m) = k_e (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2 * B(m) on the
-    // half spectrum [K0][K1][K2/2+1], G(0) = 0 (Eq. ewald_rec with the smooth-PME B factor)
-    std::vector<double> b0 = bspline_mod2(ctx->K[0], p.order);
-    std::vector<double> b1 = bspline_mod2(ctx->K[1], p.order);
-    std::vector<double> b2 = bspline_mod2(ctx->K[2], p.order);
-    const double V = p.box[0] * p.box[1] * p.box[2];
-    const double pref = p.k_e * 4.0 * kPi / V;
-    const double inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
-    std::vector<double> G((size_t)ctx->meshc_n);
-    for (int m0 = 0; m0 < ctx->K[0]; ++m0) {
-        const int c0 = m0 <= ctx->K[0] / 2 ? m0 : m0 - ctx->K[0];
-        const double kx = 2.0 * kPi * c0 / p.box[0];
-        for (int m1 = 0; m1 < ctx->K[1]; ++m1) {
-            const int c1 = m1 <= ctx->K[1] / 2 ? m1 : m1 - ctx->K[1];
-            const double ky = 2.0 * kPi * c1 / p.box[1];
-            for (int m2 = 0; m2 < K2h; ++m2) {
-                const double kz = 2.0 * kPi * m2 / p.box[2];
-                const double k2 = kx * kx + ky * ky + kz * kz;
-                const size_t t = ((size_t)m0 * ctx->K[1] + m1) * K2h + m2;
-                G[t] = k2 > 0.0 ? pref * std::exp(-k2 * inv4a2) / k2 * b0[m0] * b1[m1] * b2[m2] : 0.0;
-            }
+    // influence function on the device: per-axis |b|^2 (into the reduction
+    // partials, free until the first apply), then G on the half spectrum
+    {
+        SplineInts si{};
+        si.p = p.order;
+        {
+            std::vector<double> M(p.order, 0.0);  // M_p at the integers by the order recursion
+            M[1] = 1.0;
+            for (int nn = 3; nn <= p.order; ++nn)
+                for (int j = nn - 1; j >= 0; --j) {
+                    const double left = (j < nn - 1) ? M[j] : 0.0;
+                    const double right = (j >= 1) ? M[j - 1] : 0.0;
+                    M[j] = (j * left + (nn - j) * right) / (nn - 1);
+                }
+            for (int k = 0; k + 1 < p.order; ++k) si.Mk[k] = M[k + 1];
         }
+        double *bm = ctx->part;  // K0 + K1 + K2 <= 3 * 4096 < kMaxRedSlots * kRedBlocks
+        cudaStream_t as = ctx->alloc_stream;
+        k_bspline_mod2<<<grid_for(ctx->K[0]), kThreads, 0, as>>>(ctx->K[0], si, bm);
+        k_bspline_mod2<<<grid_for(ctx->K[1]), kThreads, 0, as>>>(ctx->K[1], si, bm + ctx->K[0]);
+        k_bspline_mod2<<<grid_for(ctx->K[2]), kThreads, 0, as>>>(ctx->K[2], si, bm + ctx->K[0] + ctx->K[1]);
+        const double V = p.box[0] * p.box[1] * p.box[2];
+        const double pref = p.k_e * 4.0 * kPi / V;
+        const double inv4a2 = 1.0 / (4.0 * p.alpha * p.alpha);
+        if (ctx->fp32)
+            k_influence_table<float><<<grid_for(ctx->meshc_n), kThreads, 0, as>>>(
+                ctx->K[0], ctx->K[1], ctx->K[2], p.box[0], p.box[1], p.box[2], pref, inv4a2, bm,
+                bm + ctx->K[0], bm + ctx->K[0] + ctx->K[1], (float *)ctx->G);
+        else
+            k_influence_table<double><<<grid_for(ctx->meshc_n), kThreads, 0, as>>>(
+                ctx->K[0], ctx->K[1], ctx->K[2], p.box[0], p.box[1], p.box[2], pref, inv4a2, bm,
+                bm + ctx->K[0], bm + ctx->K[0] + ctx->K[1], (double *)ctx->G);
+        cudaMemsetAsync(ctx->part, 0, sizeof(double) * (ctx->K[0] + ctx->K[1] + ctx->K[2]), as);
+        int rcg = cuda_check(ctx, cudaGetLastError(), "influence table");
+        if (rcg) return rcg;
     }
-    cudaError_t e;
-    if (ctx->fp32) {
-        std::vector<float> Gf(G.begin(), G.end());
-        e = cudaMemcpyAsync(ctx->G, Gf.data(), sizeof(float) * Gf.size(), cudaMemcpyHostToDevice,
-                            ctx->alloc_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
-    } else {
-        e = cudaMemcpyAsync(ctx->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice,
-                            ctx->alloc_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
-    }
-    int rc = cuda_check(ctx, e, "influence upload");
-    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    int rc = QEQ_OK;
 
     if (p.recip == QEQ_RECIP_EWALD) {
         rc = ewald_alloc(ctx);
@@ -1312,39 +1359,94 @@ int coulomb_alloc(qeq_ctx *ctx) {
         if (rca) return rca;
     }
 
-    // piecewise erfc table of the FP64 real-space kernel
+    // piecewise erfc table of the FP64 real-space kernel (computed once per process;
+    // the host copy lives until exit, so the upload needs no synchronisation)
     {
-        std::vector<double> tab = erfc_table();
+        static std::once_flag once;
+        static std::vector<double> tab;
+        std::call_once(once, [] { tab = erfc_table(); });
         rc = dev_alloc(ctx, (void **)&ctx->erfc_tab64, sizeof(double) * tab.size());
         if (rc) return rc;
         e = cudaMemcpyAsync(ctx->erfc_tab64, tab.data(), sizeof(double) * tab.size(),
                             cudaMemcpyHostToDevice, ctx->alloc_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_stream);
         rc = cuda_check(ctx, e, "erfc table upload");
         if (rc) return rc;
     }
 
-    // cuFFT plans with a work area from this library's allocator (no allocation inside cuFFT)
-    cufftResult cr = cufftCreate(&ctx->plan_r2c);
-    if (cr == CUFFT_SUCCESS) cr = cufftCreate(&ctx->plan_c2r);
-    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftCreate failed (%d)", (int)cr);
-    ctx->have_plans = true;
+    // cuFFT plans (from the plan pool) with a work area from this library's
+    // allocator (no allocation inside cuFFT)
     size_t ws1 = 0, ws2 = 0;
-    cr = cufftSetAutoAllocation(ctx->plan_r2c, 0);
-    if (cr == CUFFT_SUCCESS) cr = cufftSetAutoAllocation(ctx->plan_c2r, 0);
-    if (cr == CUFFT_SUCCESS)
-        cr = cufftMakePlan3d(ctx->plan_r2c, ctx->K[0], ctx->K[1], ctx->K[2],
-                             ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z, &ws1);
-    if (cr == CUFFT_SUCCESS)
-        cr = cufftMakePlan3d(ctx->plan_c2r, ctx->K[0], ctx->K[1], ctx->K[2],
-                             ctx->fp32 ? CUFFT_C2R : CUFFT_Z2D, &ws2);
-    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftMakePlan3d failed (%d)", (int)cr);
+    const cufftType t1 = ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z, t2 = ctx->fp32 ? CUFFT_C2R : CUFFT_Z2D;
+    cufftResult cr = plan_acquire(ctx->device, ctx->K, t1, &ctx->plan_r2c, &ws1);
+    if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cuFFT plan failed (%d)", (int)cr);
+    cr = plan_acquire(ctx->device, ctx->K, t2, &ctx->plan_c2r, &ws2);
+    if (cr != CUFFT_SUCCESS) {
+        plan_release(ctx->device, ctx->K, t1, ctx->plan_r2c, ws1);
+        return set_error(ctx, QEQ_ERR_CUFFT, "cuFFT plan failed (%d)", (int)cr);
+    }
+    ctx->have_plans = true;
+    ctx->plan_ws[0] = ws1;
+    ctx->plan_ws[1] = ws2;
     rc = dev_alloc(ctx, &ctx->fft_work, ws1 > ws2 ? ws1 : ws2);
     if (rc) return rc;
     cr = cufftSetWorkArea(ctx->plan_r2c, ctx->fft_work);
     if (cr == CUFFT_SUCCESS) cr = cufftSetWorkArea(ctx->plan_c2r, ctx->fft_work);
     if (cr != CUFFT_SUCCESS) return set_error(ctx, QEQ_ERR_CUFFT, "cufftSetWorkArea failed (%d)", (int)cr);
     return QEQ_OK;
+}
+
+// cuFFT plan pool.  Planning a 3D FFT costs milliseconds, which dominated the
+// creation of short-lived contexts (the serving loop creates one per request).
+// A destroyed context returns its plans here instead of destroying them, and a
+// new context with the same device, mesh and transform takes them back.  A
+// plan is held by one context at a time; its stream and work area are set by
+// the holder.  At most kMaxPooledPlans idle plans are kept per key.
+namespace {
+struct PlanKey {
+    int dev, K0, K1, K2, type;
+    bool operator<(const PlanKey &o) const {
+        return std::tie(dev, K0, K1, K2, type) < std::tie(o.dev, o.K0, o.K1, o.K2, o.type);
+    }
+};
+constexpr size_t kMaxPooledPlans = 32;
+std::mutex g_plan_mutex;
+std::map<PlanKey, std::vector<std::pair<cufftHandle, size_t>>> g_plan_pool;
+}  // namespace
+
+cufftResult plan_acquire(int dev, const int K[3], cufftType type, cufftHandle *out, size_t *ws) {
+    const PlanKey key{dev, K[0], K[1], K[2], (int)type};
+    {
+        std::lock_guard<std::mutex> lock(g_plan_mutex);
+        auto it = g_plan_pool.find(key);
+        if (it != g_plan_pool.end() && !it->second.empty()) {
+            *out = it->second.back().first;
+            *ws = it->second.back().second;
+            it->second.pop_back();
+            return CUFFT_SUCCESS;
+        }
+    }
+    cufftHandle h = 0;
+    cufftResult cr = cufftCreate(&h);
+    if (cr != CUFFT_SUCCESS) return cr;
+    cr = cufftSetAutoAllocation(h, 0);
+    if (cr == CUFFT_SUCCESS) cr = cufftMakePlan3d(h, K[0], K[1], K[2], type, ws);
+    if (cr != CUFFT_SUCCESS) {
+        cufftDestroy(h);
+        return cr;
+    }
+    *out = h;
+    return CUFFT_SUCCESS;
+}
+
+void plan_release(int dev, const int K[3], cufftType type, cufftHandle h, size_t ws) {
+    const PlanKey key{dev, K[0], K[1], K[2], (int)type};
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    auto &v = g_plan_pool[key];
+    if (v.size() < kMaxPooledPlans) {
+        v.emplace_back(h, ws);
+        return;
+    }
+    cufftDestroy(h);
 }
 
 int real_tile_reserve(qeq_ctx *ctx) {
@@ -1363,8 +1465,10 @@ int real_tile_reserve(qeq_ctx *ctx) {
 
 void coulomb_free(qeq_ctx *ctx) {
     if (ctx->have_plans) {
-        cufftDestroy(ctx->plan_r2c);
-        cufftDestroy(ctx->plan_c2r);
+        plan_release(ctx->device, ctx->K, ctx->fp32 ? CUFFT_R2C : CUFFT_D2Z, ctx->plan_r2c,
+                     ctx->plan_ws[0]);
+        plan_release(ctx->device, ctx->K, ctx->fp32 ? CUFFT_C2R : CUFFT_Z2D, ctx->plan_c2r,
+                     ctx->plan_ws[1]);
     }
     void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
                     ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,

@@ -306,6 +306,7 @@ struct qeq_ctx {
     void *meshc = nullptr;     // [K1][K2][K3/2+1] complex
     void *G = nullptr;         // influence function on the half spectrum (double or float)
     cufftHandle plan_r2c = 0, plan_c2r = 0;
+    size_t plan_ws[2] = {0, 0};  // work-area sizes of the two plans
     bool have_plans = false;
     void *fft_work = nullptr;  // cuFFT work area (shared by both plans, one stream at a time)
     double *erfc_tab64 = nullptr;  // piecewise erfc coefficients of the FP64 real-space kernel
@@ -382,6 +383,10 @@ int coulomb_alloc(qeq_ctx *ctx);
 // Global tile scratch of the real-space kernels when the tile capacity exceeds
 // shared memory (after each neighbour build; allocates only when it must grow).
 int real_tile_reserve(qeq_ctx *ctx);
+// cuFFT plan pool (coulomb.cu): take an idle plan of this device, mesh and type
+// (or make one), and give it back when the context goes.
+cufftResult plan_acquire(int dev, const int K[3], cufftType type, cufftHandle *out, size_t *ws);
+void plan_release(int dev, const int K[3], cufftType type, cufftHandle h, size_t ws);
 void coulomb_free(qeq_ctx *ctx);
 // v, E, F in original numbering; E / F / energy4 may be null; need_field=false
 // skips every field computation (potential-only apply).
