@@ -187,7 +187,7 @@ __device__ __forceinline__ int stage_tile(const BrickGeom &g, const int4 *__rest
     if (threadIdx.x == 0) *t_total = tile_tot[blockIdx.x];
     __syncthreads();
     const int total = *t_total;
-    if (total > cap) {
+    if (total + 1 > cap) {  // the tile plus its sentinel slot
         if (threadIdx.x == 0) atomicExch(&flags[kFlagTileOverflow], 1);
         return -1;
     }
@@ -206,6 +206,15 @@ __device__ __forceinline__ int stage_tile(const BrickGeom &g, const int4 *__rest
             tile[off + k] = x;
             tsg[off + k] = sg[st + k];
         }
+    }
+    // sentinel slot: the padding entries of the list point here, far from every
+    // atom (r^2 about 3e36 fails the cutoff test in both precisions)
+    if (threadIdx.x == 0) {
+        T4 far;
+        far.x = far.y = far.z = T(1e18);
+        far.w = T(0);
+        tile[total] = far;
+        tsg[total] = T(0);
     }
     __syncthreads();
     return total;
@@ -462,14 +471,13 @@ k_real32(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                 w1 = t + 8 < cl ? __ldg(pw + wstep) : make_uint2(0u, 0u);
                 const int ev[4] = {(int)(cur.x & 0xffffu), (int)(cur.x >> 16), (int)(cur.y & 0xffffu),
                                    (int)(cur.y >> 16)};
+                // entries past the row's end are padding (the far sentinel slot)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (t + u < cl) {
-                        const int e = ev[u];
-                        const float4 xc = tile[e];
-                        pair32<FIELD>(xc.x - xi.x, xc.y - xi.y, xc.z - xi.z, xc.w, tsg + e, si2,
-                                      gpre, a.pal_f, a.c1_f, a.rc2_f, a.tspa_f, tv, tx, ty, tz);
-                    }
+                    const int e = ev[u];
+                    const float4 xc = tile[e];
+                    pair32<FIELD>(xc.x - xi.x, xc.y - xi.y, xc.z - xi.z, xc.w, tsg + e, si2, gpre,
+                                  a.pal_f, a.c1_f, a.rc2_f, a.tspa_f, tv, tx, ty, tz);
                 }
             }
         }

@@ -81,7 +81,9 @@ enum Flag {
 // sorted atom j of tile brick rb is off[rb] + (j - start[rb]).
 // ---------------------------------------------------------------------------
 constexpr int kMaxTileBricks = 125;   // (2 br + 1)^3 with br <= 2
-constexpr int kMaxTileAtoms = 65535;  // 16-bit entries
+// 16-bit entries; index t_total (one past a brick's tile) is the padding entry
+// the emit writes after a row's last entry up to its 16-entry stripe.
+constexpr int kMaxTileAtoms = 65534;
 
 struct BrickGeom {
     int nc[3];    // cells per axis

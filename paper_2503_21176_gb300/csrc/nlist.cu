@@ -379,6 +379,14 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
                 cnt[i] = min(base, a.width);
                 if (base > a.width) atomicMax(&flags[kFlagMaxRow], base);
             }
+            // padding entries (the tile's far sentinel slot) up to the stripe end,
+            // so the real-space kernel reads whole 4-entry words without a guard
+            if (base <= a.width) {
+                const int pad_end = (base + kListStripe - 1) / kListStripe * kListStripe;
+                for (int k = base + ((s - base) % kEmitLanes + kEmitLanes) % kEmitLanes; k < pad_end;
+                     k += kEmitLanes)
+                    nbr[list_index(k, i, a.n)] = (uint16_t)t_total;
+            }
         }
     }
 }
