@@ -271,7 +271,8 @@ struct qeq_ctx {
     double *R_build = nullptr;      // [N][3] positions at the last build
     double4_32a *xs64 = nullptr;        // [N] wrapped positions at build (sorted)
     float4 *xs32 = nullptr;         // [N] FP32 copy
-    uint16_t *nbr = nullptr;        // [width][N] tile-local entries, column-major
+    uint16_t *nbr = nullptr;        // [width][N] tile-local entries (list_index layout)
+    uint32_t *nbr_scratch = nullptr;  // same shape, 32-bit: the emit's kept entries with their class
     int32_t *cnt = nullptr;         // [N] entries per sorted row
     int width = 0;
     qeq::BrickGeom geom{};

@@ -201,8 +201,7 @@ struct EmitArgs {
 // widths), inside the cutoff (d^2 < r_cut^2) and the skin beyond it.  Lanes that
 // run the same iteration of the real-space kernel then hold neighbours of the
 // same class, so its distance branches (cutoff test, Gaussian correction) agree
-// across the warp.  Pass 0 counts each class, pass 1 places the entries.
-constexpr int kClasses = 3;
+// across the warp.
 // Lanes per row in the emit: lane s of a row tests candidates s, s + 4, ... of
 // the row's candidate stream (its cell's (2 reach + 1)^3 neighbour cells,
 // concatenated).  Rows of one cell have the same stream, so the 8 rows of a warp
@@ -210,16 +209,6 @@ constexpr int kClasses = 3;
 constexpr int kEmitLanes = 4;
 constexpr int kMaxBrickCells = 8;
 constexpr int kCenterCode = 62;  // image code of the zero shift
-
-// Per-lane class counters, 16 bits a class in one 64-bit word (register
-// resident; a row holds at most 65535 entries, the tile limit).
-struct ClassCount {
-    unsigned long long v = 0;
-    __device__ __forceinline__ void add(int cls) {
-        v += cls == 0 ? 1ull : (cls == 1 ? (1ull << 16) : (1ull << 32));
-    }
-    __device__ __forceinline__ int get(int cls) const { return (int)((v >> (16 * cls)) & 0xffffu); }
-};
 
 // The candidate stream of one lane: cell k of the table, candidate j in it.
 struct Cursor {
@@ -237,31 +226,32 @@ __device__ __forceinline__ bool cursor_fix(Cursor &c, const int4 *__restrict__ t
     return true;
 }
 
-// One pass over a row's candidate stream.  PLACE = false counts the kept
-// entries per shell; PLACE = true writes each at the next slot of its shell
-// (start holds the lane's first slot per shell).  The FP64 decision is taken
-// only inside the band [lo, hi] of the FP32 distance.
-template <bool PLACE>
+// The test pass over a lane's candidate stream.  Lane s appends each kept
+// entry, with its distance class in bits 16-17, to its own slots 4 m + s of the
+// 32-bit scratch list (m < cap = width / 4), and counts each class; counts keep
+// running past cap (an overflow, reported for the regrowth).  The FP64 decision
+// is taken only inside the band [lo, hi] of the FP32 distance.
 __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, const int4 *__restrict__ tab,
                                             int ncand, const double4_32a &xi, const float4 &xf,
                                             const double4_32a *__restrict__ xs64,
-                                            const float4 *__restrict__ xs32, ClassCount &sc,
-                                            uint16_t *__restrict__ nbr) {
-    Cursor c;
-    c.k = 0;
-    c.ct = tab[0];
-    c.j = c.ct.x + s;
+                                            const float4 *__restrict__ xs32, int cap, int (&c)[3],
+                                            uint32_t *__restrict__ scr) {
+    Cursor cu;
+    cu.k = 0;
+    cu.ct = tab[0];
+    cu.j = cu.ct.x + s;
     int code = -1;
+    int m = 0;
     float shx = 0.f, shy = 0.f, shz = 0.f;
-    while (cursor_fix(c, tab, ncand)) {
-        if (c.ct.w != code) {
-            code = c.ct.w;
+    while (cursor_fix(cu, tab, ncand)) {
+        if (cu.ct.w != code) {
+            code = cu.ct.w;
             shx = (float)(code / 25 - 2) * a.Lfx;
             shy = (float)((code / 5) % 5 - 2) * a.Lfy;
             shz = (float)(code % 5 - 2) * a.Lfz;
         }
-        const int j = c.j;
-        c.j += kEmitLanes;
+        const int j = cu.j;
+        cu.j += kEmitLanes;
         if (code == kCenterCode && j == i) continue;
         const float4 xj = xs32[j];
         const float dxf = (xj.x - xf.x) + shx;
@@ -281,14 +271,13 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
             const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
             keep = d2 < a.rl2;
         }
-        if (keep) {
-            const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
-            if (PLACE) {
-                const int slot = sc.get(cls);
-                if (slot < a.width) nbr[list_index(slot, i, a.n)] = (uint16_t)(j + c.ct.z);
-            }
-            sc.add(cls);
-        }
+        if (!keep) continue;
+        const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
+        if (m < cap) scr[list_index(kEmitLanes * m + s, i, a.n)] = (uint32_t)(j + cu.ct.z) | ((uint32_t)cls << 16);
+        ++m;
+        c[0] += cls == 0;
+        c[1] += cls == 1;
+        c[2] += cls == 2;
     }
 }
 
@@ -301,8 +290,8 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
 __global__ void __launch_bounds__(kEmitThreads)
 k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
        const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
-       uint16_t *__restrict__ nbr, int32_t *__restrict__ cnt, int4 *__restrict__ tile_tab,
-       int32_t *__restrict__ tile_tot, int32_t *__restrict__ flags) {
+       uint16_t *__restrict__ nbr, uint32_t *__restrict__ scr, int32_t *__restrict__ cnt,
+       int4 *__restrict__ tile_tab, int32_t *__restrict__ tile_tot, int32_t *__restrict__ flags) {
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
     const int64_t b = blockIdx.x;
@@ -346,47 +335,54 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
     const int s = lane % kEmitLanes;
     const int nrows = i1 - i0;
     const int rows_per_warp = 32 / kEmitLanes;
+    const int cap = a.width / kEmitLanes;
     for (int r0 = warp * rows_per_warp; r0 < nrows; r0 += nw * rows_per_warp) {
         const int r = r0 + lane / kEmitLanes;
         const bool act = r < nrows;
         const int i = i0 + (act ? r : 0);
-        const int4 *tab = ctab[act ? cell_s[i] - (int)(b * g.bvol) : 0];
-        const double4_32a xi = xs64[i];
-        const float4 xf = xs32[i];
-        ClassCount sc;
-        if (act) emit_stream<false>(a, i, s, tab, ncand, xi, xf, xs64, xs32, sc, nbr);
-        // row totals per class and this lane's first slot in each class
-        ClassCount incl = sc;  // inclusive prefix over the row's lanes
-#pragma unroll
-        for (int o = 1; o < kEmitLanes; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl.v, o);
-            if (s >= o) incl.v += y;
-        }
-        const int last = (lane / kEmitLanes) * kEmitLanes + kEmitLanes - 1;
-        ClassCount tot;
-        tot.v = __shfl_sync(0xffffffffu, incl.v, last);
-        ClassCount start;
-        int base = 0;
-#pragma unroll
-        for (int k = 0; k < kClasses; ++k) {
-            const int before = incl.get(k) - sc.get(k);
-            start.v |= (unsigned long long)(base + before) << (16 * k);
-            base += tot.get(k);
-        }
+        int c[3] = {0, 0, 0};
         if (act) {
-            emit_stream<true>(a, i, s, tab, ncand, xi, xf, xs64, xs32, start, nbr);
-            if (s == 0) {
-                cnt[i] = min(base, a.width);
-                if (base > a.width) atomicMax(&flags[kFlagMaxRow], base);
+            const int4 *tab = ctab[cell_s[i] - (int)(b * g.bvol)];
+            emit_stream(a, i, s, tab, ncand, xs64[i], xs32[i], xs64, xs32, cap, c, scr);
+        }
+        const int mine = c[0] + c[1] + c[2];
+        // this lane's first row slot in each class: the classes in order, and in
+        // each class the lanes in order (exclusive scan over the row's 4 lanes)
+        int start[3], row_tot = 0, lane_max = mine;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int incl = c[k];
+#pragma unroll
+            for (int o = 1; o < kEmitLanes; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (s >= o) incl += y;
             }
-            // padding entries (the tile's far sentinel slot) up to the stripe end,
-            // so the real-space kernel reads whole 4-entry words without a guard
-            if (base <= a.width) {
-                const int pad_end = (base + kListStripe - 1) / kListStripe * kListStripe;
-                for (int k = base + ((s - base) % kEmitLanes + kEmitLanes) % kEmitLanes; k < pad_end;
-                     k += kEmitLanes)
-                    nbr[list_index(k, i, a.n)] = (uint16_t)t_total;
+            const int tot_k = __shfl_sync(0xffffffffu, incl, (lane / kEmitLanes) * kEmitLanes + kEmitLanes - 1);
+            start[k] = row_tot + incl - c[k];
+            row_tot += tot_k;
+        }
+#pragma unroll
+        for (int o = 1; o < kEmitLanes; o <<= 1)
+            lane_max = max(lane_max, __shfl_xor_sync(0xffffffffu, lane_max, o));
+        const bool fits = lane_max <= cap && row_tot <= a.width;
+        if (act && fits) {
+            // move this lane's entries to their row slots (class order, lanes
+            // interleaved inside a class), then pad to the stripe end with the
+            // tile's far sentinel slot
+            for (int m = 0; m < mine; ++m) {
+                const uint32_t v = scr[list_index(kEmitLanes * m + s, i, a.n)];
+                const int cls = (int)(v >> 16);
+                const int slot = cls == 0 ? start[0]++ : (cls == 1 ? start[1]++ : start[2]++);
+                nbr[list_index(slot, i, a.n)] = (uint16_t)(v & 0xffffu);
             }
+            const int pad_end = (row_tot + kListStripe - 1) / kListStripe * kListStripe;
+            for (int k = row_tot + ((s - row_tot) % kEmitLanes + kEmitLanes) % kEmitLanes; k < pad_end;
+                 k += kEmitLanes)
+                nbr[list_index(k, i, a.n)] = (uint16_t)t_total;
+        }
+        if (act && s == 0) {
+            cnt[i] = fits ? row_tot : 0;
+            if (!fits) atomicMax(&flags[kFlagMaxRow], max(row_tot, kEmitLanes * lane_max));
         }
     }
 }
@@ -521,8 +517,12 @@ int nl_alloc_list(qeq_ctx *ctx, int width) {
         return set_error(ctx, QEQ_ERR_CAPACITY, "neighbour row of %d entries exceeds the limit %d",
                          width, kMaxWidthLimit);
     dev_free(ctx, ctx->nbr);
+    dev_free(ctx, ctx->nbr_scratch);
     ctx->nbr = nullptr;
+    ctx->nbr_scratch = nullptr;
     int rc = dev_alloc(ctx, (void **)&ctx->nbr, sizeof(uint16_t) * (size_t)width * ctx->n);
+    if (rc) return rc;
+    rc = dev_alloc(ctx, (void **)&ctx->nbr_scratch, sizeof(uint32_t) * (size_t)width * ctx->n);
     if (rc) return rc;
     ctx->width = width;
     return QEQ_OK;
@@ -570,7 +570,7 @@ void nl_free(qeq_ctx *ctx) {
     void *ptrs[] = {ctx->cell_of, ctx->cell_count, ctx->cell_start, ctx->cell_fill, ctx->tmp_list,
                     ctx->perm,    ctx->cell_s,     ctx->wrap_off,   ctx->R_build,   ctx->xs64,
                     ctx->xs32,    ctx->nbr,        ctx->cnt,        ctx->d_flags,
-                    ctx->tile_tab, ctx->tile_tot};
+                    ctx->tile_tab, ctx->tile_tot, ctx->nbr_scratch};
     for (void *p : ptrs) dev_free(ctx, p);
     delete[] ctx->h_flags;
 }
@@ -590,8 +590,8 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     a.t_cut = (float)(ctx->p.r_cut * ctx->p.r_cut);
     a.width = ctx->width;
     k_emit<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
-        a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr, ctx->cnt,
-        ctx->tile_tab, ctx->tile_tot, ctx->d_flags);
+        a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr,
+        ctx->nbr_scratch, ctx->cnt, ctx->tile_tab, ctx->tile_tot, ctx->d_flags);
 }
 
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
