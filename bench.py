@@ -275,23 +275,19 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
 def e2e_steps(qg, md, steps, stream, device):
     """Same step through the C ABI with the state kept in HOST memory: every step
     copies the whole MD state (R, V, F, K f, n history) and the per-atom parameters
-    from pinned host buffers to the device, runs the step, and copies the advanced
-    state, the charges and the energies back to pinned host buffers, all inside the
-    timed region.  Two host state buffers alternate (the results of step k are the
-    inputs of step k + 1), so the trajectory stays on the host with no host copy."""
+    from pinned host memory to the device, runs the step, and copies the advanced
+    state, the charges and the energies back to pinned host memory, all inside the
+    timed region.  The step works on one contiguous device buffer (ShadowMD.pack),
+    so each direction is one copy; two host buffers alternate (the results of step
+    k are the inputs of step k + 1), so the trajectory stays on the host with no
+    host copy."""
     import torch
 
-    names_state = ["R", "V", "F", "Kf", "n_hist"]
-    names_param = ["chi", "eta", "sigma", "mass"]
-    names_extra = ["q", "energies"]
-    dev = {k: getattr(md, k) for k in names_state + names_param + names_extra}
-    host = [{k: dev[k].cpu().pin_memory() for k in names_state},
-            {k: torch.empty_like(dev[k], device="cpu").pin_memory() for k in names_state}]
-    host_par = {k: dev[k].cpu().pin_memory() for k in names_param}
-    host_extra = {k: torch.empty_like(dev[k], device="cpu").pin_memory() for k in names_extra}
-    nbytes = lambda ts: sum(v.numel() * v.element_size() for v in ts)
-    h2d = nbytes(list(host[0].values()) + list(host_par.values()))
-    d2h = nbytes(list(host[1].values()) + list(host_extra.values()))
+    dev_buf, (n_par, n_state, n_res) = md.pack()
+    host = [dev_buf.cpu().pin_memory(), torch.empty_like(dev_buf, device="cpu").pin_memory()]
+    host[1][:n_par].copy_(host[0][:n_par])  # the parameters, in both buffers
+    n_in, n_out = n_par + n_state, n_state + n_res
+    h2d, d2h = 8 * n_in, 8 * n_out
     with torch.cuda.stream(stream):
         torch.cuda.synchronize(device)
         t0 = torch.cuda.Event(enable_timing=True)
@@ -299,15 +295,9 @@ def e2e_steps(qg, md, steps, stream, device):
         t0.record(stream)
         for k in range(steps):
             src, dst = host[k % 2], host[(k + 1) % 2]
-            for name in names_state:
-                dev[name].copy_(src[name], non_blocking=True)
-            for name in names_param:
-                dev[name].copy_(host_par[name], non_blocking=True)
+            dev_buf[:n_in].copy_(src[:n_in], non_blocking=True)
             md.step(1, stream)
-            for name in names_state:
-                dst[name].copy_(dev[name], non_blocking=True)
-            for name in names_extra:
-                host_extra[name].copy_(dev[name], non_blocking=True)
+            dst[n_par:].copy_(dev_buf[n_par:], non_blocking=True)
             stream.synchronize()  # the caller reads the step's results on the host
         t1.record(stream)
         torch.cuda.synchronize(device)

@@ -147,6 +147,33 @@ class ShadowMD:
     def init(self, stream=None):
         qeq_shadow_init(self.sys.ctx, self._prm, self._st, stream)
 
+    # order of the tensors in pack(): parameters, then the state the step advances,
+    # then its results
+    PACK_PARAMS = ("chi", "eta", "sigma", "mass")
+    PACK_STATE = ("R", "V", "F", "Kf", "n_hist")
+    PACK_RESULTS = ("q", "energies")
+
+    def pack(self):
+        """Re-home parameters, state and results into one contiguous float64 device
+        buffer [chi, eta, sigma, mass | R, V, F, Kf, n_hist | q, energies] and point
+        the step at it.  Returns (buffer, (n_params, n_state, n_results)) in elements,
+        so a caller that keeps the state on the host moves it with one copy each way:
+        H2D of buffer[:n_params + n_state], D2H of buffer[n_params:]."""
+        names = self.PACK_PARAMS + self.PACK_STATE + self.PACK_RESULTS
+        sizes = [getattr(self, k).numel() for k in names]
+        buf = torch.empty(sum(sizes), dtype=torch.float64, device=self.sys.device)
+        off = 0
+        for k, sz in zip(names, sizes):
+            t = getattr(self, k)
+            view = buf[off:off + sz].view(t.shape)
+            view.copy_(t)
+            setattr(self, k, view)
+            off += sz
+        self._prm = md_params(self.chi, self.eta, self.sigma, self.mass)
+        self._st = md_state(self.R, self.V, self.F, self.Kf, self.n_hist, self.q, self.energies)
+        count = lambda group: sum(getattr(self, k).numel() for k in group)
+        return buf, (count(self.PACK_PARAMS), count(self.PACK_STATE), count(self.PACK_RESULTS))
+
     def step(self, n_steps: int = 1, stream=None):
         if n_steps == 1:
             qeq_shadow_step(self.sys.ctx, self._prm, self._st, stream)

@@ -164,3 +164,34 @@ def test_graph_replay_equals_eager_steps():
     assert rel_max(q1, q0) < 1e-10
     assert abs(e1 - e0) < 1e-10 * abs(e0)
     assert c1[0] == c0[0] and c1[2] == c0[2]  # same kernel and apply counts either way
+
+
+def test_packed_state_gives_the_same_trajectory():
+    """ShadowMD.pack() re-homes the state into one buffer; the steps are unchanged."""
+    qg = cuda_or_skip()
+    import torch
+
+    w = water_box(100, seed=31)
+    V0 = _maxwell(w, 0.025852, 32)
+    outs = []
+    for packed in (False, True):
+        p = qg.make_params(w.n_atoms, w.box, alpha=0.34, r_cut=7.0, skin=1.0, mesh=(24, 24, 24),
+                           order=4, precision="fp32_mixed", krylov_rank=2, dt=0.5)
+        s = qg.System(p)
+        md = qg.ShadowMD(s, dev_tensor(w.chi), dev_tensor(w.eta), dev_tensor(w.sigma),
+                         dev_tensor(w.mass), dev_tensor(w.R), dev_tensor(V0),
+                         torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda"))
+        md.init()
+        if packed:
+            buf, (n_par, n_state, n_res) = md.pack()
+            assert buf.numel() == n_par + n_state + n_res
+            assert md.R.data_ptr() == buf[n_par:].data_ptr()
+        stream = torch.cuda.Stream()
+        for _ in range(6):
+            md.step(1, stream)
+        torch.cuda.synchronize()
+        outs.append((md.R.cpu().numpy(), md.q.cpu().numpy(), md.energy_dict()["total"]))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
