@@ -158,7 +158,8 @@ class ShadowMD:
         buffer [chi, eta, sigma, mass | R, V, F, Kf, n_hist | q, energies] and point
         the step at it.  Returns (buffer, (n_params, n_state, n_results)) in elements,
         so a caller that keeps the state on the host moves it with one copy each way:
-        H2D of buffer[:n_params + n_state], D2H of buffer[n_params:]."""
+        H2D of buffer[:n_params + n_state], D2H of buffer[n_params:].  Waits for the
+        device (a one-time set-up step)."""
         names = self.PACK_PARAMS + self.PACK_STATE + self.PACK_RESULTS
         sizes = [getattr(self, k).numel() for k in names]
         buf = torch.empty(sum(sizes), dtype=torch.float64, device=self.sys.device)
@@ -171,6 +172,7 @@ class ShadowMD:
             off += sz
         self._prm = md_params(self.chi, self.eta, self.sigma, self.mass)
         self._st = md_state(self.R, self.V, self.F, self.Kf, self.n_hist, self.q, self.energies)
+        torch.cuda.synchronize(self.sys.device)  # the copies ran on the current stream
         count = lambda group: sum(getattr(self, k).numel() for k in group)
         return buf, (count(self.PACK_PARAMS), count(self.PACK_STATE), count(self.PACK_RESULTS))
 

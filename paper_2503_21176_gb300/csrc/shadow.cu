@@ -176,24 +176,45 @@ __global__ void k_normalize(int n, const double *__restrict__ scal, double *__re
         x[i] *= inv;
 }
 
-// partials of O_ab = <R_a, R_b> (a <= b) and g_a = <R_a, f>
-__global__ void k_normal_part(int n, int m, const double *__restrict__ Rb,
-                              const double *__restrict__ f, double *__restrict__ part) {
-    double acc[kMaxRank * (kMaxRank + 1) / 2 + kMaxRank];
-    const int nO = m * (m + 1) / 2;
-    for (int k = 0; k < nO + m; ++k) acc[k] = 0.0;
+// partials of O_ab = <R_a, R_b> (a <= b) and g_a = <R_a, f>; the rank M is a
+// template parameter so that the accumulators stay in registers.
+template <int M>
+__global__ void k_normal_part(int n, const double *__restrict__ Rb, const double *__restrict__ f,
+                              double *__restrict__ part) {
+    constexpr int nO = M * (M + 1) / 2;
+    double acc[nO + M];
+#pragma unroll
+    for (int k = 0; k < nO + M; ++k) acc[k] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double r[kMaxRank];
-        for (int a = 0; a < m; ++a) r[a] = Rb[(size_t)a * n + i];
+        double r[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) r[a] = Rb[(size_t)a * n + i];
+        const double fi = f[i];
         int k = 0;
-        for (int a = 0; a < m; ++a)
-            for (int b = a; b < m; ++b) acc[k++] += r[a] * r[b];
-        for (int a = 0; a < m; ++a) acc[nO + a] += r[a] * f[i];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = a; b < M; ++b) acc[k++] += r[a] * r[b];
+#pragma unroll
+        for (int a = 0; a < M; ++a) acc[nO + a] += r[a] * fi;
     }
-    for (int k = 0; k < nO + m; ++k) {
-        double vals[1] = {acc[k]};
-        block_sum<1>(vals);
-        if (threadIdx.x == 0) part[k * kRedBlocks + blockIdx.x] = vals[0];
+    block_sum<nO + M>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < nO + M; ++k) part[k * kRedBlocks + blockIdx.x] = acc[k];
+}
+
+void launch_normal_part(int m, int n, const double *Rb, const double *f, double *part,
+                        cudaStream_t s) {
+    switch (m) {
+        case 1: k_normal_part<1><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 2: k_normal_part<2><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 3: k_normal_part<3><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 4: k_normal_part<4><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 5: k_normal_part<5><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 6: k_normal_part<6><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 7: k_normal_part<7><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        default: k_normal_part<8><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
     }
 }
 
@@ -205,13 +226,14 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
                                double *__restrict__ scal, double *__restrict__ energies) {
     __shared__ double sums[kMaxRank * (kMaxRank + 1) / 2 + kMaxRank];
     const int nO = m * (m + 1) / 2;
-    for (int k = 0; k < nO + m; ++k) {
+    // one warp per slot, lanes over the block partials in a fixed order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < nO + m; k += nw) {
         double acc = 0.0;
         const double *p = part + (size_t)k * kRedBlocks;
-        for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) acc += p[b];
-        double vals[1] = {acc};
-        block_sum<1>(vals);
-        if (threadIdx.x == 0) sums[k] = vals[0];
+        for (int b = lane; b < kRedBlocks; b += 32) acc += p[b];
+        acc = warp_sum(acc);
+        if (lane == 0) sums[k] = acc;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -479,7 +501,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     auto solve_rank = [&](int k, bool *done) -> int {
         const int nO = k * (k + 1) / 2;
         prof_begin(ctx, kPhShadow, s);
-        k_normal_part<<<G, kThreads, 0, s>>>(n, k, ctx->Rb, ctx->fvec, part);
+        launch_normal_part(k, n, ctx->Rb, ctx->fvec, part, s);
         k_normal_solve<<<1, kThreads, 0, s>>>(k, ctx->p.q_tot, k + 1, part, scal, st->energies);
         ctx->launches += 2;
         prof_end(ctx, s);

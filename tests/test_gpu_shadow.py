@@ -182,6 +182,7 @@ def test_packed_state_gives_the_same_trajectory():
                          dev_tensor(w.mass), dev_tensor(w.R), dev_tensor(V0),
                          torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda"))
         md.init()
+        torch.cuda.synchronize()  # init ran on the default stream, the steps on another
         if packed:
             buf, (n_par, n_state, n_res) = md.pack()
             assert buf.numel() == n_par + n_state + n_res
