@@ -309,7 +309,9 @@ static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_st
             return rc;
         }
         if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture end");
-        e = cudaGraphInstantiate(&ctx->step_exec, g, 0);
+        // node priorities on: the mesh chain's kernels keep the priority of the
+        // side stream they were captured on
+        e = cudaGraphInstantiate(&ctx->step_exec, g, cudaGraphInstantiateFlagUseNodePriority);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
             return cuda_check(ctx, e, "graph instantiate");

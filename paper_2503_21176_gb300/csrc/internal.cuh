@@ -312,6 +312,10 @@ struct qeq_ctx {
     size_t plan_ws[2] = {0, 0};  // work-area sizes of the two plans
     bool have_plans = false;
     void *fft_work = nullptr;  // cuFFT work area (shared by both plans, one stream at a time)
+    // High-priority side stream of the mesh chain (spread, FFTs, influence) and
+    // its fork / join events: the chain runs beside the real-space kernel.
+    cudaStream_t pme_stream = nullptr;
+    cudaEvent_t pme_fork = nullptr, pme_join = nullptr;
     double *erfc_tab64 = nullptr;  // piecewise erfc coefficients of the FP64 real-space kernel
 
     // ---- explicit k-vector Ewald (ewald.cu) ----
