@@ -44,10 +44,10 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PAIR_OPS = 40
 # DRAM bytes (read + write) per launch of the FP32 real-space kernel (potential
 # and field): ncu --set full of k_real32<1,0> on the 120,000-atom water box
-# (profiles/ncu_kernels_fp32_water120k.md: 78.71 MB read + 1.79 MB written),
+# (profiles/ncu_kernels_fp32_water120k.md: 78.63 MB read + 1.86 MB written),
 # scaled to the 300,000-atom box by the list entries processed (x 2.5).  Valid
 # for the kernel version that capture was taken of.
-REAL32_TRAFFIC_BYTES = (78.71e6 + 1.79e6) * 2.5
+REAL32_TRAFFIC_BYTES = (78.63e6 + 1.86e6) * 2.5
 SM_COUNT, FP32_LANES, FP64_LANES = 152, 128, 2
 T_EV = 0.025852  # k_B * 300 K in eV
 
