@@ -97,6 +97,7 @@ struct RealArgs {
     // conversion in the kernel runs on the FP64 pipe (1/64 rate on GB300), and
     // under register pressure the compiler re-derives such values inside the loop.
     float alpha_f, rc2_f, tspa_f, c1_f, pal_f, Lx_f, Ly_f, Lz_f;
+    int fg_pieces;  // pieces of the FP64 pair-function table (0: direct erfc path only)
 };
 
 // FP64 erfc by a piecewise polynomial: [0, kErfcXMax) is cut into kErfcPieces
@@ -130,6 +131,29 @@ __device__ __forceinline__ double erfc_pw(const double *__restrict__ tab, double
     return p;
 }
 
+// FP64 pair functions of s = r^2 by piecewise polynomials:
+//   F(s) = erfc(alpha sqrt s) / sqrt s,
+//   G(s) = F'(r) / r = -(F(s) + (2 alpha / sqrt pi) exp(-alpha^2 s)) / s,
+// so that a pair adds q_j F to the potential and q_j G (r_j - r_i) to the field
+// without a square root or an erfc evaluation.  Octave e (2^e <= s < 2^(e+1))
+// of the s range [2^kFGOctLo, 2^(kFGOctLo + kFGMaxOct)) is cut into
+// 2^kFGSubLog2 equal pieces; on each piece F and G are the degree-(kFGCoef - 1)
+// polynomials in x in [-1, 1) through the Chebyshev nodes of the piece, from the
+// host's long-double erfc and exp (fg_table()).  The piece and x come from the
+// bits of s alone: the exponent and the top kFGSubLog2 mantissa bits are the
+// piece, the remaining mantissa bits the position in it (x = 2 y - 3 for the
+// double y in [1, 2) that holds them), so only the two Horner passes run on the
+// FP64 pipe.  A piece ends at least 32 half-widths from the singularity at
+// s = 0; the Gaussian factor exp(-alpha^2 s) bounds the error at large s, so
+// the host measures every piece and keeps the table only up to the first one
+// worse than 1e-13 relative (fg_valid_pieces()).  Pairs outside the table
+// (r < 0.5 A, or beyond the kept pieces) take the direct erfc path.
+constexpr int kFGOctLo = -2;
+constexpr int kFGSubLog2 = 4;
+constexpr int kFGCoef = 9;
+constexpr int kFGMaxOct = 8;
+constexpr int kFGMaxPieces = kFGMaxOct << kFGSubLog2;
+
 // Lanes per neighbour row.  kTPR consecutive lanes share one row: lane s takes
 // the row's entries s, s + kTPR, ..., which the list stores next to each other
 // (kListGroup), and their partial sums are combined with warp shuffles.
@@ -155,7 +179,7 @@ constexpr bool kRealLazySigma = QEQ_REAL_LAZY_SIGMA != 0;
 constexpr size_t kTile32Bytes = 20, kTile64Bytes = 40;
 constexpr size_t kSmemPerBlock = 232448;
 constexpr size_t kReal32SmemMax = kSmemPerBlock - 4096;
-constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096 - sizeof(double) * kErfcPieces * kErfcCoef;
+constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096 - sizeof(double2) * kFGMaxPieces * kFGCoef;
 
 // Brick spreading: block size and the largest shared-memory window it takes.
 constexpr int kSpreadThreads = 128;
@@ -229,23 +253,35 @@ __device__ __forceinline__ void home_rows(const BrickGeom &g, const int *t_start
     nrows = end - off;
 }
 
+// A non-negative double, from its high word, as a float truncated toward zero
+// (relative error below 2^-20; 0 below the float range), on the integer pipe.
+__device__ __forceinline__ float hi_to_float(int hi) {
+    const int b = hi - (896 << 20);  // rebias the exponent from 1023 to 127
+    return b > 0 ? __int_as_float(b << 3) : 0.0f;
+}
+// kErfcXMax^2 with the margin of the FP32 Gaussian-correction test.
+constexpr float kGaussTest = (float)(kErfcXMax * kErfcXMax * (1.0 + 1e-5));
+
 // FP64 real space, one block per brick: the tile (double4 positions with q,
-// sigma) and the erfc table in shared memory (GTILE: the tile in the block's
-// slice of a global scratch buffer instead), kTPR lanes per row.
+// sigma) and the pair-function table in shared memory (GTILE: the tile in the
+// block's slice of a global scratch buffer instead), kTPR lanes per row.  The
+// erfc table of the Gaussian correction and of the direct path is read through
+// the read-only cache.
 template <bool FIELD, bool GTILE>
 __global__ void __launch_bounds__(kRealMaxThreads, 2)
 k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32_t *__restrict__ tile_tot,
          const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const double4_32a *__restrict__ xq, const double *__restrict__ sg,
-         const double *__restrict__ erfc_tab, int cap, unsigned char *__restrict__ gtile,
-         int32_t *__restrict__ flags, double *__restrict__ v_s, double *__restrict__ E_s) {
+         const double *__restrict__ erfc_tab, const double2 *__restrict__ fg_tab, int cap,
+         unsigned char *__restrict__ gtile, int32_t *__restrict__ flags, double *__restrict__ v_s,
+         double *__restrict__ E_s) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    __shared__ double tab[kErfcPieces * kErfcCoef];
+    __shared__ double2 fg[kFGMaxPieces * kFGCoef];
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile64Bytes : smem_raw;
     double4_32a *tile = (double4_32a *)base;
     double *tsg = (double *)(base + (size_t)cap * 32);
-    for (int t = threadIdx.x; t < kErfcPieces * kErfcCoef; t += blockDim.x) tab[t] = erfc_tab[t];
+    for (int t = threadIdx.x; t < a.fg_pieces * kFGCoef; t += blockDim.x) fg[t] = fg_tab[t];
     const int total = stage_tile<double4_32a, double>(g, tile_tab, tile_tot, xq, sg, a.Lx, a.Ly, a.Lz, cap,
                                                      tile, tsg, t_start, t_base, t_code, &t_total,
                                                      flags);
@@ -253,6 +289,8 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
     int i0, offc, nrows;
     home_rows(g, t_start, t_base, total, i0, offc, nrows);
     const double al = a.alpha;
+    const unsigned npieces = (unsigned)a.fg_pieces;
+    const long long rc2_bits = __double_as_longlong(a.rc2);
     const int rpp = blockDim.x / kTPR;
     for (int r0 = 0; r0 < nrows; r0 += rpp) {
         const int r = r0 + threadIdx.x / kTPR, sub = threadIdx.x % kTPR;
@@ -262,6 +300,7 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
             const int i = i0 + r;
             const double4_32a xi = tile[offc + r];
             const double si2 = tsg[offc + r] * tsg[offc + r];
+            const float si2f = hi_to_float(__double2hiint(si2));
             const int c = cnt[i];
             for (int k = sub; k < c; k += kTPR) {
                 const int e = nbr[list_index(k, i, a.n)];
@@ -270,24 +309,52 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                 const double dy = xj.y - xi.y;
                 const double dz = xj.z - xi.z;
                 const double r2 = dx * dx + dy * dy + dz * dz;
-                if (!(r2 < a.rc2)) continue;
-                const double ir = rsqrt(r2);
-                const double rr = r2 * ir;
-                double d1;
-                double f = erfc_pw(tab, al * rr, d1) * ir;
-                double dfr = (al * d1 - f) * ir;  // d/dr [erfc(alpha r) / r]
-                const double g2 = si2 + tsg[e] * tsg[e];
-                // Gaussian correction; the table is exactly 0 beyond r / gamma = kErfcXMax
-                if (r2 < kErfcXMax * kErfcXMax * g2) {
+                // r2 >= 0, so the cutoff test compares the bit patterns (integer pipe)
+                if (!(__double_as_longlong(r2) < rc2_bits)) continue;
+                // f = erfc(alpha r) / r, gc = (d/dr f) / r
+                double f, gc;
+                const int hi = __double2hiint(r2);
+                const unsigned piece =
+                    (unsigned)((hi >> (20 - kFGSubLog2)) - ((1023 + kFGOctLo) << kFGSubLog2));
+                if (piece < npieces) {
+                    const unsigned lo = (unsigned)__double2loint(r2);
+                    const int hy = 0x3FF00000 | ((hi << kFGSubLog2) & 0x000FFFFF) |
+                                   (int)(lo >> (32 - kFGSubLog2));
+                    const double x = fma(__hiloint2double(hy, (int)(lo << kFGSubLog2)), 2.0, -3.0);
+                    const double2 *cf = fg + piece * kFGCoef;
+                    double2 cm = cf[kFGCoef - 1];
+                    f = cm.x;
+                    gc = cm.y;
+#pragma unroll
+                    for (int m = kFGCoef - 2; m >= 0; --m) {
+                        cm = cf[m];
+                        f = fma(f, x, cm.x);
+                        gc = fma(gc, x, cm.y);
+                    }
+                } else {
+                    const double ir = rsqrt(r2);
+                    double d1;
+                    f = erfc_pw(erfc_tab, al * (r2 * ir), d1) * ir;
+                    gc = (al * d1 - f) * ir * ir;
+                }
+                // Gaussian correction; the erfc table is exactly 0 beyond r / gamma =
+                // kErfcXMax.  The test runs in FP32 on values truncated from the
+                // high words of r^2 and sigma_j (each at most 2^-20 low) with a
+                // 1e-5 margin, so it never drops a pair the FP64 test would keep,
+                // and a pair it keeps beyond the bound adds exactly 0.
+                const float sjf = hi_to_float(((const int *)tsg)[2 * e + 1]);
+                if (hi_to_float(hi) < kGaussTest * fmaf(sjf, sjf, si2f)) {
+                    const double g2 = si2 + tsg[e] * tsg[e];
+                    const double ir = rsqrt(r2);
                     const double ig = rsqrt(g2);
                     double d2;
-                    const double fg = erfc_pw(tab, rr * ig, d2) * ir;
-                    f -= fg;
-                    dfr -= (ig * d2 - fg) * ir;
+                    const double fg2 = erfc_pw(erfc_tab, (r2 * ir) * ig, d2) * ir;
+                    f -= fg2;
+                    gc -= (ig * d2 - fg2) * ir * ir;
                 }
                 v += xj.w * f;
                 if (FIELD) {
-                    const double gq = xj.w * dfr * ir;
+                    const double gq = xj.w * gc;
                     ex += gq * dx;
                     ey += gq * dy;
                     ez += gq * dz;
@@ -993,6 +1060,110 @@ std::vector<double> erfc_table() {
     return out;
 }
 
+// Pair-function table of the FP64 real-space kernel for a given alpha: npieces
+// pieces of kFGCoef (F, G) coefficient pairs, piece p covering octave
+// e = kFGOctLo + p / 2^kFGSubLog2, sub-piece j = p mod 2^kFGSubLog2, i.e.
+// s = 2^e (1 + (j + (x + 1) / 2) / 2^kFGSubLog2) for x in [-1, 1).  The
+// interpolation nodes are the same Chebyshev nodes in x for every piece, so the
+// Vandermonde matrix in x is inverted once (Gauss-Jordan with partial pivoting
+// in long double) and applied to the long-double F and G at the nodes of each
+// piece.
+std::vector<double> fg_table(double alpha, int npieces) {
+    const int D = kFGCoef;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    long double xs[kFGCoef], W[kFGCoef][2 * kFGCoef];
+    for (int k = 0; k < D; ++k) {
+        xs[k] = cosl(pi * (k + 0.5L) / D);
+        long double pw = 1.0L;
+        for (int m = 0; m < D; ++m) {
+            W[k][m] = pw;
+            W[k][D + m] = (k == m) ? 1.0L : 0.0L;
+            pw *= xs[k];
+        }
+    }
+    for (int c = 0; c < D; ++c) {
+        int best = c;
+        for (int r = c + 1; r < D; ++r)
+            if (fabsl(W[r][c]) > fabsl(W[best][c])) best = r;
+        for (int m = 0; m < 2 * D; ++m) {
+            const long double tmp = W[c][m];
+            W[c][m] = W[best][m];
+            W[best][m] = tmp;
+        }
+        const long double piv = W[c][c];
+        for (int m = 0; m < 2 * D; ++m) W[c][m] /= piv;
+        for (int r = 0; r < D; ++r) {
+            if (r == c) continue;
+            const long double f = W[r][c];
+            for (int m = 0; m < 2 * D; ++m) W[r][m] -= f * W[c][m];
+        }
+    }
+    // W[.][D..2D) is now the inverse: coefficient m = sum_k inv[m][k] value(x_k)
+    const long double al = alpha, tspa = 2.0L * al / sqrtl(pi);
+    const int S = 1 << kFGSubLog2;
+    std::vector<double> out((size_t)npieces * D * 2);
+    for (int p = 0; p < npieces; ++p) {
+        const int e = kFGOctLo + p / S, j = p % S;
+        long double F[kFGCoef], G[kFGCoef];
+        for (int k = 0; k < D; ++k) {
+            const long double sk = ldexpl(1.0L + (j + (xs[k] + 1.0L) * 0.5L) / S, e);
+            const long double r = sqrtl(sk);
+            F[k] = erfcl(al * r) / r;
+            G[k] = -(F[k] + tspa * expl(-al * al * sk)) / sk;
+        }
+        for (int m = 0; m < D; ++m) {
+            long double cf = 0.0L, cg = 0.0L;
+            for (int k = 0; k < D; ++k) {
+                cf += W[m][D + k] * F[k];
+                cg += W[m][D + k] * G[k];
+            }
+            out[((size_t)p * D + m) * 2] = (double)cf;
+            out[((size_t)p * D + m) * 2 + 1] = (double)cg;
+        }
+    }
+    return out;
+}
+
+// Pieces of the pair-function table for cutoff^2 rc2: the octaves from
+// 2^kFGOctLo up to the one holding the largest s below rc2, at most kFGMaxOct.
+int fg_pieces_for(double rc2) {
+    if (!(rc2 > 0.0)) return 0;
+    int E = 0;
+    const double m = std::frexp(rc2, &E);  // rc2 = m 2^E, m in [0.5, 1)
+    const int emax = (m == 0.5) ? E - 2 : E - 1;  // exponent of the largest s < rc2
+    const int oct = std::max(0, std::min(kFGMaxOct, emax - kFGOctLo + 1));
+    return oct << kFGSubLog2;
+}
+
+// Leading pieces of the table whose F and G, evaluated by the kernel's Horner
+// scheme in double at 33 points of each piece, stay within 1e-13 relative of
+// the long-double functions; the rest of the s range takes the direct path.
+int fg_valid_pieces(const std::vector<double> &tab, double alpha, int npieces) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const long double al = alpha, tspa = 2.0L * al / sqrtl(pi);
+    const int S = 1 << kFGSubLog2;
+    for (int p = 0; p < npieces; ++p) {
+        const int e = kFGOctLo + p / S, j = p % S;
+        const double *c = tab.data() + (size_t)p * kFGCoef * 2;
+        for (int t = 0; t <= 32; ++t) {
+            const double x = -1.0 + t / 16.0 - (t == 32 ? 0x1p-40 : 0.0);
+            double f = c[2 * (kFGCoef - 1)], g = c[2 * (kFGCoef - 1) + 1];
+            for (int m = kFGCoef - 2; m >= 0; --m) {
+                f = std::fma(f, x, c[2 * m]);
+                g = std::fma(g, x, c[2 * m + 1]);
+            }
+            const long double sk = ldexpl(1.0L + (j + ((long double)x + 1.0L) * 0.5L) / S, e);
+            const long double r = sqrtl(sk);
+            const long double F = erfcl(al * r) / r;
+            const long double G = -(F + tspa * expl(-al * al * sk)) / sk;
+            if (fabsl((long double)f - F) > 1e-13L * fabsl(F) ||
+                fabsl((long double)g - G) > 1e-13L * fabsl(G))
+                return p;
+        }
+    }
+    return npieces;
+}
+
 // M_P(P / 2), the peak of the cardinal B-spline of order P, by the same order
 // recursion as bspline_mod2 (evaluated at the midpoint).
 double bspline_peak(int P) {
@@ -1206,6 +1377,7 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.Lx_f = (float)ra.Lx;
     ra.Ly_f = (float)ra.Ly;
     ra.Lz_f = (float)ra.Lz;
+    ra.fg_pieces = ctx->fg_pieces;
     // The mesh chain goes first, on the context's high-priority side stream
     // (forked here, joined before the combining gather), so that its short,
     // latency-bound kernels fill the issue slots the real-space kernel leaves;
@@ -1235,13 +1407,13 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
             auto *x4 = (const double4_32a *)xq;
             auto *s1 = (const double *)sg;
             if (need_field && !L.gtile)
-                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (need_field)
-                k_real64<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (!L.gtile)
-                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else
-                k_real64<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
         } else {
             auto *x4 = (const float4 *)xq;
             auto *s1 = (const float *)sg;
@@ -1420,6 +1592,40 @@ int coulomb_alloc(qeq_ctx *ctx) {
         if (rc) return rc;
     }
 
+    // pair-function table of the FP64 real-space kernel (per alpha and cutoff;
+    // the host copies live until exit in a process-wide cache, so the upload
+    // needs no synchronisation)
+    if (!ctx->fp32) {
+        struct FGEntry {
+            std::vector<double> tab;
+            int valid;
+        };
+        static std::mutex mu;
+        static std::map<std::pair<double, int>, FGEntry> cache;
+        const int np = fg_pieces_for(p.r_cut * p.r_cut);
+        const std::vector<double> *tab = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            auto key = std::make_pair(p.alpha, np);
+            auto it = cache.find(key);
+            if (it == cache.end()) {
+                FGEntry en{fg_table(p.alpha, np), 0};
+                en.valid = fg_valid_pieces(en.tab, p.alpha, np);
+                it = cache.emplace(key, std::move(en)).first;
+            }
+            tab = &it->second.tab;
+            ctx->fg_pieces = it->second.valid;
+        }
+        if (ctx->fg_pieces > 0) {
+            rc = dev_alloc(ctx, (void **)&ctx->fg_tab64, sizeof(double) * tab->size());
+            if (rc) return rc;
+            e = cudaMemcpyAsync(ctx->fg_tab64, tab->data(), sizeof(double) * tab->size(),
+                                cudaMemcpyHostToDevice, ctx->alloc_stream);
+            rc = cuda_check(ctx, e, "pair-function table upload");
+            if (rc) return rc;
+        }
+    }
+
     // cuFFT plans (from the plan pool) with a work area from this library's
     // allocator (no allocation inside cuFFT)
     size_t ws1 = 0, ws2 = 0;
@@ -1519,7 +1725,7 @@ void coulomb_free(qeq_ctx *ctx) {
     }
     void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
                     ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
-                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->tile_scratch,
+                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->fg_tab64, ctx->tile_scratch,
                     ctx->ticket};
     for (void *p : ptrs) dev_free(ctx, p);
     if (ctx->pme_fork) cudaEventDestroy(ctx->pme_fork);

@@ -317,6 +317,8 @@ struct qeq_ctx {
     cudaStream_t pme_stream = nullptr;
     cudaEvent_t pme_fork = nullptr, pme_join = nullptr;
     double *erfc_tab64 = nullptr;  // piecewise erfc coefficients of the FP64 real-space kernel
+    double *fg_tab64 = nullptr;    // piecewise pair functions F(r^2), G(r^2) of the FP64 kernel
+    int fg_pieces = 0;
 
     // ---- explicit k-vector Ewald (ewald.cu) ----
     void *ewald_k = nullptr;        // [nk] double4 (kx, ky, kz, g)

@@ -72,6 +72,25 @@ def test_fp64_point_charges_no_gaussian_self():
     _check64(g, _oracle(w, q, 0.4, 6.0, (24, 24, 24), 4, gaussian_self=False))
 
 
+@pytest.mark.parametrize("alpha,r_cut", [(0.45, 9.5), (0.8, 6.0)])
+def test_fp64_pair_table_ranges(alpha, r_cut):
+    """Uniform random atoms: pairs closer than 0.5 A and pairs beyond r = 8 A go
+    past the ends of the FP64 kernel's piecewise pair-function table (direct
+    erfc path), the rest cross its octave and piece boundaries; sigma mixes 0,
+    small and large widths so that the Gaussian-correction test sees both sides."""
+    import types
+    rng = np.random.default_rng(int(alpha * 100))
+    n, L = 360, 19.0
+    sigma = rng.choice([0.0, 0.3, 0.7, 1.6], size=n)
+    w = types.SimpleNamespace(n_atoms=n, box=np.array([L, L, L]), R=rng.uniform(0.0, L, (n, 3)),
+                              sigma=sigma)
+    q = random_neutral_charges(n, seed=7, scale=0.5)
+    mesh = (24, 24, 24)
+    # gaussian_self off: the Gaussian self energy is undefined at sigma = 0
+    _check64(_gpu_apply(w, q, alpha, r_cut, mesh, 4, gaussian_self=False),
+             _oracle(w, q, alpha, r_cut, mesh, 4, gaussian_self=False))
+
+
 def test_fp64_non_neutral_and_single_atom():
     w = water_box(1, seed=2)  # 3 atoms in a 4.5 A box: everything is multi-image
     w.box[:] = 5.0
