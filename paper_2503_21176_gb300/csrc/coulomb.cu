@@ -47,7 +47,7 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
                             const double *__restrict__ sigma, double sK0, double sK1, double sK2,
                             typename V4<T>::type *__restrict__ xq, T *__restrict__ sg,
                             int4 *__restrict__ sbase, typename V4<T>::type *__restrict__ sfrac,
-                            int32_t *__restrict__ smax_bits) {
+                            int32_t *__restrict__ smax_bits, float4 *__restrict__ xf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (smax_bits) {
         // max |sigma| as float bits (non-negative floats order like their bits)
@@ -62,6 +62,7 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
     const double z = R[3 * (size_t)a + 2] + w[3 * (size_t)a + 2];
     const double qa = q[a];
     xq[i] = {(T)x, (T)y, (T)z, (T)qa};
+    if (xf) xf[i] = make_float4((float)x, (float)y, (float)z, 0.0f);
     sg[i] = (T)sigma[a];
     // scaled fractional coordinates u = K x / L, split into floor and fraction in FP64
     const double ux = x * sK0, uy = y * sK1, uz = z * sK2;
@@ -97,7 +98,9 @@ struct RealArgs {
     // conversion in the kernel runs on the FP64 pipe (1/64 rate on GB300), and
     // under register pressure the compiler re-derives such values inside the loop.
     float alpha_f, rc2_f, tspa_f, c1_f, pal_f, Lx_f, Ly_f, Lz_f;
-    int fg_pieces;  // pieces of the FP64 pair-function table (0: direct erfc path only)
+    int fg_pieces;  // kept pieces of the FP64 pair-function tables (0: direct erfc path only)
+    int gc_pieces;
+    float pre_rc2_f;  // FP32 prefilter bound of the FP64 kernel (r_c^2 plus the FP32 error)
 };
 
 // FP64 erfc by a piecewise polynomial: [0, kErfcXMax) is cut into kErfcPieces
@@ -131,28 +134,59 @@ __device__ __forceinline__ double erfc_pw(const double *__restrict__ tab, double
     return p;
 }
 
-// FP64 pair functions of s = r^2 by piecewise polynomials:
-//   F(s) = erfc(alpha sqrt s) / sqrt s,
-//   G(s) = F'(r) / r = -(F(s) + (2 alpha / sqrt pi) exp(-alpha^2 s)) / s,
-// so that a pair adds q_j F to the potential and q_j G (r_j - r_i) to the field
-// without a square root or an erfc evaluation.  Octave e (2^e <= s < 2^(e+1))
-// of the s range [2^kFGOctLo, 2^(kFGOctLo + kFGMaxOct)) is cut into
-// 2^kFGSubLog2 equal pieces; on each piece F and G are the degree-(kFGCoef - 1)
-// polynomials in x in [-1, 1) through the Chebyshev nodes of the piece, from the
-// host's long-double erfc and exp (fg_table()).  The piece and x come from the
-// bits of s alone: the exponent and the top kFGSubLog2 mantissa bits are the
-// piece, the remaining mantissa bits the position in it (x = 2 y - 3 for the
-// double y in [1, 2) that holds them), so only the two Horner passes run on the
-// FP64 pipe.  A piece ends at least 32 half-widths from the singularity at
-// s = 0; the Gaussian factor exp(-alpha^2 s) bounds the error at large s, so
-// the host measures every piece and keeps the table only up to the first one
-// worse than 1e-13 relative (fg_valid_pieces()).  Pairs outside the table
-// (r < 0.5 A, or beyond the kept pieces) take the direct erfc path.
-constexpr int kFGOctLo = -2;
-constexpr int kFGSubLog2 = 4;
-constexpr int kFGCoef = 9;
-constexpr int kFGMaxOct = 8;
-constexpr int kFGMaxPieces = kFGMaxOct << kFGSubLog2;
+// FP64 pair functions by piecewise polynomials.  With
+//   F_a(s) = erfc(a sqrt s) / sqrt s,
+//   G_a(s) = F_a'(r) / r = 2 dF_a/ds = -(F_a(s) + (2 a / sqrt pi) exp(-a^2 s)) / s,
+// a pair at s = r^2 adds q_j F_alpha(s) to the potential and q_j G_alpha(s)
+// (r_j - r_i) to the field, and the Gaussian correction erfc(r / gamma) / r is
+// F_1(t) / gamma with t = s / gamma^2, its field coefficient G_1(t) / gamma^3.
+// Each table covers octaves [2^oct_lo, 2^(oct_lo + octaves)) of its argument,
+// octave e (2^e <= s < 2^(e+1)) cut into 2^sub_log2 equal pieces; on each piece
+// the two functions are the degree-(ncoef - 1) polynomials in x in [-1, 1)
+// through the Chebyshev nodes of the piece, from the host's long-double erfc
+// and exp (pw_table()).  The piece and x come from the bits of the argument
+// alone: the exponent and the top sub_log2 mantissa bits are the piece, the
+// remaining mantissa bits the position in it (x = 2 y - 3 for the double y in
+// [1, 2) that holds them), so only the two Horner passes run on the FP64 pipe.
+// A piece ends at least 2^(sub_log2 + 1) half-widths from the singularity at 0;
+// the Gaussian factor bounds the error at large arguments, so the host measures
+// every piece and keeps a table only up to the first one worse than 1e-13
+// relative (or 1e-15 of the bare Coulomb term 1 / r, where the function is
+// below 1e-2 of it) (pw_valid_pieces()).  Arguments outside the kept pieces
+// (r < 0.5 A; t < 1/32) take the direct erfc path.
+struct PwShape {
+    int oct_lo, sub_log2, ncoef, max_oct;
+};
+constexpr PwShape kFGShape{-2, 5, 8, 8};   // F_alpha, G_alpha of s in [1/4, 64)
+constexpr PwShape kGCShape{-5, 4, 9, 11};  // F_1, G_1 of t in [1/32, 64)
+constexpr int kFGMaxPieces = kFGShape.max_oct << kFGShape.sub_log2;
+constexpr int kGCMaxPieces = kGCShape.max_oct << kGCShape.sub_log2;
+// both tables, at the head of the FP64 kernel's dynamic shared memory
+constexpr size_t kFGTableBytes = sizeof(double2) * kFGMaxPieces * kFGShape.ncoef;
+constexpr size_t kPwTableBytes = kFGTableBytes + sizeof(double2) * kGCMaxPieces * kGCShape.ncoef;
+
+// Evaluate both functions of a table at arg > 0 (false: outside the npieces kept).
+template <int OCT_LO, int SUB, int NC>
+__device__ __forceinline__ bool pw_eval(const double2 *tab, unsigned npieces, double arg, double &f,
+                                        double &g) {
+    const int hi = __double2hiint(arg);
+    const unsigned piece = (unsigned)((hi >> (20 - SUB)) - ((1023 + OCT_LO) << SUB));
+    if (piece >= npieces) return false;
+    const unsigned lo = (unsigned)__double2loint(arg);
+    const int hy = 0x3FF00000 | ((hi << SUB) & 0x000FFFFF) | (int)(lo >> (32 - SUB));
+    const double x = fma(__hiloint2double(hy, (int)(lo << SUB)), 2.0, -3.0);
+    const double2 *c = tab + piece * NC;
+    double2 cm = c[NC - 1];
+    f = cm.x;
+    g = cm.y;
+#pragma unroll
+    for (int m = NC - 2; m >= 0; --m) {
+        cm = c[m];
+        f = fma(f, x, cm.x);
+        g = fma(g, x, cm.y);
+    }
+    return true;
+}
 
 // Lanes per neighbour row.  kTPR consecutive lanes share one row: lane s takes
 // the row's entries s, s + kTPR, ..., which the list stores next to each other
@@ -176,10 +210,12 @@ constexpr bool kRealLazySigma = QEQ_REAL_LAZY_SIGMA != 0;
 
 // Tile bytes per atom (position and charge, sigma) and the dynamic shared
 // memory the kernels may take: 227 KB per block less their static tables.
-constexpr size_t kTile32Bytes = 20, kTile64Bytes = 40;
+// (FP64: double4 position and q, double sigma, and the float4 position copy of
+// the FP32 cutoff prefilter.)
+constexpr size_t kTile32Bytes = 20, kTile64Bytes = 56;
 constexpr size_t kSmemPerBlock = 232448;
 constexpr size_t kReal32SmemMax = kSmemPerBlock - 4096;
-constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096 - sizeof(double2) * kFGMaxPieces * kFGCoef;
+constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096;  // tables included
 
 // Brick spreading: block size and the largest shared-memory window it takes.
 constexpr int kSpreadThreads = 128;
@@ -272,24 +308,46 @@ __global__ void __launch_bounds__(kRealMaxThreads, 2)
 k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32_t *__restrict__ tile_tot,
          const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const double4_32a *__restrict__ xq, const double *__restrict__ sg,
-         const double *__restrict__ erfc_tab, const double2 *__restrict__ fg_tab, int cap,
+         const float4 *__restrict__ xf, const double *__restrict__ erfc_tab,
+         const double2 *__restrict__ fg_tab, const double2 *__restrict__ gc_tab, int cap,
          unsigned char *__restrict__ gtile, int32_t *__restrict__ flags, double *__restrict__ v_s,
          double *__restrict__ E_s) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
-    __shared__ double2 fg[kFGMaxPieces * kFGCoef];
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
-    unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile64Bytes : smem_raw;
+    double2 *fg = (double2 *)smem_raw;
+    double2 *gct = (double2 *)(smem_raw + kFGTableBytes);
+    unsigned char *base =
+        GTILE ? gtile + (size_t)blockIdx.x * cap * kTile64Bytes : smem_raw + kPwTableBytes;
     double4_32a *tile = (double4_32a *)base;
     double *tsg = (double *)(base + (size_t)cap * 32);
-    for (int t = threadIdx.x; t < a.fg_pieces * kFGCoef; t += blockDim.x) fg[t] = fg_tab[t];
+    for (int t = threadIdx.x; t < a.fg_pieces * kFGShape.ncoef; t += blockDim.x) fg[t] = fg_tab[t];
+    for (int t = threadIdx.x; t < a.gc_pieces * kGCShape.ncoef; t += blockDim.x) gct[t] = gc_tab[t];
     const int total = stage_tile<double4_32a, double>(g, tile_tab, tile_tot, xq, sg, a.Lx, a.Ly, a.Lz, cap,
                                                      tile, tsg, t_start, t_base, t_code, &t_total,
                                                      flags);
     if (total < 0) return;
+    // float copy of the tile positions for the FP32 cutoff prefilter
+    float4 *tf = (float4 *)(base + (size_t)cap * 40);
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int rb = warp; rb < g.T; rb += nw) {
+            const int st = t_start[rb], off = st + t_base[rb];
+            const int end = rb + 1 < g.T ? t_start[rb + 1] + t_base[rb + 1] : total;
+            const int code = t_code[rb];
+            const float sx = (float)(code / 25 - 2) * a.Lx_f, sy = (float)((code / 5) % 5 - 2) * a.Ly_f,
+                        sz = (float)(code % 5 - 2) * a.Lz_f;
+            for (int k = lane; k < end - off; k += 32) {
+                const float4 x = xf[st + k];
+                tf[off + k] = make_float4(x.x + sx, x.y + sy, x.z + sz, 0.0f);
+            }
+        }
+        if (threadIdx.x == 0) tf[total] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+        __syncthreads();
+    }
     int i0, offc, nrows;
     home_rows(g, t_start, t_base, total, i0, offc, nrows);
     const double al = a.alpha;
-    const unsigned npieces = (unsigned)a.fg_pieces;
+    const unsigned npieces = (unsigned)a.fg_pieces, gpieces = (unsigned)a.gc_pieces;
     const long long rc2_bits = __double_as_longlong(a.rc2);
     const int rpp = blockDim.x / kTPR;
     for (int r0 = 0; r0 < nrows; r0 += rpp) {
@@ -301,9 +359,15 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
             const double4_32a xi = tile[offc + r];
             const double si2 = tsg[offc + r] * tsg[offc + r];
             const float si2f = hi_to_float(__double2hiint(si2));
+            const float4 xif = tf[offc + r];
             const int c = cnt[i];
             for (int k = sub; k < c; k += kTPR) {
                 const int e = nbr[list_index(k, i, a.n)];
+                // FP32 prefilter: pre_rc2_f exceeds r_c^2 by more than the FP32
+                // error of r^2, so only pairs that fail the FP64 test are dropped
+                const float4 xjf = tf[e];
+                const float fx = xjf.x - xif.x, fy = xjf.y - xif.y, fz = xjf.z - xif.z;
+                if (!(fmaf(fx, fx, fmaf(fy, fy, fz * fz)) < a.pre_rc2_f)) continue;
                 const double4_32a xj = tile[e];
                 const double dx = xj.x - xi.x;
                 const double dy = xj.y - xi.y;
@@ -313,25 +377,7 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                 if (!(__double_as_longlong(r2) < rc2_bits)) continue;
                 // f = erfc(alpha r) / r, gc = (d/dr f) / r
                 double f, gc;
-                const int hi = __double2hiint(r2);
-                const unsigned piece =
-                    (unsigned)((hi >> (20 - kFGSubLog2)) - ((1023 + kFGOctLo) << kFGSubLog2));
-                if (piece < npieces) {
-                    const unsigned lo = (unsigned)__double2loint(r2);
-                    const int hy = 0x3FF00000 | ((hi << kFGSubLog2) & 0x000FFFFF) |
-                                   (int)(lo >> (32 - kFGSubLog2));
-                    const double x = fma(__hiloint2double(hy, (int)(lo << kFGSubLog2)), 2.0, -3.0);
-                    const double2 *cf = fg + piece * kFGCoef;
-                    double2 cm = cf[kFGCoef - 1];
-                    f = cm.x;
-                    gc = cm.y;
-#pragma unroll
-                    for (int m = kFGCoef - 2; m >= 0; --m) {
-                        cm = cf[m];
-                        f = fma(f, x, cm.x);
-                        gc = fma(gc, x, cm.y);
-                    }
-                } else {
+                if (!pw_eval<kFGShape.oct_lo, kFGShape.sub_log2, kFGShape.ncoef>(fg, npieces, r2, f, gc)) {
                     const double ir = rsqrt(r2);
                     double d1;
                     f = erfc_pw(erfc_tab, al * (r2 * ir), d1) * ir;
@@ -340,17 +386,27 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                 // Gaussian correction; the erfc table is exactly 0 beyond r / gamma =
                 // kErfcXMax.  The test runs in FP32 on values truncated from the
                 // high words of r^2 and sigma_j (each at most 2^-20 low) with a
-                // 1e-5 margin, so it never drops a pair the FP64 test would keep,
-                // and a pair it keeps beyond the bound adds exactly 0.
+                // 1e-5 margin, so it never drops a pair the FP64 test would keep; a
+                // pair it keeps beyond the bound adds below erfc(6.5) ~ 4e-20 of 1 / r.
+                const int hi = __double2hiint(r2);
                 const float sjf = hi_to_float(((const int *)tsg)[2 * e + 1]);
                 if (hi_to_float(hi) < kGaussTest * fmaf(sjf, sjf, si2f)) {
-                    const double g2 = si2 + tsg[e] * tsg[e];
-                    const double ir = rsqrt(r2);
+                    const double sj = tsg[e];
+                    const double g2 = si2 + sj * sj;
                     const double ig = rsqrt(g2);
-                    double d2;
-                    const double fg2 = erfc_pw(erfc_tab, (r2 * ir) * ig, d2) * ir;
-                    f -= fg2;
-                    gc -= (ig * d2 - fg2) * ir * ir;
+                    const double ig2 = ig * ig;
+                    double fc, gcc;
+                    if (pw_eval<kGCShape.oct_lo, kGCShape.sub_log2, kGCShape.ncoef>(gct, gpieces, r2 * ig2,
+                                                                                    fc, gcc)) {
+                        f -= ig * fc;
+                        gc -= ig2 * ig * gcc;
+                    } else {
+                        const double ir = rsqrt(r2);
+                        double d2;
+                        const double fg2 = erfc_pw(erfc_tab, (r2 * ir) * ig, d2) * ir;
+                        f -= fg2;
+                        gc -= (ig * d2 - fg2) * ir * ir;
+                    }
                 }
                 v += xj.w * f;
                 if (FIELD) {
@@ -1060,18 +1116,32 @@ std::vector<double> erfc_table() {
     return out;
 }
 
-// Pair-function table of the FP64 real-space kernel for a given alpha: npieces
-// pieces of kFGCoef (F, G) coefficient pairs, piece p covering octave
-// e = kFGOctLo + p / 2^kFGSubLog2, sub-piece j = p mod 2^kFGSubLog2, i.e.
-// s = 2^e (1 + (j + (x + 1) / 2) / 2^kFGSubLog2) for x in [-1, 1).  The
+// Piecewise table of F_a and G_a (shape sh, npieces pieces of sh.ncoef
+// coefficient pairs, interleaved F, G): piece p covers octave
+// e = sh.oct_lo + p / 2^sh.sub_log2, sub-piece j = p mod 2^sh.sub_log2, i.e.
+// s = 2^e (1 + (j + (x + 1) / 2) / 2^sh.sub_log2) for x in [-1, 1).  The
 // interpolation nodes are the same Chebyshev nodes in x for every piece, so the
 // Vandermonde matrix in x is inverted once (Gauss-Jordan with partial pivoting
 // in long double) and applied to the long-double F and G at the nodes of each
 // piece.
-std::vector<double> fg_table(double alpha, int npieces) {
-    const int D = kFGCoef;
+constexpr int kPwMaxCoef = 16;
+
+void pw_functions(long double a, long double s, long double &F, long double &G) {
     const long double pi = 3.141592653589793238462643383279502884L;
-    long double xs[kFGCoef], W[kFGCoef][2 * kFGCoef];
+    const long double r = sqrtl(s);
+    F = erfcl(a * r) / r;
+    G = -(F + 2.0L * a / sqrtl(pi) * expl(-a * a * s)) / s;
+}
+
+long double pw_arg(const PwShape &sh, int p, long double x) {
+    const int S = 1 << sh.sub_log2;
+    return ldexpl(1.0L + (p % S + (x + 1.0L) * 0.5L) / S, sh.oct_lo + p / S);
+}
+
+std::vector<double> pw_table(double alpha, const PwShape &sh, int npieces) {
+    const int D = sh.ncoef;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    long double xs[kPwMaxCoef], W[kPwMaxCoef][2 * kPwMaxCoef];
     for (int k = 0; k < D; ++k) {
         xs[k] = cosl(pi * (k + 0.5L) / D);
         long double pw = 1.0L;
@@ -1099,18 +1169,10 @@ std::vector<double> fg_table(double alpha, int npieces) {
         }
     }
     // W[.][D..2D) is now the inverse: coefficient m = sum_k inv[m][k] value(x_k)
-    const long double al = alpha, tspa = 2.0L * al / sqrtl(pi);
-    const int S = 1 << kFGSubLog2;
     std::vector<double> out((size_t)npieces * D * 2);
     for (int p = 0; p < npieces; ++p) {
-        const int e = kFGOctLo + p / S, j = p % S;
-        long double F[kFGCoef], G[kFGCoef];
-        for (int k = 0; k < D; ++k) {
-            const long double sk = ldexpl(1.0L + (j + (xs[k] + 1.0L) * 0.5L) / S, e);
-            const long double r = sqrtl(sk);
-            F[k] = erfcl(al * r) / r;
-            G[k] = -(F[k] + tspa * expl(-al * al * sk)) / sk;
-        }
+        long double F[kPwMaxCoef], G[kPwMaxCoef];
+        for (int k = 0; k < D; ++k) pw_functions(alpha, pw_arg(sh, p, xs[k]), F[k], G[k]);
         for (int m = 0; m < D; ++m) {
             long double cf = 0.0L, cg = 0.0L;
             for (int k = 0; k < D; ++k) {
@@ -1124,44 +1186,67 @@ std::vector<double> fg_table(double alpha, int npieces) {
     return out;
 }
 
-// Pieces of the pair-function table for cutoff^2 rc2: the octaves from
-// 2^kFGOctLo up to the one holding the largest s below rc2, at most kFGMaxOct.
-int fg_pieces_for(double rc2) {
-    if (!(rc2 > 0.0)) return 0;
+// Pieces of a table whose argument stays below smax: the octaves from
+// 2^sh.oct_lo up to the one holding the largest argument below smax, at most
+// sh.max_oct.
+int pw_pieces_for(const PwShape &sh, double smax) {
+    if (!(smax > 0.0)) return 0;
     int E = 0;
-    const double m = std::frexp(rc2, &E);  // rc2 = m 2^E, m in [0.5, 1)
-    const int emax = (m == 0.5) ? E - 2 : E - 1;  // exponent of the largest s < rc2
-    const int oct = std::max(0, std::min(kFGMaxOct, emax - kFGOctLo + 1));
-    return oct << kFGSubLog2;
+    const double m = std::frexp(smax, &E);  // smax = m 2^E, m in [0.5, 1)
+    const int emax = (m == 0.5) ? E - 2 : E - 1;  // exponent of the largest s < smax
+    const int oct = std::max(0, std::min(sh.max_oct, emax - sh.oct_lo + 1));
+    return oct << sh.sub_log2;
 }
 
-// Leading pieces of the table whose F and G, evaluated by the kernel's Horner
-// scheme in double at 33 points of each piece, stay within 1e-13 relative of
-// the long-double functions; the rest of the s range takes the direct path.
-int fg_valid_pieces(const std::vector<double> &tab, double alpha, int npieces) {
-    const long double pi = 3.141592653589793238462643383279502884L;
-    const long double al = alpha, tspa = 2.0L * al / sqrtl(pi);
-    const int S = 1 << kFGSubLog2;
+// Leading pieces of a table whose F and G, evaluated by the kernel's Horner
+// scheme in double at 33 points of each piece, stay within 1e-13 of the
+// long-double functions, relative to the larger of the function and 1e-2 of the
+// bare Coulomb term (1 / r for F, 1 / r^3 for G), i.e. within 1e-15 of the bare
+// term where the screened one is far below it; the rest takes the direct path.
+int pw_valid_pieces(const std::vector<double> &tab, double alpha, const PwShape &sh, int npieces) {
+    const int D = sh.ncoef;
     for (int p = 0; p < npieces; ++p) {
-        const int e = kFGOctLo + p / S, j = p % S;
-        const double *c = tab.data() + (size_t)p * kFGCoef * 2;
+        const double *c = tab.data() + (size_t)p * D * 2;
         for (int t = 0; t <= 32; ++t) {
             const double x = -1.0 + t / 16.0 - (t == 32 ? 0x1p-40 : 0.0);
-            double f = c[2 * (kFGCoef - 1)], g = c[2 * (kFGCoef - 1) + 1];
-            for (int m = kFGCoef - 2; m >= 0; --m) {
+            double f = c[2 * (D - 1)], g = c[2 * (D - 1) + 1];
+            for (int m = D - 2; m >= 0; --m) {
                 f = std::fma(f, x, c[2 * m]);
                 g = std::fma(g, x, c[2 * m + 1]);
             }
-            const long double sk = ldexpl(1.0L + (j + ((long double)x + 1.0L) * 0.5L) / S, e);
-            const long double r = sqrtl(sk);
-            const long double F = erfcl(al * r) / r;
-            const long double G = -(F + tspa * expl(-al * al * sk)) / sk;
-            if (fabsl((long double)f - F) > 1e-13L * fabsl(F) ||
-                fabsl((long double)g - G) > 1e-13L * fabsl(G))
+            const long double sk = pw_arg(sh, p, x);
+            long double F, G;
+            pw_functions(alpha, sk, F, G);
+            const long double bare = 1.0L / sqrtl(sk);
+            const long double fs = std::max(fabsl(F), 1e-2L * bare);
+            const long double gs = std::max(fabsl(G), 1e-2L * bare / sk);
+            if (fabsl((long double)f - F) > 1e-13L * fs || fabsl((long double)g - G) > 1e-13L * gs)
                 return p;
         }
     }
     return npieces;
+}
+
+// Process-wide cache of the tables (their host copies live until exit, so the
+// uploads need no synchronisation): the coefficients and the kept pieces per
+// alpha, shape and size.
+const std::vector<double> &pw_cached(double alpha, const PwShape &sh, int np, int *valid) {
+    struct Entry {
+        std::vector<double> tab;
+        int valid;
+    };
+    static std::mutex mu;
+    static std::map<std::tuple<double, int, int>, Entry> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(alpha, sh.oct_lo, np);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        Entry en{pw_table(alpha, sh, np), 0};
+        en.valid = pw_valid_pieces(en.tab, alpha, sh, np);
+        it = cache.emplace(key, std::move(en)).first;
+    }
+    *valid = it->second.valid;
+    return it->second.tab;
 }
 
 // M_P(P / 2), the peak of the cardinal B-spline of order P, by the same order
@@ -1284,8 +1369,9 @@ RealLaunch real_launch(const qeq_ctx *ctx, bool f64) {
     L.threads = real_block_threads(ctx->rows_cap);
     L.cap = ctx->tile_cap;
     const size_t bytes = (size_t)L.cap * (f64 ? kTile64Bytes : kTile32Bytes);
-    L.gtile = bytes > (f64 ? kReal64SmemMax : kReal32SmemMax);
-    L.smem = L.gtile ? 0 : bytes;
+    const size_t tables = f64 ? kPwTableBytes : 0;  // the FP64 pair-function tables
+    L.gtile = tables + bytes > (f64 ? kReal64SmemMax : kReal32SmemMax);
+    L.smem = tables + (L.gtile ? 0 : bytes);
     return L;
 }
 
@@ -1357,7 +1443,8 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
         if (smax_bits) cudaMemsetAsync(smax_bits, 0, sizeof(int32_t), s);
         k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
             n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
-            ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac, smax_bits);
+            ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac, smax_bits,
+            f64 ? ctx->xf_pre : nullptr);
         ctx->gathered = true;
     }
     prof_end(ctx, s);
@@ -1378,6 +1465,14 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.Ly_f = (float)ra.Ly;
     ra.Lz_f = (float)ra.Lz;
     ra.fg_pieces = ctx->fg_pieces;
+    ra.gc_pieces = ctx->gc_pieces;
+    {
+        // tile coordinates lie within 3 box lengths of 0, so each FP32 coordinate
+        // difference is off by at most 4.8e-7 L_max and r^2 by far less than
+        // 4e-6 r_list L_max + 1e-5 r_c^2
+        const double Lm = std::max(ra.Lx, std::max(ra.Ly, ra.Lz));
+        ra.pre_rc2_f = (float)(ra.rc2 * (1.0 + 1e-5) + 4e-6 * ctx->rl * Lm);
+    }
     // The mesh chain goes first, on the context's high-priority side stream
     // (forked here, joined before the combining gather), so that its short,
     // latency-bound kernels fill the issue slots the real-space kernel leaves;
@@ -1407,13 +1502,13 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
             auto *x4 = (const double4_32a *)xq;
             auto *s1 = (const double *)sg;
             if (need_field && !L.gtile)
-                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (need_field)
-                k_real64<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, true><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else if (!L.gtile)
-                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
             else
-                k_real64<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, true><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
         } else {
             auto *x4 = (const float4 *)xq;
             auto *s1 = (const float *)sg;
@@ -1489,6 +1584,7 @@ int coulomb_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->sfrac, 4 * rs * n},
         {ctx->fp32 ? (void **)&ctx->xq32 : (void **)&ctx->xq64, 4 * rs * n},
         {ctx->fp32 ? (void **)&ctx->sg32 : (void **)&ctx->sg64, rs * n},
+        {(void **)&ctx->xf_pre, ctx->fp32 ? 0 : sizeof(float4) * n},
         {&ctx->mesh, rs * ctx->mesh_n},
         {&ctx->meshc, 2 * rs * ctx->meshc_n},
         {&ctx->G, rs * ctx->meshc_n},
@@ -1574,6 +1670,12 @@ int coulomb_alloc(qeq_ctx *ctx) {
         if (ea == cudaSuccess)
             ea = cudaFuncSetAttribute(k_real64<false, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal64SmemMax);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_real64<true, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPwTableBytes);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(k_real64<false, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPwTableBytes);
         const int rca = cuda_check(ctx, ea, "real-space shared memory attribute");
         if (rca) return rca;
     }
@@ -1592,35 +1694,28 @@ int coulomb_alloc(qeq_ctx *ctx) {
         if (rc) return rc;
     }
 
-    // pair-function table of the FP64 real-space kernel (per alpha and cutoff;
-    // the host copies live until exit in a process-wide cache, so the upload
-    // needs no synchronisation)
+    // pair-function tables of the FP64 real-space kernel: F_alpha, G_alpha of
+    // r^2 < r_c^2, and F_1, G_1 of r^2 / gamma^2 below the Gaussian-correction bound
     if (!ctx->fp32) {
-        struct FGEntry {
-            std::vector<double> tab;
-            int valid;
+        struct {
+            const PwShape *sh;
+            double alpha, smax;
+            double **dev;
+            int *pieces;
+        } tabs[2] = {
+            {&kFGShape, p.alpha, p.r_cut * p.r_cut, &ctx->fg_tab64, &ctx->fg_pieces},
+            {&kGCShape, 1.0, kErfcXMax * kErfcXMax * (1.0 + 2e-5), &ctx->gc_tab64, &ctx->gc_pieces},
         };
-        static std::mutex mu;
-        static std::map<std::pair<double, int>, FGEntry> cache;
-        const int np = fg_pieces_for(p.r_cut * p.r_cut);
-        const std::vector<double> *tab = nullptr;
-        {
-            std::lock_guard<std::mutex> lock(mu);
-            auto key = std::make_pair(p.alpha, np);
-            auto it = cache.find(key);
-            if (it == cache.end()) {
-                FGEntry en{fg_table(p.alpha, np), 0};
-                en.valid = fg_valid_pieces(en.tab, p.alpha, np);
-                it = cache.emplace(key, std::move(en)).first;
-            }
-            tab = &it->second.tab;
-            ctx->fg_pieces = it->second.valid;
-        }
-        if (ctx->fg_pieces > 0) {
-            rc = dev_alloc(ctx, (void **)&ctx->fg_tab64, sizeof(double) * tab->size());
+        for (auto &t : tabs) {
+            const int np = pw_pieces_for(*t.sh, t.smax);
+            int valid = 0;
+            const std::vector<double> &tab = pw_cached(t.alpha, *t.sh, np, &valid);
+            *t.pieces = valid;
+            if (valid == 0) continue;
+            rc = dev_alloc(ctx, (void **)t.dev, sizeof(double) * tab.size());
             if (rc) return rc;
-            e = cudaMemcpyAsync(ctx->fg_tab64, tab->data(), sizeof(double) * tab->size(),
-                                cudaMemcpyHostToDevice, ctx->alloc_stream);
+            e = cudaMemcpyAsync(*t.dev, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice,
+                                ctx->alloc_stream);
             rc = cuda_check(ctx, e, "pair-function table upload");
             if (rc) return rc;
         }
@@ -1725,7 +1820,7 @@ void coulomb_free(qeq_ctx *ctx) {
     }
     void *ptrs[] = {ctx->v_s,  ctx->E_s,  ctx->sbase, ctx->sfrac, ctx->xq32, ctx->xq64,
                     ctx->sg32, ctx->sg64, ctx->mesh,  ctx->meshc, ctx->G,    ctx->part,
-                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->fg_tab64, ctx->tile_scratch,
+                    ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->fg_tab64, ctx->gc_tab64, ctx->xf_pre, ctx->tile_scratch,
                     ctx->ticket};
     for (void *p : ptrs) dev_free(ctx, p);
     if (ctx->pme_fork) cudaEventDestroy(ctx->pme_fork);

@@ -319,6 +319,9 @@ struct qeq_ctx {
     double *erfc_tab64 = nullptr;  // piecewise erfc coefficients of the FP64 real-space kernel
     double *fg_tab64 = nullptr;    // piecewise pair functions F(r^2), G(r^2) of the FP64 kernel
     int fg_pieces = 0;
+    double *gc_tab64 = nullptr;    // piecewise F_1(t), G_1(t) of the Gaussian correction (FP64)
+    int gc_pieces = 0;
+    float4 *xf_pre = nullptr;      // [N] FP32 positions (sorted) of the FP64 kernel's prefilter
 
     // ---- explicit k-vector Ewald (ewald.cu) ----
     void *ewald_k = nullptr;        // [nk] double4 (kx, ky, kz, g)
