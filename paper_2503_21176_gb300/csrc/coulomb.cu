@@ -216,6 +216,8 @@ constexpr size_t kTile32Bytes = 20, kTile64Bytes = 56;
 constexpr size_t kSmemPerBlock = 232448;
 constexpr size_t kReal32SmemMax = kSmemPerBlock - 4096;
 constexpr size_t kReal64SmemMax = kSmemPerBlock - 4096;  // tables included
+// Largest deferred Gaussian-correction queue of the FP64 kernel (entries per lane).
+constexpr int kCorrQueueMax = 48;
 
 // Brick spreading: block size and the largest shared-memory window it takes.
 constexpr int kSpreadThreads = 128;
@@ -295,6 +297,29 @@ __device__ __forceinline__ float hi_to_float(int hi) {
     const int b = hi - (896 << 20);  // rebias the exponent from 1023 to 127
     return b > 0 ? __int_as_float(b << 3) : 0.0f;
 }
+// Gaussian correction of an FP64 pair at r^2 = r2 with gamma^2 = si2 + sj^2: the
+// amounts fc = erfc(r / gamma) / r and gcc = (d/dr fc) / r that the pair's
+// potential and field coefficient lose.  F_1, G_1 of t = r^2 / gamma^2 from the
+// table, else the direct piecewise erfc (exactly 0 beyond r / gamma = kErfcXMax).
+__device__ __forceinline__ void gauss_corr64(double r2, double si2, double sj,
+                                             const double *__restrict__ erfc_tab,
+                                             const double2 *gct, unsigned gpieces, double &fc,
+                                             double &gcc) {
+    const double g2 = si2 + sj * sj;
+    const double ig = rsqrt(g2);
+    const double ig2 = ig * ig;
+    double f1, g1;
+    if (pw_eval<kGCShape.oct_lo, kGCShape.sub_log2, kGCShape.ncoef>(gct, gpieces, r2 * ig2, f1, g1)) {
+        fc = ig * f1;
+        gcc = ig2 * ig * g1;
+    } else {
+        const double ir = rsqrt(r2);
+        double d2;
+        fc = erfc_pw(erfc_tab, (r2 * ir) * ig, d2) * ir;
+        gcc = (ig * d2 - fc) * ir * ir;
+    }
+}
+
 // kErfcXMax^2 with the margin of the FP32 Gaussian-correction test.
 constexpr float kGaussTest = (float)(kErfcXMax * kErfcXMax * (1.0 + 1e-5));
 
@@ -309,7 +334,7 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
          const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const double4_32a *__restrict__ xq, const double *__restrict__ sg,
          const float4 *__restrict__ xf, const double *__restrict__ erfc_tab,
-         const double2 *__restrict__ fg_tab, const double2 *__restrict__ gc_tab, int cap,
+         const double2 *__restrict__ fg_tab, const double2 *__restrict__ gc_tab, int cap, int qcap,
          unsigned char *__restrict__ gtile, int32_t *__restrict__ flags, double *__restrict__ v_s,
          double *__restrict__ E_s) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -320,6 +345,8 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
         GTILE ? gtile + (size_t)blockIdx.x * cap * kTile64Bytes : smem_raw + kPwTableBytes;
     double4_32a *tile = (double4_32a *)base;
     double *tsg = (double *)(base + (size_t)cap * 32);
+    // per-lane queue of deferred Gaussian corrections (slot-major), after the tile
+    uint16_t *cq = (uint16_t *)(smem_raw + kPwTableBytes + (GTILE ? 0 : (size_t)cap * kTile64Bytes));
     for (int t = threadIdx.x; t < a.fg_pieces * kFGShape.ncoef; t += blockDim.x) fg[t] = fg_tab[t];
     for (int t = threadIdx.x; t < a.gc_pieces * kGCShape.ncoef; t += blockDim.x) gct[t] = gc_tab[t];
     const int total = stage_tile<double4_32a, double>(g, tile_tab, tile_tot, xq, sg, a.Lx, a.Ly, a.Lz, cap,
@@ -361,6 +388,7 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
             const float si2f = hi_to_float(__double2hiint(si2));
             const float4 xif = tf[offc + r];
             const int c = cnt[i];
+            int nq = 0;
             for (int k = sub; k < c; k += kTPR) {
                 const int e = nbr[list_index(k, i, a.n)];
                 // FP32 prefilter: pre_rc2_f exceeds r_c^2 by more than the FP32
@@ -383,29 +411,25 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                     f = erfc_pw(erfc_tab, al * (r2 * ir), d1) * ir;
                     gc = (al * d1 - f) * ir * ir;
                 }
-                // Gaussian correction; the erfc table is exactly 0 beyond r / gamma =
-                // kErfcXMax.  The test runs in FP32 on values truncated from the
-                // high words of r^2 and sigma_j (each at most 2^-20 low) with a
+                // Gaussian correction.  The test runs in FP32 on values truncated from
+                // the high words of r^2 and sigma_j (each at most 2^-20 low) with a
                 // 1e-5 margin, so it never drops a pair the FP64 test would keep; a
-                // pair it keeps beyond the bound adds below erfc(6.5) ~ 4e-20 of 1 / r.
+                // pair it keeps beyond r / gamma = kErfcXMax adds below
+                // erfc(6.5) ~ 4e-20 of 1 / r.  About a quarter of the pairs need it,
+                // scattered over the lanes, so the lane queues them (the tile slot)
+                // and runs them together after the list: the FP64 pipe then works
+                // on nearly full warps.
                 const int hi = __double2hiint(r2);
                 const float sjf = hi_to_float(((const int *)tsg)[2 * e + 1]);
                 if (hi_to_float(hi) < kGaussTest * fmaf(sjf, sjf, si2f)) {
-                    const double sj = tsg[e];
-                    const double g2 = si2 + sj * sj;
-                    const double ig = rsqrt(g2);
-                    const double ig2 = ig * ig;
-                    double fc, gcc;
-                    if (pw_eval<kGCShape.oct_lo, kGCShape.sub_log2, kGCShape.ncoef>(gct, gpieces, r2 * ig2,
-                                                                                    fc, gcc)) {
-                        f -= ig * fc;
-                        gc -= ig2 * ig * gcc;
+                    if (nq < qcap) {
+                        cq[nq * blockDim.x + threadIdx.x] = (uint16_t)e;
+                        ++nq;
                     } else {
-                        const double ir = rsqrt(r2);
-                        double d2;
-                        const double fg2 = erfc_pw(erfc_tab, (r2 * ir) * ig, d2) * ir;
-                        f -= fg2;
-                        gc -= (ig * d2 - fg2) * ir * ir;
+                        double fc, gcc;
+                        gauss_corr64(r2, si2, tsg[e], erfc_tab, gct, gpieces, fc, gcc);
+                        f -= fc;
+                        gc -= gcc;
                     }
                 }
                 v += xj.w * f;
@@ -414,6 +438,23 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                     ex += gq * dx;
                     ey += gq * dy;
                     ez += gq * dz;
+                }
+            }
+            for (int m = 0; m < nq; ++m) {
+                const int e = cq[m * blockDim.x + threadIdx.x];
+                const double4_32a xj = tile[e];
+                const double dx = xj.x - xi.x;
+                const double dy = xj.y - xi.y;
+                const double dz = xj.z - xi.z;
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                double fc, gcc;
+                gauss_corr64(r2, si2, tsg[e], erfc_tab, gct, gpieces, fc, gcc);
+                v -= xj.w * fc;
+                if (FIELD) {
+                    const double gq = xj.w * gcc;
+                    ex -= gq * dx;
+                    ey -= gq * dy;
+                    ez -= gq * dz;
                 }
             }
         }
@@ -1360,6 +1401,7 @@ void dispatch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const v
 struct RealLaunch {
     int threads;
     int cap;
+    int qcap;  // FP64: deferred-correction queue entries per lane
     size_t smem;
     bool gtile;
 };
@@ -1372,6 +1414,13 @@ RealLaunch real_launch(const qeq_ctx *ctx, bool f64) {
     const size_t tables = f64 ? kPwTableBytes : 0;  // the FP64 pair-function tables
     L.gtile = tables + bytes > (f64 ? kReal64SmemMax : kReal32SmemMax);
     L.smem = tables + (L.gtile ? 0 : bytes);
+    L.qcap = 0;
+    if (f64) {
+        // the correction queue takes what shared memory is left, up to kCorrQueueMax
+        const size_t left = kReal64SmemMax - L.smem;
+        L.qcap = (int)std::min<size_t>(kCorrQueueMax, left / (sizeof(uint16_t) * L.threads));
+        L.smem += (size_t)L.qcap * L.threads * sizeof(uint16_t);
+    }
     return L;
 }
 
@@ -1502,13 +1551,13 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
             auto *x4 = (const double4_32a *)xq;
             auto *s1 = (const double *)sg;
             if (need_field && !L.gtile)
-                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, L.qcap, gt, fl, ctx->v_s, ctx->E_s);
             else if (need_field)
-                k_real64<true, true><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<true, true><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, L.qcap, gt, fl, ctx->v_s, ctx->E_s);
             else if (!L.gtile)
-                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, L.qcap, gt, fl, ctx->v_s, ctx->E_s);
             else
-                k_real64<false, true><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real64<false, true><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, ctx->xf_pre, ctx->erfc_tab64, (const double2 *)ctx->fg_tab64, (const double2 *)ctx->gc_tab64, L.cap, L.qcap, gt, fl, ctx->v_s, ctx->E_s);
         } else {
             auto *x4 = (const float4 *)xq;
             auto *s1 = (const float *)sg;
@@ -1672,10 +1721,10 @@ int coulomb_alloc(qeq_ctx *ctx) {
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal64SmemMax);
         if (ea == cudaSuccess)
             ea = cudaFuncSetAttribute(k_real64<true, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPwTableBytes);
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal64SmemMax);
         if (ea == cudaSuccess)
             ea = cudaFuncSetAttribute(k_real64<false, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPwTableBytes);
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReal64SmemMax);
         const int rca = cuda_check(ctx, ea, "real-space shared memory attribute");
         if (rca) return rca;
     }
