@@ -193,6 +193,9 @@ def test_packed_state_gives_the_same_trajectory():
         torch.cuda.synchronize()
         outs.append((md.R.cpu().numpy(), md.q.cpu().numpy(), md.energy_dict()["total"]))
         s.close()
-    assert np.array_equal(outs[0][0], outs[1][0])
-    assert np.array_equal(outs[0][1], outs[1][1])
-    assert outs[0][2] == outs[1][2]
+    # the FP32 mesh spread adds with float atomics in an order that varies from
+    # run to run, so the two trajectories agree to that rounding (a mis-homed
+    # buffer would differ at O(1))
+    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(outs[0][1], outs[1][1], rtol=0, atol=1e-5)
+    assert abs(outs[0][2] - outs[1][2]) <= 1e-7 * abs(outs[0][2])
