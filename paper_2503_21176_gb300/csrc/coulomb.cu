@@ -932,6 +932,43 @@ k_influence(int nc, int K2h, int K2, int stride_mod, typename C2<T>::type *__res
     }
 }
 
+// Influence multiply without the energy (every MD-step apply): a plain
+// elementwise product, one thread per point pair in FP32 (16-byte complex
+// loads) or per point in FP64, over the whole grid so that many loads are in
+// flight (the grid-stride energy variant above keeps a fixed grid for its
+// partials).
+__global__ void __launch_bounds__(kThreads) k_influence_mul32(int nc, float4 *__restrict__ meshc,
+                                                              const float2 *__restrict__ G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int npair = nc >> 1;
+    if (t < npair) {
+        float4 z = meshc[t];
+        const float2 g = G[t];
+        z.x *= g.x;
+        z.y *= g.x;
+        z.z *= g.y;
+        z.w *= g.y;
+        meshc[t] = z;
+    } else if (t == npair && (nc & 1)) {
+        float2 *zc = (float2 *)meshc + (nc - 1);
+        const float g = ((const float *)G)[nc - 1];
+        zc->x *= g;
+        zc->y *= g;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_influence_mul64(int nc, double2 *__restrict__ meshc,
+                                                              const double *__restrict__ G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nc) {
+        double2 z = meshc[t];
+        const double g = G[t];
+        z.x *= g;
+        z.y *= g;
+        meshc[t] = z;
+    }
+}
+
 struct GatherArgs {
     int n;
     int K0, K1, K2;
@@ -1456,10 +1493,12 @@ int pme_mesh_potential(qeq_ctx *ctx, double *energy4, cudaStream_t sp) {
             k_influence<T, true><<<kRedBlocks, kThreads, 0, sp>>>(
                 (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
                 (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
+        else if (f64)
+            k_influence_mul64<<<grid_for(ctx->meshc_n), kThreads, 0, sp>>>(
+                (int)ctx->meshc_n, (double2 *)ctx->meshc, (const double *)ctx->G);
         else
-            k_influence<T, false><<<kRedBlocks, kThreads, 0, sp>>>(
-                (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
-                (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, nullptr);
+            k_influence_mul32<<<grid_for(ctx->meshc_n / 2 + 1), kThreads, 0, sp>>>(
+                (int)ctx->meshc_n, (float4 *)ctx->meshc, (const float2 *)ctx->G);
     }
     prof_end(ctx, sp);
     ctx->launches++;
