@@ -41,6 +41,50 @@ template <> struct C2<float> { using type = float2; };
 // gather_in: sorted copies of the inputs
 // ---------------------------------------------------------------------------
 
+// Double to float by truncation toward zero on the integer pipe (GB300 runs
+// FP64 conversions on its 1/64-rate FP64 pipe): relative error below 2^-23,
+// magnitudes below 2^-126 become zero.  Valid for |x| < 2^128.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int sign = hi & (int)0x80000000;
+    const int ex = ((hi >> 20) & 0x7FF) - 1023 + 127;
+    if (ex <= 0) return __int_as_float(sign);
+    return __int_as_float(sign | (ex << 23) | ((hi & 0xFFFFF) << 3) | (int)(lo >> 29));
+}
+
+// floor(u) and the fraction u - floor(u) of u < 2^31.  For u >= 0 both come
+// from the bits of u (the fraction exact in 64-bit fixed point, then truncated
+// to float); a negative u (an atom that left the box through its lower face
+// since the list was built) takes the FP64 floor.
+__device__ __forceinline__ void split_floor(double u, int &k, float &frac) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    if (b >> 63) {
+        const double fl = floor(u);
+        k = (int)fl;
+        frac = f64_to_f32_trunc(u - fl);
+        return;
+    }
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < 0) {  // u < 1 (or 0)
+        k = 0;
+        frac = f64_to_f32_trunc(u);
+        return;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 52 - e;  // fraction bits (e <= 30)
+    k = (int)(m >> sh);
+    const unsigned long long f = m & ((1ull << sh) - 1);  // fraction = f 2^-sh
+    if (f == 0) {
+        frac = 0.0f;
+        return;
+    }
+    const int lz = __clzll(f);                 // the leading one at bit 63 - lz
+    const unsigned long long nf = f << lz;      // leading one at bit 63
+    const int fe = (63 - lz) - sh;              // fraction = 1.xxx 2^fe
+    frac = fe + 127 > 0 ? __int_as_float(((fe + 127) << 23) | (int)((nf >> 40) & 0x7FFFFF)) : 0.0f;
+}
+
 template <typename T>
 __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const double *__restrict__ R,
                             const double *__restrict__ w, const double *__restrict__ q,
@@ -51,7 +95,7 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (smax_bits) {
         // max |sigma| as float bits (non-negative floats order like their bits)
-        int32_t b = i < n ? __float_as_int(fabsf((float)sigma[perm[i]])) : 0;
+        int32_t b = i < n ? __float_as_int(f64_to_f32_trunc(sigma[perm[i]])) & 0x7FFFFFFF : 0;
         b = __reduce_max_sync(0xffffffffu, b);
         if ((threadIdx.x & 31) == 0 && b > 0) atomicMax(smax_bits, b);
     }
@@ -61,14 +105,30 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
     const double y = R[3 * (size_t)a + 1] + w[3 * (size_t)a + 1];
     const double z = R[3 * (size_t)a + 2] + w[3 * (size_t)a + 2];
     const double qa = q[a];
-    xq[i] = {(T)x, (T)y, (T)z, (T)qa};
-    if (xf) xf[i] = make_float4((float)x, (float)y, (float)z, 0.0f);
-    sg[i] = (T)sigma[a];
-    // scaled fractional coordinates u = K x / L, split into floor and fraction in FP64
+    // scaled fractional coordinates u = K x / L (x wrapped into [0, L)), split
+    // into floor and fraction
     const double ux = x * sK0, uy = y * sK1, uz = z * sK2;
-    const double fx = floor(ux), fy = floor(uy), fz = floor(uz);
-    sbase[i] = make_int4((int)fx, (int)fy, (int)fz, 0);
-    sfrac[i] = {(T)(ux - fx), (T)(uy - fy), (T)(uz - fz), (T)qa};
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 copies truncated on the integer pipe (at most 1 ulp, against the
+        // half ulp of rounding), the split exact from the bits
+        const float qf = f64_to_f32_trunc(qa);
+        xq[i] = {f64_to_f32_trunc(x), f64_to_f32_trunc(y), f64_to_f32_trunc(z), qf};
+        sg[i] = f64_to_f32_trunc(sigma[a]);
+        int kx, ky, kz;
+        float fx, fy, fz;
+        split_floor(ux, kx, fx);
+        split_floor(uy, ky, fy);
+        split_floor(uz, kz, fz);
+        sbase[i] = make_int4(kx, ky, kz, 0);
+        sfrac[i] = {fx, fy, fz, qf};
+    } else {
+        xq[i] = {(T)x, (T)y, (T)z, (T)qa};
+        if (xf) xf[i] = make_float4((float)x, (float)y, (float)z, 0.0f);
+        sg[i] = (T)sigma[a];
+        const double fx = floor(ux), fy = floor(uy), fz = floor(uz);
+        sbase[i] = make_int4((int)fx, (int)fy, (int)fz, 0);
+        sfrac[i] = {(T)(ux - fx), (T)(uy - fy), (T)(uz - fz), (T)qa};
+    }
 }
 
 // Charges only, for an apply at the positions of the previous one: the sorted
