@@ -132,7 +132,10 @@ void qeq_params_default(qeq_params *p);
 
 /* Check *p and allocate every device buffer.  The buffers are the cell arrays,
  * the ELLPACK neighbour list at its initial width, the PME meshes, the
- * influence table, the cuFFT plans and the Krylov / reduction scratch.
+ * influence table, the cuFFT plans and the Krylov / reduction scratch (FP64
+ * precision adds the pair-function tables of the real-space kernel, built on
+ * the host once per alpha and cutoff).  The context also owns one
+ * high-priority non-blocking stream and two events, used inside each apply.
  * Uses the current CUDA device.
  * On failure *out is NULL and the return code says why.  Synchronises. */
 int qeq_create(const qeq_params *p, qeq_ctx **out);
@@ -263,6 +266,12 @@ int qeq_neighbor_build_noalloc(const double *R, int64_t n_atoms, const double *b
  * F:      device [N][3] output Coulomb force q_i E_i (nullable).
  * energy: device [4] output doubles (nullable): total 1/2 q.v, real-space part,
  *         reciprocal mesh energy 1/2 sum G |Q^|^2, self part.
+ * Ordering: all work is ordered on `stream`.  Inside, the mesh chain (spread,
+ * FFTs, influence) runs on the context's own stream, forked from `stream`
+ * after the gathers and joined back into it before the outputs are written,
+ * so to the caller the apply is one step of `stream` (capturable in a graph).
+ * FP32-mixed results agree between runs to the rounding of the mesh's float
+ * reductions, not bit for bit.
  * Returns QEQ_ERR_NOLIST before the first neighbour build.
  */
 int qeq_coulomb_apply(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
