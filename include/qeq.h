@@ -400,6 +400,31 @@ int qeq_selftest_erfc64(qeq_ctx *ctx, const double *x, double *out, double *dout
                         void *stream);
 
 /*
+ * Diagnostic, host only (touches no device): the FP64 real-space kernel's
+ * piecewise pair functions, built and evaluated exactly as a context builds
+ * and the kernel evaluates them (same tables, same bit indexing, same fused
+ * Horner steps).  which = 0: F(s) = erfc(alpha sqrt s) / sqrt s and
+ * G(s) = -(F(s) + (2 alpha / sqrt pi) exp(-alpha^2 s)) / s, the table of a
+ * context with this alpha and r_cut^2 = smax (both > 0); which = 1: the same
+ * functions at alpha = 1 of t = r^2 / gamma^2, the Gaussian-correction table
+ * (alpha and smax ignored).  For the n host arguments arg[k] > 0 it writes
+ * F[k], G[k] (host doubles) and in_table[k] = 1 where arg[k] falls in the
+ * kept pieces, else in_table[k] = 0 and leaves F[k], G[k] (the kernel then
+ * takes its direct erfc path).  *kept: the number of kept pieces.
+ * Returns QEQ_ERR_INVALID for a bad argument.
+ */
+int qeq_pair_table_eval(double alpha, double smax, int32_t which, int64_t n, const double *arg,
+                        double *F, double *G, int32_t *in_table, int32_t *kept);
+
+/*
+ * Diagnostic: the same evaluation on the device, with the tables of an FP64
+ * context (which as in qeq_pair_table_eval); arg, F, G, in_table are device
+ * arrays of n entries.  QEQ_ERR_INVALID for an FP32-mixed context.
+ */
+int qeq_selftest_pair64(qeq_ctx *ctx, int32_t which, const double *arg, double *F, double *G,
+                        int32_t *in_table, int64_t n, void *stream);
+
+/*
  * Tracing.  The paper reports a per-component time breakdown of its MD runs
  * (Sec. 4.2.3, Fig. MD_simulation).  These calls give the same breakdown per
  * library phase, measured with CUDA events on the caller's stream.

@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     qeq_neighbor_build,
     qeq_neighbor_displacement,
     qeq_neighbor_export,
+    qeq_pair_table_eval,
     qeq_params,
     qeq_params_default,
     qeq_profile_enable,
@@ -43,6 +44,7 @@ from ._lib import (  # noqa: F401
     qeq_bomd_step,
     qeq_shadow_init,
     qeq_shadow_run,
+    qeq_selftest_pair64,
     qeq_shadow_step,
     qeq_solve,
 )

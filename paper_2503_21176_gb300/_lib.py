@@ -123,6 +123,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_selftest_erfc32.restype = ctypes.c_int
     L.qeq_selftest_erfc64.argtypes = [P, P, P, P, ctypes.c_int64, P]
     L.qeq_selftest_erfc64.restype = ctypes.c_int
+    L.qeq_pair_table_eval.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int64,
+                                      P, P, P, P, ctypes.POINTER(ctypes.c_int32)]
+    L.qeq_pair_table_eval.restype = ctypes.c_int
+    L.qeq_selftest_pair64.argtypes = [P, ctypes.c_int32, P, P, P, P, ctypes.c_int64, P]
+    L.qeq_selftest_pair64.restype = ctypes.c_int
     SI = ctypes.POINTER(qeq_solve_info)
     L.qeq_solve.argtypes = [P, P, P, P, P, P, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, SI, P]
     L.qeq_solve.restype = ctypes.c_int
@@ -354,6 +359,34 @@ def qeq_selftest_erfc64(ctx, x, out, dout, stream=None) -> None:
     """FP64 piecewise erfc and its derivative of the real-space kernel (CUDA float64 tensors)."""
     _check(ctx, load().qeq_selftest_erfc64(ctx, _dev(x, "x"), _dev(out, "out"), _dev(dout, "dout"),
                                            x.numel(), _stream(stream)))
+
+
+def qeq_pair_table_eval(alpha, smax, which, arg):
+    """Host evaluation of the FP64 kernel's pair-function table (no device).
+
+    arg: float64 array.  Returns (F, G, in_table, kept): F, G are NaN where
+    in_table is 0 (outside the kept pieces)."""
+    import numpy as np
+
+    a = np.ascontiguousarray(arg, dtype=np.float64)
+    F = np.full(a.shape, np.nan)
+    G = np.full(a.shape, np.nan)
+    inn = np.zeros(a.shape, dtype=np.int32)
+    kept = ctypes.c_int32(0)
+    ptr = lambda x: ctypes.c_void_p(x.ctypes.data)
+    _check(None, load().qeq_pair_table_eval(float(alpha), float(smax), int(which), a.size, ptr(a),
+                                            ptr(F), ptr(G), ptr(inn), ctypes.byref(kept)))
+    return F, G, inn, int(kept.value)
+
+
+def qeq_selftest_pair64(ctx, which, arg, F, G, in_table, stream=None) -> None:
+    """Device evaluation of an FP64 context's pair-function table (CUDA tensors)."""
+    if not (isinstance(in_table, torch.Tensor) and in_table.is_cuda and in_table.dtype == torch.int32
+            and in_table.is_contiguous()):
+        raise ValueError("in_table must be a contiguous CUDA int32 tensor")
+    _check(ctx, load().qeq_selftest_pair64(ctx, int(which), _dev(arg, "arg"), _dev(F, "F"), _dev(G, "G"),
+                                           ctypes.c_void_p(in_table.data_ptr()), arg.numel(),
+                                           _stream(stream)))
 
 
 def qeq_solve(ctx, R, chi, eta, sigma, q, tol, max_iter=500, restart=40, stream=None):

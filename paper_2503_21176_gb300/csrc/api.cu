@@ -430,6 +430,31 @@ QEQ_API int qeq_selftest_erfc32(const float *x, float *out, int64_t n, void *str
 }
 
 namespace qeq {
+int pair_table_eval_host(int which, double alpha, double smax, int64_t n, const double *arg,
+                         double *F, double *G, int32_t *in, int32_t *kept);
+int pair64_selftest(qeq_ctx *ctx, int which, const double *arg, double *F, double *G, int32_t *in,
+                    int64_t n, cudaStream_t s);
+}
+
+QEQ_API int qeq_pair_table_eval(double alpha, double smax, int32_t which, int64_t n, const double *arg,
+                                double *F, double *G, int32_t *in_table, int32_t *kept) {
+    if ((which != 0 && which != 1) || n < 0 || !kept || (n > 0 && (!arg || !F || !G || !in_table)))
+        return set_error(nullptr, QEQ_ERR_INVALID, "pair_table_eval: bad argument");
+    if (which == 0 && !(alpha > 0.0 && smax > 0.0))
+        return set_error(nullptr, QEQ_ERR_INVALID, "pair_table_eval: alpha and smax must be positive");
+    return pair_table_eval_host(which, alpha, smax, n, arg, F, G, in_table, kept);
+}
+
+QEQ_API int qeq_selftest_pair64(qeq_ctx *ctx, int32_t which, const double *arg, double *F, double *G,
+                                int32_t *in_table, int64_t n, void *stream) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if ((which != 0 && which != 1) || n < 0 || (n > 0 && (!arg || !F || !G || !in_table)))
+        return set_error(ctx, QEQ_ERR_INVALID, "selftest: bad argument");
+    if (n == 0) return QEQ_OK;
+    return pair64_selftest(ctx, which, arg, F, G, in_table, n, (cudaStream_t)stream);
+}
+
+namespace qeq {
 int erfc64_selftest(qeq_ctx *ctx, const double *x, double *out, double *dout, int64_t n,
                     cudaStream_t s);
 }

@@ -17,6 +17,7 @@
 // spreading, the FFT and the gather in float.  It accumulates rows in float
 // chunks of 32 flushed into double, and keeps the energies and outputs in double.
 #include <cmath>
+#include <cstring>
 #include <tuple>
 #include <map>
 #include <mutex>
@@ -233,7 +234,7 @@ __device__ __forceinline__ bool pw_eval(const double2 *tab, unsigned npieces, do
     const unsigned piece = (unsigned)((hi >> (20 - SUB)) - ((1023 + OCT_LO) << SUB));
     if (piece >= npieces) return false;
     const unsigned lo = (unsigned)__double2loint(arg);
-    const int hy = 0x3FF00000 | ((hi << SUB) & 0x000FFFFF) | (int)(lo >> (32 - SUB));
+    const int hy = 0x3FF00000 | (int)(((unsigned)hi << SUB) & 0x000FFFFFu) | (int)(lo >> (32 - SUB));
     const double x = fma(__hiloint2double(hy, (int)(lo << SUB)), 2.0, -3.0);
     const double2 *c = tab + piece * NC;
     double2 cm = c[NC - 1];
@@ -547,6 +548,26 @@ __global__ void k_erfc64(int64_t n, const double *__restrict__ tab, const double
         double d;
         out[t] = erfc_pw(tab, x[t], d);
         dout[t] = d;
+    }
+}
+
+// Self-test hook: the FP64 kernel's pair-function table (which 0: F_alpha,
+// G_alpha of s; 1: F_1, G_1 of t) at n device arguments, as the kernel
+// evaluates it; in = 0 where the argument is outside the kept pieces.
+__global__ void k_pair64_selftest(int64_t n, int which, const double2 *__restrict__ tab,
+                                  unsigned npieces, const double *__restrict__ arg,
+                                  double *__restrict__ F, double *__restrict__ G,
+                                  int32_t *__restrict__ in) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double f = 0.0, g = 0.0;
+    const bool ok =
+        which == 0 ? pw_eval<kFGShape.oct_lo, kFGShape.sub_log2, kFGShape.ncoef>(tab, npieces, arg[t], f, g)
+                   : pw_eval<kGCShape.oct_lo, kGCShape.sub_log2, kGCShape.ncoef>(tab, npieces, arg[t], f, g);
+    in[t] = ok ? 1 : 0;
+    if (ok) {
+        F[t] = f;
+        G[t] = g;
     }
 }
 
@@ -1387,6 +1408,46 @@ const std::vector<double> &pw_cached(double alpha, const PwShape &sh, int np, in
     return it->second.tab;
 }
 
+// The kernel's table evaluation on the host (same bit indexing, same fused
+// Horner steps), for the host-only diagnostic.
+bool pw_eval_host(const PwShape &sh, const double *tab, int npieces, double arg, double &f,
+                  double &g) {
+    uint64_t b;
+    std::memcpy(&b, &arg, sizeof b);
+    const int hi = (int)(uint32_t)(b >> 32);
+    const unsigned piece =
+        (unsigned)((hi >> (20 - sh.sub_log2)) - ((1023 + sh.oct_lo) << sh.sub_log2));
+    if (piece >= (unsigned)npieces) return false;
+    const uint32_t lo = (uint32_t)b;
+    const uint32_t hy = 0x3FF00000u | (((uint32_t)hi << sh.sub_log2) & 0x000FFFFFu) |
+                        (lo >> (32 - sh.sub_log2));
+    const uint64_t yb = ((uint64_t)hy << 32) | (uint32_t)(lo << sh.sub_log2);
+    double y;
+    std::memcpy(&y, &yb, sizeof y);
+    const double x = std::fma(y, 2.0, -3.0);
+    const int D = sh.ncoef;
+    const double *c = tab + (size_t)piece * D * 2;
+    f = c[2 * (D - 1)];
+    g = c[2 * (D - 1) + 1];
+    for (int m = D - 2; m >= 0; --m) {
+        f = std::fma(f, x, c[2 * m]);
+        g = std::fma(g, x, c[2 * m + 1]);
+    }
+    return true;
+}
+
+// The table a context with this alpha and cutoff^2 smax uses (which 0), or the
+// Gaussian-correction table (which 1).
+const std::vector<double> &pw_context_table(int which, double alpha, double smax, const PwShape **sh,
+                                            int *kept) {
+    if (which == 0) {
+        *sh = &kFGShape;
+        return pw_cached(alpha, kFGShape, pw_pieces_for(kFGShape, smax), kept);
+    }
+    *sh = &kGCShape;
+    return pw_cached(1.0, kGCShape, pw_pieces_for(kGCShape, kErfcXMax * kErfcXMax * (1.0 + 2e-5)), kept);
+}
+
 // M_P(P / 2), the peak of the cardinal B-spline of order P, by the same order
 // recursion as bspline_mod2 (evaluated at the midpoint).
 double bspline_peak(int P) {
@@ -1846,18 +1907,14 @@ int coulomb_alloc(qeq_ctx *ctx) {
     // r^2 < r_c^2, and F_1, G_1 of r^2 / gamma^2 below the Gaussian-correction bound
     if (!ctx->fp32) {
         struct {
-            const PwShape *sh;
-            double alpha, smax;
             double **dev;
             int *pieces;
-        } tabs[2] = {
-            {&kFGShape, p.alpha, p.r_cut * p.r_cut, &ctx->fg_tab64, &ctx->fg_pieces},
-            {&kGCShape, 1.0, kErfcXMax * kErfcXMax * (1.0 + 2e-5), &ctx->gc_tab64, &ctx->gc_pieces},
-        };
-        for (auto &t : tabs) {
-            const int np = pw_pieces_for(*t.sh, t.smax);
+        } tabs[2] = {{&ctx->fg_tab64, &ctx->fg_pieces}, {&ctx->gc_tab64, &ctx->gc_pieces}};
+        for (int which = 0; which < 2; ++which) {
+            auto &t = tabs[which];
+            const PwShape *sh = nullptr;
             int valid = 0;
-            const std::vector<double> &tab = pw_cached(t.alpha, *t.sh, np, &valid);
+            const std::vector<double> &tab = pw_context_table(which, p.alpha, p.r_cut * p.r_cut, &sh, &valid);
             *t.pieces = valid;
             if (valid == 0) continue;
             rc = dev_alloc(ctx, (void **)t.dev, sizeof(double) * tab.size());
@@ -1989,6 +2046,33 @@ int erfc64_selftest(qeq_ctx *ctx, const double *x, double *out, double *dout, in
                     cudaStream_t s) {
     k_erfc64<<<grid_for(n), kThreads, 0, s>>>(n, ctx->erfc_tab64, x, out, dout);
     return cuda_check(ctx, cudaGetLastError(), "erfc64 selftest");
+}
+
+int pair_table_eval_host(int which, double alpha, double smax, int64_t n, const double *arg,
+                         double *F, double *G, int32_t *in, int32_t *kept) {
+    const PwShape *sh = nullptr;
+    int valid = 0;
+    const std::vector<double> &tab = pw_context_table(which, alpha, smax, &sh, &valid);
+    *kept = valid;
+    for (int64_t k = 0; k < n; ++k) {
+        double f, g;
+        const bool ok = pw_eval_host(*sh, tab.data(), valid, arg[k], f, g);
+        in[k] = ok ? 1 : 0;
+        if (ok) {
+            F[k] = f;
+            G[k] = g;
+        }
+    }
+    return QEQ_OK;
+}
+
+int pair64_selftest(qeq_ctx *ctx, int which, const double *arg, double *F, double *G, int32_t *in,
+                    int64_t n, cudaStream_t s) {
+    if (ctx->fp32) return set_error(ctx, QEQ_ERR_INVALID, "no FP64 pair tables in FP32-mixed mode");
+    const double2 *tab = (const double2 *)(which == 0 ? ctx->fg_tab64 : ctx->gc_tab64);
+    const unsigned np = (unsigned)(which == 0 ? ctx->fg_pieces : ctx->gc_pieces);
+    k_pair64_selftest<<<grid_for(n), kThreads, 0, s>>>(n, which, tab, np, arg, F, G, in);
+    return cuda_check(ctx, cudaGetLastError(), "pair table selftest");
 }
 
 int coulomb_apply_impl(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
