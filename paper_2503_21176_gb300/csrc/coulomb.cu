@@ -384,11 +384,14 @@ __device__ __forceinline__ void gauss_corr64(double r2, double si2, double sj,
 // kErfcXMax^2 with the margin of the FP32 Gaussian-correction test.
 constexpr float kGaussTest = (float)(kErfcXMax * kErfcXMax * (1.0 + 1e-5));
 
-// FP64 real space, one block per brick: the tile (double4 positions with q,
-// sigma) and the pair-function table in shared memory (GTILE: the tile in the
-// block's slice of a global scratch buffer instead), kTPR lanes per row.  The
-// erfc table of the Gaussian correction and of the direct path is read through
-// the read-only cache.
+// FP64 real space, one block per brick, kTPR lanes per row.  Dynamic shared
+// memory holds the two pair-function tables, the tile (double4 positions with
+// q, double sigma, float4 positions for the FP32 prefilter; GTILE: in the
+// block's slice of a global scratch buffer instead) and the per-lane queues of
+// deferred Gaussian corrections; usually one block per SM fits, which keeps the
+// FP64 pipe (the bound) about 88% busy.  The piecewise erfc of the direct path
+// is read through the read-only cache.  The register cap of two blocks per SM
+// (64) leaves the loop without spills.
 template <bool FIELD, bool GTILE>
 __global__ void __launch_bounds__(kRealMaxThreads, 2)
 k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32_t *__restrict__ tile_tot,
