@@ -48,6 +48,9 @@ PAIR_OPS = 40
 # scaled to the 300,000-atom box by the list entries processed (x 2.5).  Valid
 # for the kernel version that capture was taken of.
 REAL32_TRAFFIC_BYTES = (78.63e6 + 1.86e6) * 2.5
+# The same for the FP64 kernel: k_real64<1,0> on the 120,000-atom box moved
+# 31.49 GB/s x 2.744 ms = 86.4 MB (profiles/ncu_real64_water120k.md), x 2.5.
+REAL64_TRAFFIC_BYTES = 31.49e9 * 2.744e-3 * 2.5
 SM_COUNT, FP32_LANES, FP64_LANES = 152, 128, 2
 T_EV = 0.025852  # k_B * 300 K in eV
 
@@ -321,7 +324,7 @@ def roofline(res, precision, n_pairs_rc, peaks):
         achieved = n_pairs_rc * PAIR_OPS / (avg_ms * 1e-3) / 1e12
         out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-               "traffic": REAL32_TRAFFIC_BYTES if precision == "fp32_mixed" else None,
+               "traffic": REAL32_TRAFFIC_BYTES if precision == "fp32_mixed" else REAL64_TRAFFIC_BYTES,
                "traffic_unit": "DRAM bytes per launch (ncu, scaled from 120k atoms)",
                "peak_source": f"{SM_COUNT} SMs x {lanes} lanes x 2.07 GHz",
                "pairs_per_s": round(n_pairs_rc / (avg_ms * 1e-3), 1)}
