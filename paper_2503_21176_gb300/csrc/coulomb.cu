@@ -1778,6 +1778,53 @@ void launch_finalize(const double *part, int nslots, double *out, cudaStream_t s
     k_finalize<<<nslots, kThreads, 0, s>>>(part, out);
 }
 
+// Process-wide pool of mesh side streams (high-priority, non-blocking) and
+// their fork / join events, per device: a context takes one at creation and
+// returns it at destruction, so per-request contexts create no streams.  A
+// returned stream may still hold its last owner's queued work; the next
+// owner's work queues behind it, and each owner reaches its stream only
+// through its own fork and join events.
+namespace {
+struct SideStream {
+    int device;
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+std::mutex g_side_mu;
+std::vector<SideStream> g_side_free;
+}  // namespace
+
+cudaError_t side_acquire(int device, cudaStream_t *s, cudaEvent_t *fork, cudaEvent_t *join) {
+    {
+        std::lock_guard<std::mutex> lock(g_side_mu);
+        for (size_t k = 0; k < g_side_free.size(); ++k)
+            if (g_side_free[k].device == device) {
+                *s = g_side_free[k].s;
+                *fork = g_side_free[k].fork;
+                *join = g_side_free[k].join;
+                g_side_free.erase(g_side_free.begin() + (std::ptrdiff_t)k);
+                return cudaSuccess;
+            }
+    }
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(join, cudaEventDisableTiming);
+    return e;
+}
+
+void side_release(int device, cudaStream_t s, cudaEvent_t fork, cudaEvent_t join) {
+    if (!s || !fork || !join) {  // a partly created set (creation failed): destroy it
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (s) cudaStreamDestroy(s);
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_side_mu);
+    g_side_free.push_back({device, s, fork, join});
+}
+
 int coulomb_alloc(qeq_ctx *ctx) {
     const qeq_params &p = ctx->p;
     const int64_t n = ctx->n;
@@ -1854,11 +1901,7 @@ int coulomb_alloc(qeq_ctx *ctx) {
     cudaError_t e = cudaSuccess;
     int rc = QEQ_OK;
     if (p.recip != QEQ_RECIP_EWALD) {
-        int lo = 0, hi = 0;
-        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->pme_stream, cudaStreamNonBlocking, hi);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->pme_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->pme_join, cudaEventDisableTiming);
+        e = side_acquire(ctx->device, &ctx->pme_stream, &ctx->pme_fork, &ctx->pme_join);
         rc = cuda_check(ctx, e, "mesh side stream");
         if (rc) return rc;
     }
@@ -2031,9 +2074,7 @@ void coulomb_free(qeq_ctx *ctx) {
                     ctx->scal, ctx->energy4, ctx->fft_work, ctx->erfc_tab64, ctx->fg_tab64, ctx->gc_tab64, ctx->xf_pre, ctx->tile_scratch,
                     ctx->ticket};
     for (void *p : ptrs) dev_free(ctx, p);
-    if (ctx->pme_fork) cudaEventDestroy(ctx->pme_fork);
-    if (ctx->pme_join) cudaEventDestroy(ctx->pme_join);
-    if (ctx->pme_stream) cudaStreamDestroy(ctx->pme_stream);
+    if (ctx->pme_stream) side_release(ctx->device, ctx->pme_stream, ctx->pme_fork, ctx->pme_join);
     ctx->pme_fork = ctx->pme_join = nullptr;
     ctx->pme_stream = nullptr;
     ewald_free(ctx);
