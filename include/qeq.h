@@ -134,8 +134,9 @@ void qeq_params_default(qeq_params *p);
  * the ELLPACK neighbour list at its initial width, the PME meshes, the
  * influence table, the cuFFT plans and the Krylov / reduction scratch (FP64
  * precision adds the pair-function tables of the real-space kernel, built on
- * the host once per alpha and cutoff).  The context also owns one
- * high-priority non-blocking stream and two events, used inside each apply.
+ * the host once per alpha and cutoff).  The context also takes one
+ * high-priority non-blocking stream and two events, used inside each apply,
+ * from a process-wide pool per device (returned by qeq_destroy).
  * Uses the current CUDA device.
  * On failure *out is NULL and the return code says why.  Synchronises. */
 int qeq_create(const qeq_params *p, qeq_ctx **out);
