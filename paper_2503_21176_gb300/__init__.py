@@ -189,6 +189,35 @@ class ShadowMD:
         return {"kinetic": e[0], "shadow_potential": e[1], "total": e[2], "short": e[3],
                 "lambda": e[4], "sum_q": e[5], "residual_norm": e[6], "applies": e[7]}
 
+    def checkpoint(self, path, step: int = 0) -> None:
+        """Write the MD state, the per-atom parameters, `step` and the system
+        signature to the host file `path` (see checkpoint.py).  Waits for the
+        device."""
+        from . import checkpoint as ck
+
+        torch.cuda.synchronize(self.sys.device)
+        arrays = {k: getattr(self, k).cpu().numpy() for k in ck.STATE + ck.PARAMS}
+        ck.write(path, arrays, ck.system_signature(self.sys.params), step)
+
+    @classmethod
+    def resume(cls, system: System, path):
+        """A ShadowMD on `system` continuing from the checkpoint `path`, and the
+        stored step count.  The system must have the checkpoint's parameters
+        (ValueError otherwise); its neighbour list is built at the stored
+        positions.  Waits for the device."""
+        from . import checkpoint as ck
+
+        arrays, signature, step = ck.read(path)
+        ck.check_signature(signature, ck.system_signature(system.params))
+        t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=system.device).contiguous()
+        md = cls(system, t(arrays["chi"]), t(arrays["eta"]), t(arrays["sigma"]), t(arrays["mass"]),
+                 t(arrays["R"]), t(arrays["V"]), t(arrays["n_hist"][0]))
+        for k in ("F", "Kf", "n_hist", "q", "energies"):
+            getattr(md, k).copy_(t(arrays[k]))
+        system.neighbor_build(md.R)
+        torch.cuda.synchronize(system.device)
+        return md, step
+
 
 class BOMD:
     """Caller-side state of regular Born-Oppenheimer MD with a GMRES QEq solve per step."""
