@@ -74,6 +74,7 @@ class Result:
     t_admit: float
     t_done: float
     phases_ms: dict = field(default_factory=dict)  # host wall time per stage of the request
+    error: str | None = None  # set when the request failed (its arrays are then None)
 
     @property
     def latency_ms(self) -> float:
@@ -174,8 +175,9 @@ class Server:
                     req = ready.pop(0)
                     slot = self._free_slots.pop()
                     self._reserved += est[req.rid]
-                    fut = pool.submit(self._execute, req, slot, t0, time.perf_counter())
-                    inflight[fut] = (req, slot)
+                    t_admit = time.perf_counter()
+                    fut = pool.submit(self._execute, req, slot, t0, t_admit)
+                    inflight[fut] = (req, slot, t_admit)
                     max_conc = max(max_conc, len(inflight))
                 if not inflight:
                     if pending:
@@ -186,27 +188,35 @@ class Server:
                     timeout = max(0.0, pending[0].arrival - (time.perf_counter() - t0))
                 done, _ = cf.wait(list(inflight), timeout=timeout, return_when=cf.FIRST_COMPLETED)
                 for fut in done:
-                    req, slot = inflight.pop(fut)
+                    req, slot, t_admit = inflight.pop(fut)
                     self._reserved -= est[req.rid]
                     self._free_slots.append(slot)
-                    results[req.rid] = fut.result()
+                    try:
+                        results[req.rid] = fut.result()
+                    except Exception as exc:  # reported with the request; the others go on
+                        results[req.rid] = Result(req.rid, req.kind, req.n_atoms, None, None, None, {},
+                                                  t0 + req.arrival, t_admit, time.perf_counter(),
+                                                  error=f"{type(exc).__name__}: {exc}")
         finally:
             pool.shutdown(wait=True)
         t_end = time.perf_counter()
         res = [results[r] for r in sorted(results)]
-        lat = np.array([r.latency_ms for r in res])
+        ok = [r for r in res if r.error is None]
+        lat = np.array([r.latency_ms for r in ok]) if ok else np.zeros(1)
+        mean = lambda xs: round(float(np.mean(xs)), 3) if len(xs) else 0.0
         stats = {
             "requests": len(res),
-            "throughput_req_per_s": round(len(res) / max(1e-9, t_end - t0), 3),
+            "failed": len(res) - len(ok),
+            "throughput_req_per_s": round(len(ok) / max(1e-9, t_end - t0), 3),
             "makespan_s": round(t_end - t0, 4),
             "latency_ms_p50": round(float(np.percentile(lat, 50)), 3),
             "latency_ms_p99": round(float(np.percentile(lat, 99)), 3),
             "latency_ms_max": round(float(lat.max()), 3),
             "max_concurrent": max_conc,
-            "atoms_total": int(sum(r.n_atoms for r in res)),
+            "atoms_total": int(sum(r.n_atoms for r in ok)),
             "md_steps_total": int(sum(r.steps for r in requests if r.kind == "md")),
-            "queue_ms_mean": round(float(np.mean([1e3 * (r.t_admit - r.t_arrival) for r in res])), 3),
-            "stage_ms_mean": {k: round(float(np.mean([r.phases_ms.get(k, 0.0) for r in res])), 3)
+            "queue_ms_mean": mean([1e3 * (r.t_admit - r.t_arrival) for r in res]),
+            "stage_ms_mean": {k: mean([r.phases_ms.get(k, 0.0) for r in ok])
                               for k in ("upload", "create", "neighbor_build", "init", "steps",
                                         "download", "close")},
         }
