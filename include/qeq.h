@@ -171,8 +171,9 @@ int qeq_get_sizes(const qeq_ctx *ctx, int64_t *n_atoms, int32_t *width);
 /*
  * Cell-list neighbour build (Sec. 3.1, Alg. 1).
  * Steps: wrap positions into the box (x + w, w = -(L floor(x / L))); bin into
- * cells of edge >= r_cut + skin; counting sort by cell (ascending atom id
- * inside a cell); emit, for every atom, each (j, image) with
+ * cells of edge >= (r_cut + skin) / 2, paired into 2 x 2 x 2 bricks on axes
+ * with four or more cells (qeq_neighbor_plan); counting sort brick-major
+ * (ascending atom id inside a cell); emit, for every atom, each (j, image) with
  * |x_j - x_i + s L| < r_cut + skin into an ELLPACK row.  The pair decision
  * runs in FP64 with a fixed operation order and no fused multiply-add, so
  * the pair set is exactly the geometric one.
@@ -182,6 +183,32 @@ int qeq_get_sizes(const qeq_ctx *ctx, int64_t *n_atoms, int32_t *width);
  * Returns QEQ_OK, or QEQ_ERR_NONFINITE for a non-finite coordinate.
  */
 int qeq_neighbor_build(qeq_ctx *ctx, const double *R, void *stream);
+
+/*
+ * Host only (touches no device): the cell and brick decomposition that
+ * qeq_create / qeq_neighbor_build use for *p, and the FP32 prefilter band of
+ * the pair decision.  Per axis: nc cells of width cell_width >= r_list / 2
+ * (r_list = r_cut + skin; nc made even when >= 4), reach = cells a pair can
+ * span, brick = cells per brick (2, or 1 on axes with fewer than 4 cells),
+ * bricks = nc / brick, tile_reach = bricks a tile extends on each side;
+ * tile_bricks = prod (2 tile_reach + 1), n_bricks = prod bricks.  The emit
+ * keeps a candidate whose FP32 squared distance is below band_lo and drops
+ * one above band_hi without the FP64 test; inside the band the FP64 test
+ * decides.  Returns QEQ_ERR_INVALID / QEQ_ERR_UNSUPPORTED as qeq_create does.
+ */
+typedef struct qeq_nl_plan {
+    int32_t nc[3];
+    int32_t reach[3];
+    int32_t brick[3];
+    int32_t bricks[3];
+    int32_t tile_reach[3];
+    int32_t tile_bricks;
+    int64_t n_bricks;
+    double cell_width[3];
+    double r_list;
+    float band_lo, band_hi;
+} qeq_nl_plan;
+int qeq_neighbor_plan(const qeq_params *p, qeq_nl_plan *out);
 
 /*
  * Copy the current list to HOST memory in original atom numbering (for tests).

@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     qeq_neighbor_build,
     qeq_neighbor_displacement,
     qeq_neighbor_export,
+    qeq_neighbor_plan,
     qeq_pair_table_eval,
     qeq_params,
     qeq_params_default,

@@ -66,6 +66,22 @@ class qeq_params(ctypes.Structure):
     ]
 
 
+class qeq_nl_plan(ctypes.Structure):
+    _fields_ = [
+        ("nc", ctypes.c_int32 * 3),
+        ("reach", ctypes.c_int32 * 3),
+        ("brick", ctypes.c_int32 * 3),
+        ("bricks", ctypes.c_int32 * 3),
+        ("tile_reach", ctypes.c_int32 * 3),
+        ("tile_bricks", ctypes.c_int32),
+        ("n_bricks", ctypes.c_int64),
+        ("cell_width", ctypes.c_double * 3),
+        ("r_list", ctypes.c_double),
+        ("band_lo", ctypes.c_float),
+        ("band_hi", ctypes.c_float),
+    ]
+
+
 class qeq_md_state(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in ("R", "V", "F", "Kf", "n_hist", "q", "energies")]
 
@@ -123,6 +139,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_selftest_erfc32.restype = ctypes.c_int
     L.qeq_selftest_erfc64.argtypes = [P, P, P, P, ctypes.c_int64, P]
     L.qeq_selftest_erfc64.restype = ctypes.c_int
+    L.qeq_neighbor_plan.argtypes = [P, P]
+    L.qeq_neighbor_plan.restype = ctypes.c_int
     L.qeq_pair_table_eval.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int64,
                                       P, P, P, P, ctypes.POINTER(ctypes.c_int32)]
     L.qeq_pair_table_eval.restype = ctypes.c_int
@@ -359,6 +377,17 @@ def qeq_selftest_erfc64(ctx, x, out, dout, stream=None) -> None:
     """FP64 piecewise erfc and its derivative of the real-space kernel (CUDA float64 tensors)."""
     _check(ctx, load().qeq_selftest_erfc64(ctx, _dev(x, "x"), _dev(out, "out"), _dev(dout, "dout"),
                                            x.numel(), _stream(stream)))
+
+
+def qeq_neighbor_plan(params: qeq_params) -> dict:
+    """Host-only cell / brick decomposition and FP32 prefilter band for params."""
+    out = qeq_nl_plan()
+    _check(None, load().qeq_neighbor_plan(ctypes.byref(params), ctypes.byref(out)))
+    return {"nc": list(out.nc), "reach": list(out.reach), "brick": list(out.brick),
+            "bricks": list(out.bricks), "tile_reach": list(out.tile_reach),
+            "tile_bricks": int(out.tile_bricks), "n_bricks": int(out.n_bricks),
+            "cell_width": list(out.cell_width), "r_list": float(out.r_list),
+            "band_lo": float(out.band_lo), "band_hi": float(out.band_hi)}
 
 
 def qeq_pair_table_eval(alpha, smax, which, arg):

@@ -240,6 +240,37 @@ QEQ_API int qeq_neighbor_displacement(qeq_ctx *ctx, const double *R, double *max
     return nl_displacement(ctx, R, (cudaStream_t)stream, max_disp2);
 }
 
+QEQ_API int qeq_neighbor_plan(const qeq_params *p, qeq_nl_plan *out) {
+    if (!out) return set_error(nullptr, QEQ_ERR_INVALID, "out is NULL");
+    int rc = validate(p);
+    if (rc) return rc;
+    qeq_ctx *ctx = new (std::nothrow) qeq_ctx();
+    if (!ctx) return set_error(nullptr, QEQ_ERR_NOMEM, "host allocation failed");
+    ctx->p = *p;
+    ctx->n = p->n_atoms;
+    rc = nl_configure(ctx);  // host arithmetic only
+    if (rc) {
+        set_error(nullptr, rc, "%s", ctx->err.c_str());
+    } else {
+        const BrickGeom &g = ctx->geom;
+        for (int d = 0; d < 3; ++d) {
+            out->nc[d] = ctx->nc[d];
+            out->reach[d] = ctx->reach[d];
+            out->brick[d] = g.B[d];
+            out->bricks[d] = g.nb[d];
+            out->tile_reach[d] = g.br[d];
+            out->cell_width[d] = ctx->cw[d];
+        }
+        out->tile_bricks = g.T;
+        out->n_bricks = g.nbricks;
+        out->r_list = ctx->rl;
+        out->band_lo = ctx->rl2f_lo;
+        out->band_hi = ctx->rl2f_hi;
+    }
+    delete ctx;
+    return rc;
+}
+
 QEQ_API int qeq_coulomb_apply(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                               double *v, double *E, double *F, double *energy, void *stream) {
     if (!ctx) return QEQ_ERR_INVALID;
