@@ -44,7 +44,8 @@ enum qeq_status {
     QEQ_ERR_NOMEM = -5,       /* device allocation failed */
     QEQ_ERR_NOLIST = -6,      /* coulomb_apply before any neighbor_build */
     QEQ_ERR_NONFINITE = -7,   /* NaN or Inf found in the inputs */
-    QEQ_ERR_CAPACITY = -8     /* a neighbour row exceeds the hard width limit */
+    QEQ_ERR_CAPACITY = -8,    /* a neighbour row exceeds the hard width limit */
+    QEQ_ERR_BOUNDS = -9       /* bounds-checked build: a kernel index check failed */
 };
 
 enum qeq_precision {
@@ -451,6 +452,19 @@ int qeq_pair_table_eval(double alpha, double smax, int32_t which, int64_t n, con
  */
 int qeq_selftest_pair64(qeq_ctx *ctx, int32_t which, const double *arg, double *F, double *G,
                         int32_t *in_table, int64_t n, void *stream);
+
+/*
+ * Bounds-checked build.  Compiled with -DQEQ_BOUNDS (libqeq_bounds.so), the
+ * kernels check their data-dependent indices (list entries against the tile,
+ * the sorted-order permutation, tile slots in the emit) and, where one fails,
+ * record the first failing site and skip the access instead of reading or
+ * writing out of range.  qeq_build_info: *bounds_checked = 1 in that build,
+ * 0 otherwise (host only).  qeq_bounds_status: synchronises, writes the first
+ * failing site (0: none) to *site, clears it, and returns QEQ_ERR_BOUNDS when
+ * a check failed since the last call.
+ */
+int qeq_build_info(int32_t *bounds_checked);
+int qeq_bounds_status(qeq_ctx *ctx, int32_t *site);
 
 /*
  * Tracing.  The paper reports a per-component time breakdown of its MD runs

@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqeq.so")
+# the bounds-checked variant (-DQEQ_BOUNDS): kernels check their data-dependent
+# indices and report a failing site instead of accessing out of range
+BUILD_BOUNDS = os.path.join(PKG, "_build_bounds")
+LIB_BOUNDS = os.path.join(PKG, "libqeq_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
@@ -42,18 +46,22 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Compile (what is stale) and link; returns the library path.  bounds=True
+    builds the bounds-checked variant libqeq_bounds.so in its own directory."""
+    build_dir, lib = (BUILD_BOUNDS, LIB_BOUNDS) if bounds else (BUILD, LIB)
+    extra = ["-DQEQ_BOUNDS"] if bounds else []
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "qeq.h"))
     cc = nvcc()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src, *headers, __file__]):
-            jobs.append([cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj])
+            jobs.append([cc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
@@ -64,8 +72,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     print(r.stdout, r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {j[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft",
                "-Xlinker", "--exclude-libs,ALL", "-Xlinker", f"-rpath,{cudalib}"]
@@ -73,9 +81,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             print(" ".join(cmd))
             print(r.stdout, r.stderr)
-            raise RuntimeError("link of libqeq.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+            raise RuntimeError(f"link of {os.path.basename(lib)} failed")
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

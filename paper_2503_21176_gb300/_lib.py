@@ -32,6 +32,7 @@ _ERRORS = {
     -6: "QEQ_ERR_NOLIST",
     -7: "QEQ_ERR_NONFINITE",
     -8: "QEQ_ERR_CAPACITY",
+    -9: "QEQ_ERR_BOUNDS",
 }
 
 
@@ -139,6 +140,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_selftest_erfc32.restype = ctypes.c_int
     L.qeq_selftest_erfc64.argtypes = [P, P, P, P, ctypes.c_int64, P]
     L.qeq_selftest_erfc64.restype = ctypes.c_int
+    L.qeq_build_info.argtypes = [P]
+    L.qeq_build_info.restype = ctypes.c_int
+    L.qeq_bounds_status.argtypes = [P, P]
+    L.qeq_bounds_status.restype = ctypes.c_int
     L.qeq_neighbor_plan.argtypes = [P, P]
     L.qeq_neighbor_plan.restype = ctypes.c_int
     L.qeq_pair_table_eval.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int64,
@@ -377,6 +382,21 @@ def qeq_selftest_erfc64(ctx, x, out, dout, stream=None) -> None:
     """FP64 piecewise erfc and its derivative of the real-space kernel (CUDA float64 tensors)."""
     _check(ctx, load().qeq_selftest_erfc64(ctx, _dev(x, "x"), _dev(out, "out"), _dev(dout, "dout"),
                                            x.numel(), _stream(stream)))
+
+
+def qeq_build_info() -> dict:
+    """{"bounds_checked": bool}: whether the loaded library is the bounds-checked build."""
+    b = ctypes.c_int32(0)
+    _check(None, load().qeq_build_info(ctypes.byref(b)))
+    return {"bounds_checked": bool(b.value)}
+
+
+def qeq_bounds_status(ctx) -> int:
+    """First failing bounds-check site since the last call (0: none); raises
+    QeqError(QEQ_ERR_BOUNDS) when one failed.  Synchronises."""
+    site = ctypes.c_int32(0)
+    _check(ctx, load().qeq_bounds_status(ctx, ctypes.byref(site)))
+    return int(site.value)
 
 
 def qeq_neighbor_plan(params: qeq_params) -> dict:

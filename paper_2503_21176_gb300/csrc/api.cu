@@ -240,6 +240,31 @@ QEQ_API int qeq_neighbor_displacement(qeq_ctx *ctx, const double *R, double *max
     return nl_displacement(ctx, R, (cudaStream_t)stream, max_disp2);
 }
 
+QEQ_API int qeq_build_info(int32_t *bounds_checked) {
+    if (!bounds_checked) return set_error(nullptr, QEQ_ERR_INVALID, "NULL argument");
+#ifdef QEQ_BOUNDS
+    *bounds_checked = 1;
+#else
+    *bounds_checked = 0;
+#endif
+    return QEQ_OK;
+}
+
+QEQ_API int qeq_bounds_status(qeq_ctx *ctx, int32_t *site) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (!site) return set_error(ctx, QEQ_ERR_INVALID, "NULL argument");
+    int32_t v = 0;
+    cudaError_t e = cudaDeviceSynchronize();  // the context's kernels may run on any stream
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&v, ctx->d_flags + kFlagBounds, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_flags + kFlagBounds, 0, sizeof(int32_t));
+    const int rc = cuda_check(ctx, e, "bounds status");
+    if (rc) return rc;
+    *site = v;
+    if (v) return set_error(ctx, QEQ_ERR_BOUNDS, "bounds check failed at site %d", (int)v);
+    return QEQ_OK;
+}
+
 QEQ_API int qeq_neighbor_plan(const qeq_params *p, qeq_nl_plan *out) {
     if (!out) return set_error(nullptr, QEQ_ERR_INVALID, "out is NULL");
     int rc = validate(p);

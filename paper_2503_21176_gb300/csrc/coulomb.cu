@@ -92,16 +92,20 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
                             const double *__restrict__ sigma, double sK0, double sK1, double sK2,
                             typename V4<T>::type *__restrict__ xq, T *__restrict__ sg,
                             int4 *__restrict__ sbase, typename V4<T>::type *__restrict__ sfrac,
-                            int32_t *__restrict__ smax_bits, float4 *__restrict__ xf) {
+                            int32_t *__restrict__ smax_bits, float4 *__restrict__ xf,
+                            int32_t *__restrict__ flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (smax_bits) {
         // max |sigma| as float bits (non-negative floats order like their bits)
-        int32_t b = i < n ? __float_as_int(f64_to_f32_trunc(sigma[perm[i]])) & 0x7FFFFFFF : 0;
+        int32_t b = i < n && QEQ_IN_BOUNDS((unsigned)perm[i] < (unsigned)n, flags, kSiteGatherPerm)
+                        ? __float_as_int(f64_to_f32_trunc(sigma[perm[i]])) & 0x7FFFFFFF
+                        : 0;
         b = __reduce_max_sync(0xffffffffu, b);
         if ((threadIdx.x & 31) == 0 && b > 0) atomicMax(smax_bits, b);
     }
     if (i >= n) return;
     const int a = perm[i];
+    if (!QEQ_IN_BOUNDS((unsigned)a < (unsigned)n, flags, kSiteGatherPerm)) return;
     const double x = R[3 * (size_t)a] + w[3 * (size_t)a];
     const double y = R[3 * (size_t)a + 1] + w[3 * (size_t)a + 1];
     const double z = R[3 * (size_t)a + 2] + w[3 * (size_t)a + 2];
@@ -137,9 +141,10 @@ __global__ void k_gather_in(int n, const int32_t *__restrict__ perm, const doubl
 template <typename T>
 __global__ void k_gather_q(int n, const int32_t *__restrict__ perm, const double *__restrict__ q,
                            typename V4<T>::type *__restrict__ xq,
-                           typename V4<T>::type *__restrict__ sfrac) {
+                           typename V4<T>::type *__restrict__ sfrac, int32_t *__restrict__ flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (!QEQ_IN_BOUNDS((unsigned)perm[i] < (unsigned)n, flags, kSiteGatherPerm)) return;
     const T qa = (T)q[perm[i]];
     xq[i].w = qa;
     sfrac[i].w = qa;
@@ -455,6 +460,7 @@ k_real64(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
             int nq = 0;
             for (int k = sub; k < c; k += kTPR) {
                 const int e = nbr[list_index(k, i, a.n)];
+                if (!QEQ_IN_BOUNDS(e <= total, flags, kSiteReal64Entry)) continue;
                 // FP32 prefilter: pre_rc2_f exceeds r_c^2 by more than the FP32
                 // error of r^2, so only pairs that fail the FP64 test are dropped
                 const float4 xjf = tf[e];
@@ -723,6 +729,7 @@ k_real32(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int e = ev[u];
+                    if (!QEQ_IN_BOUNDS(e <= total, flags, kSiteReal32Entry)) continue;
                     const float4 xc = tile[e];
                     pair32<FIELD>(xc.x - xi.x, xc.y - xi.y, xc.z - xi.z, xc.w, tsg + e, si2, gpre,
                                   a.pal_f, a.c1_f, a.rc2_f, a.tspa_f, tv, tx, ty, tz);
@@ -1649,14 +1656,15 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ctx->applies++;
     prof_begin(ctx, kPhGatherIn, s);
     if (q_only) {
-        k_gather_q<T><<<grid_for(n), kThreads, 0, s>>>(n, ctx->perm, q, xq, (T4 *)ctx->sfrac);
+        k_gather_q<T><<<grid_for(n), kThreads, 0, s>>>(n, ctx->perm, q, xq, (T4 *)ctx->sfrac,
+                                                       ctx->d_flags);
     } else {
         int32_t *smax_bits = (!f64 && kRealLazySigma) ? ctx->d_flags + kFlagSigmaMax : nullptr;
         if (smax_bits) cudaMemsetAsync(smax_bits, 0, sizeof(int32_t), s);
         k_gather_in<T><<<grid_for(n), kThreads, 0, s>>>(
             n, ctx->perm, R, ctx->wrap_off, q, sigma, ctx->K[0] / p.box[0], ctx->K[1] / p.box[1],
             ctx->K[2] / p.box[2], xq, sg, ctx->sbase, (T4 *)ctx->sfrac, smax_bits,
-            f64 ? ctx->xf_pre : nullptr);
+            f64 ? ctx->xf_pre : nullptr, ctx->d_flags);
         ctx->gathered = true;
     }
     prof_end(ctx, s);

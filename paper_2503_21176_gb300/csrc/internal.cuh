@@ -62,8 +62,31 @@ enum Flag {
     kFlagMaxTile = 3,
     kFlagMaxRows = 4,
     kFlagTileOverflow = 5,
+    kFlagBounds = 6,  // bounds-checked build: first failing check site (kept across builds)
     kNumFlags = 8
 };
+
+// Sites of the bounds checks (the value kFlagBounds records).
+enum BoundsSite {
+    kSiteReal32Entry = 1,
+    kSiteReal64Entry = 2,
+    kSiteGatherPerm = 3,
+    kSiteEmitTile = 4,
+};
+
+// Bounds-checked build (-DQEQ_BOUNDS): QEQ_IN_BOUNDS(cond, flags, site) is
+// cond, and records site in flags[kFlagBounds] (first one wins) where cond is
+// false, so the caller skips the access.  Without QEQ_BOUNDS it is true and no
+// check is compiled.
+#ifdef QEQ_BOUNDS
+__device__ __forceinline__ bool qeq_bounds_check(bool ok, int32_t *flags, int site) {
+    if (!ok) atomicCAS(&flags[kFlagBounds], 0, site);
+    return ok;
+}
+#define QEQ_IN_BOUNDS(cond, flags, site) qeq_bounds_check((cond), (flags), (site))
+#else
+#define QEQ_IN_BOUNDS(cond, flags, site) true
+#endif
 
 // ---------------------------------------------------------------------------
 // Brick tiling of the cell grid.

@@ -235,7 +235,8 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
                                             int ncand, const double4_32a &xi, const float4 &xf,
                                             const double4_32a *__restrict__ xs64,
                                             const float4 *__restrict__ xs32, int cap, int (&c)[3],
-                                            uint32_t *__restrict__ scr) {
+                                            uint32_t *__restrict__ scr, int t_total,
+                                            int32_t *__restrict__ flags) {
     Cursor cu;
     cu.k = 0;
     cu.ct = tab[0];
@@ -272,6 +273,7 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
             keep = d2 < a.rl2;
         }
         if (!keep) continue;
+        if (!QEQ_IN_BOUNDS((unsigned)(j + cu.ct.z) < (unsigned)t_total, flags, kSiteEmitTile)) continue;
         const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
         if (m < cap) scr[list_index(kEmitLanes * m + s, i, a.n)] = (uint32_t)(j + cu.ct.z) | ((uint32_t)cls << 16);
         ++m;
@@ -343,7 +345,7 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
         int c[3] = {0, 0, 0};
         if (act) {
             const int4 *tab = ctab[cell_s[i] - (int)(b * g.bvol)];
-            emit_stream(a, i, s, tab, ncand, xs64[i], xs32[i], xs64, xs32, cap, c, scr);
+            emit_stream(a, i, s, tab, ncand, xs64[i], xs32[i], xs64, xs32, cap, c, scr, t_total, flags);
         }
         const int mine = c[0] + c[1] + c[2];
         // this lane's first row slot in each class: the classes in order, and in
@@ -556,6 +558,8 @@ int nl_alloc(qeq_ctx *ctx) {
     }
     ctx->h_flags = new (std::nothrow) int32_t[kNumFlags];
     if (!ctx->h_flags) return set_error(ctx, QEQ_ERR_NOMEM, "host allocation failed");
+    // every flag starts at 0; the builds clear all but the bounds flag
+    cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, ctx->alloc_stream);
     int width = ctx->p.max_neighbors;
     if (width <= 0) {
         const double V = ctx->p.box[0] * ctx->p.box[1] * ctx->p.box[2];
@@ -600,7 +604,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
     prof_begin(ctx, kPhNeighbor, s);
     ctx->launches += 5;
     cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s);
-    cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
+    cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kFlagBounds, s);  // the bounds flag persists
     k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(
         n, R, ctx->p.box[0], ctx->p.box[1], ctx->p.box[2], ctx->cw[0], ctx->cw[1], ctx->cw[2],
         ctx->geom, ctx->cell_of, ctx->cell_count, ctx->wrap_off, ctx->R_build, ctx->d_flags);
@@ -637,7 +641,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
             ctx->list_valid = false;
             return rc;
         }
-        cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kNumFlags, s);
+        cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kFlagBounds, s);
         prof_begin(ctx, kPhNeighbor, s);
         launch_emit(ctx, s);
         prof_end(ctx, s);
