@@ -210,6 +210,7 @@ QEQ_API int qeq_get_sizes(const qeq_ctx *ctx, int64_t *n_atoms, int32_t *width) 
 }
 
 QEQ_API int qeq_neighbor_build(qeq_ctx *ctx, const double *R, void *stream) {
+    NvtxRange nvtx_range("qeq_neighbor_build");
     if (!ctx) return QEQ_ERR_INVALID;
     if (!R) return set_error(ctx, QEQ_ERR_INVALID, "R is NULL");
     ctx->err.clear();
@@ -298,6 +299,7 @@ QEQ_API int qeq_neighbor_plan(const qeq_params *p, qeq_nl_plan *out) {
 
 QEQ_API int qeq_coulomb_apply(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
                               double *v, double *E, double *F, double *energy, void *stream) {
+    NvtxRange nvtx_range("qeq_coulomb_apply");
     if (!ctx) return QEQ_ERR_INVALID;
     if (!R || !q || !sigma || !v) return set_error(ctx, QEQ_ERR_INVALID, "NULL input or output");
     const bool field = E || F;
@@ -317,6 +319,7 @@ static int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *
 
 QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
                             void *stream) {
+    NvtxRange nvtx_range("qeq_shadow_init");
     int rc = check_md(ctx, prm, st);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
@@ -388,6 +391,7 @@ static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_st
 
 QEQ_API int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
                             void *stream) {
+    NvtxRange nvtx_range("qeq_shadow_step");
     int rc = check_md(ctx, prm, st);
     if (rc) return rc;
     if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "call qeq_shadow_init first");
@@ -406,6 +410,7 @@ QEQ_API int qeq_set_graphs(qeq_ctx *ctx, int on) {
 
 QEQ_API int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
                            int32_t n_steps, void *stream) {
+    NvtxRange nvtx_range("qeq_shadow_run");
     for (int32_t k = 0; k < n_steps; ++k) {
         int rc = qeq_shadow_step(ctx, prm, st, stream);
         if (rc) return rc;
@@ -528,6 +533,7 @@ QEQ_API int qeq_selftest_erfc64(qeq_ctx *ctx, const double *x, double *out, doub
 QEQ_API int qeq_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *eta,
                       const double *sigma, double *q, double tol, int32_t max_iter, int32_t restart,
                       qeq_solve_info *info, void *stream) {
+    NvtxRange nvtx_range("qeq_solve");
     if (!ctx) return QEQ_ERR_INVALID;
     if (!R || !chi || !eta || !sigma || !q) return set_error(ctx, QEQ_ERR_INVALID, "NULL argument");
     if (!(tol > 0.0) || max_iter < 1 || restart < 1)
@@ -563,6 +569,7 @@ static int check_bo(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *
 
 QEQ_API int qeq_bomd_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
                           int32_t max_iter, qeq_solve_info *info, void *stream) {
+    NvtxRange nvtx_range("qeq_bomd_init");
     int rc = check_bo(ctx, prm, st);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
@@ -577,6 +584,7 @@ QEQ_API int qeq_bomd_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *
 
 QEQ_API int qeq_bomd_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
                           int32_t max_iter, qeq_solve_info *info, void *stream) {
+    NvtxRange nvtx_range("qeq_bomd_step");
     int rc = check_bo(ctx, prm, st);
     if (rc) return rc;
     if (!ctx->list_valid) return set_error(ctx, QEQ_ERR_NOLIST, "call qeq_bomd_init first");

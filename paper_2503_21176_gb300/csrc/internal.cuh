@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cufft.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -524,6 +525,15 @@ __device__ __forceinline__ bool finalize_last_block(const double *part, double *
     __syncthreads();
     return true;
 }
+
+// NVTX range over a library entry point (host side: a timeline tool shows where
+// each call enqueues its work; without a tool attached the calls do nothing).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Record the start / end event of a profiled phase on stream s (no-op when off).
 inline void prof_begin(qeq_ctx *c, int ph, cudaStream_t s) {
