@@ -364,6 +364,23 @@ int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, vo
  * default stream.  on = 0 always launches kernel by kernel. */
 int qeq_set_graphs(qeq_ctx *ctx, int on);
 
+/*
+ * User short-range model.  A callback of this type replaces the
+ * parameter-selected short-range term (qeq_params.short_range) in
+ * qeq_shadow_init / qeq_shadow_step / qeq_shadow_run and the BO-MD calls:
+ * each evaluation calls it on the host with the current positions
+ * R (device [n_atoms][3]) and it writes the short-range forces F (device
+ * [n_atoms][3], overwritten) and energy (device double, overwritten), with
+ * all its work ordered on `stream` (it may be asynchronous; it must not wait
+ * for other streams' work).  It returns 0, or non-zero to fail the call
+ * (QEQ_ERR_INVALID).  qeq_set_short_range(ctx, NULL, NULL) restores the
+ * parameter-selected term.  While a callback is set the step is not captured
+ * into a CUDA graph (the callback may allocate or launch anything).
+ */
+typedef int (*qeq_short_fn)(void *user, int64_t n_atoms, const double *R, double *F, double *energy,
+                            void *stream);
+int qeq_set_short_range(qeq_ctx *ctx, qeq_short_fn fn, void *user);
+
 /* Same as qeq_shadow_step repeated n_steps times. */
 int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int32_t n_steps,
                    void *stream);

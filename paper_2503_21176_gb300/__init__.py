@@ -121,6 +121,40 @@ class System:
     def displacement2(self, R, stream=None) -> float:
         return qeq_neighbor_displacement(self.ctx, R, stream)
 
+    def set_short_range(self, fn=None):
+        """A user short-range model for the MD steps on this system: fn(R) ->
+        (F, E) with R, F CUDA float64 [N, 3] tensors and E a CUDA float64
+        scalar tensor, run on the step's stream.  fn None restores the
+        parameter-selected model.  Steps are not captured into graphs while it
+        is set."""
+        if fn is None:
+            _lib.qeq_set_short_range(self.ctx, None)
+            self._short_cb = None
+            return
+        dev = self.device
+
+        def view(ptr, shape):
+            class _Cai:
+                __cuda_array_interface__ = {"shape": shape, "typestr": "<f8", "data": (ptr, False),
+                                            "version": 3, "strides": None}
+            return torch.as_tensor(_Cai(), device=dev)
+
+        def cb(user, n, R_ptr, F_ptr, E_ptr, stream_ptr):
+            try:
+                st = torch.cuda.ExternalStream(stream_ptr, device=dev) if stream_ptr else \
+                    torch.cuda.default_stream(dev)
+                with torch.cuda.device(dev), torch.cuda.stream(st):
+                    F, E = fn(view(R_ptr, (n, 3)))
+                    view(F_ptr, (n, 3)).copy_(F)
+                    view(E_ptr, (1,)).copy_(torch.as_tensor(E, dtype=torch.float64, device=dev).reshape(1))
+                return 0
+            except Exception as exc:  # the library reports it as QEQ_ERR_INVALID
+                self.short_range_error = exc
+                return 1
+
+        self._short_cb = _lib.QEQ_SHORT_FN(cb)  # kept alive while set
+        _lib.qeq_set_short_range(self.ctx, self._short_cb)
+
     def apply(self, R, q, sigma, field=True, stream=None):
         """v = Phi q; returns (v, E, F, energy[4]) views of the preallocated outputs."""
         qeq_coulomb_apply(self.ctx, R, q, sigma, self.v, self.E if field else None,

@@ -67,6 +67,11 @@ class qeq_params(ctypes.Structure):
     ]
 
 
+# int (*)(void *user, int64_t n_atoms, const double *R, double *F, double *energy, void *stream)
+QEQ_SHORT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class qeq_nl_plan(ctypes.Structure):
     _fields_ = [
         ("nc", ctypes.c_int32 * 3),
@@ -140,6 +145,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_selftest_erfc32.restype = ctypes.c_int
     L.qeq_selftest_erfc64.argtypes = [P, P, P, P, ctypes.c_int64, P]
     L.qeq_selftest_erfc64.restype = ctypes.c_int
+    L.qeq_set_short_range.argtypes = [P, QEQ_SHORT_FN, P]
+    L.qeq_set_short_range.restype = ctypes.c_int
     L.qeq_build_info.argtypes = [P]
     L.qeq_build_info.restype = ctypes.c_int
     L.qeq_bounds_status.argtypes = [P, P]
@@ -382,6 +389,13 @@ def qeq_selftest_erfc64(ctx, x, out, dout, stream=None) -> None:
     """FP64 piecewise erfc and its derivative of the real-space kernel (CUDA float64 tensors)."""
     _check(ctx, load().qeq_selftest_erfc64(ctx, _dev(x, "x"), _dev(out, "out"), _dev(dout, "dout"),
                                            x.numel(), _stream(stream)))
+
+
+def qeq_set_short_range(ctx, fn, user=None) -> None:
+    """Set (fn: a QEQ_SHORT_FN) or clear (fn None) the user short-range model.
+    The caller keeps fn alive while it is set."""
+    cb = fn if fn is not None else QEQ_SHORT_FN()
+    _check(ctx, load().qeq_set_short_range(ctx, cb, user))
 
 
 def qeq_build_info() -> dict:

@@ -342,7 +342,7 @@ QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
 static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
                                cudaStream_t s) {
     const bool graphable = ctx->use_graphs && s != nullptr && !(ctx->p.krylov_tol > 0.0) &&
-                           !ctx->prof.on;
+                           !ctx->prof.on && !ctx->short_fn;
     if (!graphable) {
         int rc = shadow_evaluate(ctx, prm, st, s);
         if (rc) return rc;
@@ -399,6 +399,18 @@ QEQ_API int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
     rc = shadow_advance(ctx, prm, st, s);
     if (rc) return rc;
     return evaluate_and_finish(ctx, prm, st, s);
+}
+
+QEQ_API int qeq_set_short_range(qeq_ctx *ctx, qeq_short_fn fn, void *user) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (fn && !ctx->F_short) {
+        const int rc = dev_alloc(ctx, (void **)&ctx->F_short, sizeof(double) * 3 * (size_t)ctx->n);
+        if (rc) return rc;
+    }
+    ctx->short_fn = fn;
+    ctx->short_user = fn ? user : nullptr;
+    drop_graph(ctx);  // a captured step holds the previous short-range term
+    return QEQ_OK;
 }
 
 QEQ_API int qeq_set_graphs(qeq_ctx *ctx, int on) {

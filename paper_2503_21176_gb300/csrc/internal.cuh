@@ -364,6 +364,8 @@ struct qeq_ctx {
     double *Wb = nullptr;      // [m][N] Krylov basis
     double *Rb = nullptr;      // [m][N] J applied to the basis
     double *F_short = nullptr; // [N][3]
+    qeq_short_fn short_fn = nullptr;  // user short-range model (qeq_set_short_range)
+    void *short_user = nullptr;
     double *inv_u = nullptr;   // [N] 1 / u of the current evaluation
     double *inv_m = nullptr;   // [N] 1 / (m * mass_unit) of the current step
 
@@ -405,6 +407,14 @@ void dev_free(qeq_ctx *ctx, void *p);
 
 // ---- neighbour list (nlist.cu) ----
 int nl_configure(qeq_ctx *ctx);  // cell grid from params
+// Short-range term of an evaluation: the user callback, else the
+// parameter-selected model, else zero; forces into ctx->F_short, energies into
+// e_slot[0..1], on stream s.  has_short: whether ctx->F_short holds forces.
+int short_range_eval(qeq_ctx *ctx, const double *R, const double *mass, double *e_slot,
+                     cudaStream_t s);
+inline bool has_short(const qeq_ctx *ctx) {
+    return ctx->short_fn != nullptr || ctx->p.short_range == QEQ_SHORT_WATER;
+}
 int nl_alloc(qeq_ctx *ctx);
 int nl_alloc_list(qeq_ctx *ctx, int width);
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s);

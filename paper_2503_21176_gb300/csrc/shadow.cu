@@ -459,11 +459,9 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
 
     // short-range stand-in (or zero)
     prof_begin(ctx, kPhShadow, s);
-    if (ctx->p.short_range == QEQ_SHORT_WATER) {
-        int rc = short_range_forces(ctx, st->R, prm->mass, ctx->F_short, scal + S_SHORT, s);
+    {
+        int rc = short_range_eval(ctx, st->R, prm->mass, scal + S_SHORT, s);
         if (rc) return rc;
-    } else {
-        cudaMemsetAsync(scal + S_SHORT, 0, 2 * sizeof(double), s);
     }
     prof_end(ctx, s);
 
@@ -487,7 +485,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     const bool adaptive = ctx->p.krylov_tol > 0.0;
     prof_begin(ctx, kPhShadow, s);
     k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
-                                       ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr,
+                                       has_short(ctx) ? ctx->F_short : nullptr,
                                        ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb, ctx->phi, part,
                                        scal + S_MU, tk);
     fin();

@@ -144,4 +144,19 @@ int short_range_forces(qeq_ctx *ctx, const double *R, const double *, double *F_
     return cuda_check(ctx, cudaGetLastError(), "short-range launch");
 }
 
+int short_range_eval(qeq_ctx *ctx, const double *R, const double *mass, double *e_slot,
+                     cudaStream_t s) {
+    if (ctx->short_fn) {
+        cudaMemsetAsync(e_slot, 0, 2 * sizeof(double), s);
+        const int rc = ctx->short_fn(ctx->short_user, ctx->n, R, ctx->F_short, e_slot, (void *)s);
+        if (rc) return set_error(ctx, QEQ_ERR_INVALID, "short-range callback returned %d", rc);
+        return cuda_check(ctx, cudaGetLastError(), "short-range callback");
+    }
+    if (ctx->p.short_range == QEQ_SHORT_WATER)
+        return short_range_forces(ctx, R, mass, ctx->F_short, e_slot, s);
+    cudaMemsetAsync(e_slot, 0, 2 * sizeof(double), s);
+    return QEQ_OK;
+}
+
+
 }  // namespace qeq

@@ -438,19 +438,15 @@ int bomd_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, doub
     if (rc) return rc;
     cudaMemcpyAsync(st->q, ctx->gmSol, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
     double *scal = ctx->scal;
-    if (ctx->p.short_range == QEQ_SHORT_WATER) {
-        rc = short_range_forces(ctx, st->R, prm->mass, ctx->F_short, scal + 126, s);
-        if (rc) return rc;
-    } else {
-        cudaMemsetAsync(scal + 126, 0, 2 * sizeof(double), s);
-    }
+    rc = short_range_eval(ctx, st->R, prm->mass, scal + 126, s);
+    if (rc) return rc;
     // the solve applied the operator at these positions already
     rc = coulomb_apply_impl(ctx, st->R, st->q, prm->sigma, ctx->v_n, ctx->E_n, nullptr, nullptr,
                             true, s, true);
     if (rc) return rc;
     local.applies += 1;
     k_bo_forces<<<kRedBlocks, kThreads, 0, s>>>(
-        n, st->q, ctx->E_n, ctx->p.short_range == QEQ_SHORT_WATER ? ctx->F_short : nullptr, st->F);
+        n, st->q, ctx->E_n, has_short(ctx) ? ctx->F_short : nullptr, st->F);
     k_bo_energy_part<<<kRedBlocks, kThreads, 0, s>>>(n, st->q, prm->chi, prm->eta, ctx->v_n, ctx->part);
     launch_finalize(ctx->part, 4, scal + 128, s);
     k_bo_energies<<<1, 1, 0, s>>>(scal + 128, scal + 126, local.lambda, local.rel_residual,

@@ -58,3 +58,10 @@ def test_binding_rejects_host_tensors():
         qg._lib._dev(torch.zeros(3, dtype=torch.float64), "x")
     with pytest.raises(ValueError):
         qg._lib._dev(np.zeros(3), "x")
+
+
+def test_short_range_callback_needs_a_context():
+    """qeq_set_short_range rejects a NULL context before touching a device."""
+    from paper_2503_21176_gb300 import _lib
+
+    assert _lib.load().qeq_set_short_range(None, _lib.QEQ_SHORT_FN(), None) == -1
