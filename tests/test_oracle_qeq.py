@@ -224,3 +224,84 @@ def test_adaptive_krylov_stops_at_tolerance(system):
         N = w.n_atoms
         J = np.stack([qeq.jacobian_apply(Phi[:, j], np.eye(N)[j], w.eta) for j in range(N)], axis=1)
         assert np.linalg.norm(J @ Kf - f) <= tol * np.linalg.norm(f) * (1 + 1e-9) or extra == 7
+
+
+# ---------------------------------------------------------------------------
+# Regular BO-MD (Sec. 3.4): the oracle's BOSystem, pinned by identities that do
+# not restate its own energy expression
+# ---------------------------------------------------------------------------
+
+def _bo_system(w, tol, short=True):
+    from oracle import short_range
+
+    coul = _apply_ewald(w)
+    sr = (lambda R: short_range.water_short_range(R, w.box, RC)) if short else None
+    return qeq.BOSystem(coul, w.chi, w.eta, w.mass, dt=0.5, tol=tol, short=sr)
+
+
+def test_bo_energy_is_half_q_chi_at_the_solution(system):
+    """At the constrained minimum of Eq. (qeq_energy_func), (diag(u) + Phi) q = -chi - lambda,
+    so with Q_tot = 0 the BO energy collapses to 1/2 q.chi.  BOSystem.evaluate must
+    reach the dense LU charges and report that energy (plus V_short); a dropped or
+    doubled 1/2 on either quadratic term, or a v taken from other charges, breaks it."""
+    from oracle import short_range
+
+    w, Phi = system
+    qd, lam = qeq.qeq_dense_solve(Phi, w.chi, w.eta, 0.0)
+    e_short = short_range.water_short_range(w.R, w.box, RC)[0]
+    ev = _bo_system(w, 1e-13).evaluate(w.R, np.zeros(w.n_atoms))
+    assert np.abs(ev["q"] - qd).max() < 1e-10
+    assert abs(ev["lam"] - lam) < 1e-9
+    assert abs((ev["e_pot"] - e_short) - 0.5 * qd @ w.chi) < 1e-10 * abs(0.5 * qd @ w.chi)
+    # and the BO energy is below the QEq energy of any other neutral charge vector
+    rng = np.random.default_rng(12)
+    for _ in range(3):
+        d = rng.standard_normal(w.n_atoms)
+        d -= d.mean()
+        q2 = qd + 1e-2 * d
+        e2 = float(q2 @ w.chi + 0.5 * np.sum(w.eta * q2 * q2) + 0.5 * q2 @ Phi @ q2)
+        assert e2 > ev["e_pot"] - e_short
+
+
+def test_bo_forces_are_minus_gradient_of_the_bo_energy(system):
+    """F = q o E[q] + F_short equals -dU_BO/dR, with U_BO(R) the energy at the solved
+    charges of each displaced geometry (the charge response drops out at the
+    minimum).  Central differences, solver tolerance 1e-12."""
+    w, _ = system
+    bo = _bo_system(w, 1e-12)
+    ev = bo.evaluate(w.R, np.zeros(w.n_atoms))
+    h = 1e-5
+    for i in (0, 7, 31):
+        for d in range(3):
+            e = []
+            for sgn in (1.0, -1.0):
+                R = w.R.copy()
+                R[i, d] += sgn * h
+                e.append(bo.evaluate(R, ev["q"], ev["lam"])["e_pot"])
+            fd = -(e[0] - e[1]) / (2 * h)
+            assert abs(fd - ev["F"][i, d]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_bo_md_conserves_energy():
+    """40 regular BO-MD steps (0.5 fs, tolerance 1e-10, Coulomb only): the total energy
+    stays within the bound of the shadow run (measured 1.0e-5 eV) and the charges stay
+    neutral.  A second half kick with the forces of the previous geometry leaves it by
+    a factor of about 14, a doubled 1/2 q.v by about 160.  (The stiff bonds of the
+    flexible-water V_short add a Verlet fluctuation of about 1e-2 eV at this step, so
+    V_short is pinned by the force test instead.)"""
+    w = water_box(8, seed=51)
+    bo = _bo_system(w, 1e-10, short=False)
+    rng = np.random.default_rng(2)
+    V = rng.standard_normal(w.R.shape) * np.sqrt(0.0259 / (w.mass[:, None] * qeq.AMU_A2_FS2_IN_EV))
+    V -= (w.mass[:, None] * V).sum(0) / w.mass.sum()
+    st = bo.init_state(w.R, V, np.zeros(w.n_atoms))
+    e0 = st["e_kin"] + st["e_pot"]
+    es, kin = [], []
+    for _ in range(40):
+        st = bo.step(st)
+        assert abs(st["q"].sum()) < 1e-9
+        es.append(st["e_kin"] + st["e_pot"])
+        kin.append(st["e_kin"])
+    es = np.array(es)
+    assert np.ptp(kin) > 1e-2  # energy really moves between kinetic and potential
+    assert np.abs(es - e0).max() < 2e-4
