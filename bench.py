@@ -40,18 +40,21 @@ N_MOL = 100_000
 SEED = 2504
 ALPHA, R_CUT, SKIN, MESH, ORDER, RANK, KD, DT = 0.34, 8.0, 1.0, 144, 4, 2, 5, 0.5
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
-# algorithmic work per directed real-space pair inside r_c (FMA-pipe operations)
-PAIR_OPS = 40
+# algorithmic work per directed real-space pair inside r_c: about 40 floating-point
+# operations (the pair potential and field with the Gaussian correction) and 4
+# special-function evaluations (a reciprocal square root, a reciprocal and two
+# exponentials of the erfc forms)
+PAIR_FLOPS = 40
+PAIR_SFU = 4
 # DRAM bytes (read + write) per launch of the FP32 real-space kernel (potential
-# and field): ncu --set full of k_real32<1,0> on the 120,000-atom water box
-# (profiles/ncu_kernels_fp32_water120k.md: 78.63 MB read + 1.86 MB written),
-# scaled to the 300,000-atom box by the list entries processed (x 2.5).  Valid
-# for the kernel version that capture was taken of.
+# and field), from an ncu capture of k_real32<1,0> on the 120,000-atom water box
+# (78.63 MB read + 1.86 MB written), scaled to the 300,000-atom box by the list
+# entries processed (x 2.5).  Valid for the kernel version that capture was
+# taken of; None once the kernel changes.
 REAL32_TRAFFIC_BYTES = (78.63e6 + 1.86e6) * 2.5
 # The same for the FP64 kernel: k_real64<1,0> on the 120,000-atom box moved
-# 31.49 GB/s x 2.744 ms = 86.4 MB (profiles/ncu_real64_water120k.md), x 2.5.
+# 31.49 GB/s x 2.744 ms = 86.4 MB, x 2.5.
 REAL64_TRAFFIC_BYTES = 31.49e9 * 2.744e-3 * 2.5
-SM_COUNT, FP32_LANES, FP64_LANES = 152, 128, 2
 T_EV = 0.025852  # k_B * 300 K in eV
 
 
@@ -182,7 +185,7 @@ def aggregate_over_ranks(local_ms, steps, world, dist=None, device=None):
 # our arm
 # ---------------------------------------------------------------------------
 
-def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
+def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile, q0):
     import torch
 
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
@@ -215,12 +218,9 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
         res["apply_ms_p99"] = round(pct(ams, 99), 4)
         res["applies_per_s"] = round(1e3 / statistics.mean(ams), 2)
 
-        # shadow MD: initial n from the shadow charges of n = 0
+        # shadow MD from n(0) = the converged QEq charges of the initial geometry
         V0 = t(initial_state(w, SEED + 1))
-        md = qg.ShadowMD(sysm, t(w.chi), t(w.eta), sigma, t(w.mass), R, V0,
-                         torch.zeros(w.n_atoms, dtype=torch.float64, device=device))
-        md.init(stream)
-        md.n_hist.copy_(md.q.reshape(1, -1).expand_as(md.n_hist))
+        md = qg.ShadowMD(sysm, t(w.chi), t(w.eta), sigma, t(w.mass), R, V0, q0)
         md.init(stream)
         for _ in range(warmup):
             md.step(1, stream)
@@ -241,10 +241,17 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
             return [a.elapsed_time(b) for a, b in ev], [b - a for a, b in zip(c0, c1)]
 
         # timed region: the production path (each step's evaluation replayed from a
-        # CUDA graph), clocks sampled throughout
+        # CUDA graph), clocks sampled throughout.  A short timed region can end
+        # before nvidia-smi reports; the same steps then continue (not timed) until
+        # the sampler holds a few samples of this load, at most 5 s.
         sampler = ClockSampler(device.index)
+        clock_passes = 1
         with sampler:
             sms, dc = timed(steps)
+            t_end = time.perf_counter() + 5.0
+            while len(sampler.lines) < 5 and time.perf_counter() < t_end:
+                timed(steps)
+                clock_passes += 1
         # profiled pass over as many further steps: per-phase device time from CUDA
         # events on the launching stream (the profiler records events between
         # phases, so these steps run un-graphed)
@@ -265,7 +272,9 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
             "neighbor_rebuilds": dc[1],
             "applies_in_timed_steps": dc[2],
             "ms_per_step_profiled_pass": None if prof_ms is None else round(prof_ms, 4),
-            "clocks": sampler.summary(),
+            "clocks": dict(sampler.summary(), passes=clock_passes,
+                           note="the timed pass, then the same steps repeated (not timed) until "
+                                "the sampler held 5 samples"),
             "final_energy_eV": {k: round(v, 6) for k, v in e.items()},
         })
         res["_step_ms_sum"] = float(sum(sms))
@@ -273,6 +282,66 @@ def run_mode(qg, w, precision, device, steps, warmup, stream, flush, profile):
         res["_md"] = md
         res["_sys"] = sysm
     return res
+
+
+def converged_charges(qg, w, device, stream):
+    """QEq charges of the initial geometry: FP64 GMRES to a relative residual of 1e-10."""
+    import torch
+
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    s0 = qg.System(qg.make_params(w.n_atoms, w.box, alpha=ALPHA, r_cut=R_CUT, skin=SKIN,
+                                  mesh=(MESH, MESH, MESH), order=ORDER, precision="fp64"),
+                   device=device.index)
+    q0 = torch.zeros(w.n_atoms, dtype=torch.float64, device=device)
+    with torch.cuda.stream(stream):
+        s0.neighbor_build(t(w.R), stream)
+        info = qg.qeq_solve(s0.ctx, t(w.R), t(w.chi), t(w.eta), t(w.sigma), q0, tol=1e-10,
+                            stream=stream)
+        stream.synchronize()
+    s0.close()
+    return q0, info
+
+
+def tolerance_steps(qg, w, device, steps, warmup, stream, flush, q0, tol=0.1, max_rank=8):
+    """Shadow steps with the Krylov rank grown until the kernel residual |R c - f| / |f| is
+    <= tol (the paper's loose shadow tolerance, Sec. 4.2.3), FP32-mixed, from the
+    converged start.  Such a step reads the residual on the host after each added
+    vector, so it is launched kernel by kernel (no graph)."""
+    import torch
+
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    p = qg.make_params(w.n_atoms, w.box, alpha=ALPHA, r_cut=R_CUT, skin=SKIN, mesh=(MESH, MESH, MESH),
+                       order=ORDER, precision="fp32_mixed", krylov_rank=max_rank, krylov_tol=tol,
+                       dissipation_k=KD, dt=DT)
+    sysm = qg.System(p, device=device.index)
+    with torch.cuda.stream(stream):
+        md = qg.ShadowMD(sysm, t(w.chi), t(w.eta), t(w.sigma), t(w.mass), t(w.R),
+                         t(initial_state(w, SEED + 1)), q0)
+        md.init(stream)
+        for _ in range(warmup):
+            md.step(1, stream)
+        torch.cuda.synchronize(device)
+        ms, applies, resid = [], [], []
+        for k in range(steps):
+            flush.zero_()
+            a0 = qg.qeq_get_counters(sysm.ctx)[2]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            md.step(1, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            applies.append(qg.qeq_get_counters(sysm.ctx)[2] - a0)
+            resid.append(round(md.energy_dict()["residual_norm"], 6))
+    sysm.close()
+    return {"krylov_tol": tol, "max_rank": max_rank, "precision": "fp32_mixed",
+            "steps_per_s": round(1e3 / statistics.mean(ms), 3),
+            "ms_per_step": round(statistics.mean(ms), 4),
+            "step_ms_p50": round(pct(ms, 50), 4), "step_ms_p99": round(pct(ms, 99), 4),
+            "applies_per_step": round(statistics.mean(applies), 3),
+            "residual_norm_per_step": resid,
+            "note": "|q[n] - n| after each timed step; n(0) = converged QEq charges; "
+                    "kernel by kernel with one host read per added Krylov vector"}
 
 
 def e2e_steps(qg, md, steps, stream, device):
@@ -309,25 +378,38 @@ def e2e_steps(qg, md, steps, stream, device):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4)}
 
 
-def roofline(res, precision, n_pairs_rc, peaks):
-    """Roofline of the dominant phase of the timed steps (CUDA events on the launch stream)."""
+def roofline(res, precision, n_pairs_rc, peaks, pipes):
+    """Roofline of the dominant phase of the timed steps (CUDA events on the launch stream).
+
+    The real-space kernel is bound by the arithmetic pipes, so its fraction is the
+    method's floating-point work (PAIR_FLOPS per directed pair inside r_c) over
+    the FP32 (or FP64) FMA rate measured on this GPU by qeq_measure_peaks; the
+    special-function work is quoted beside it against the measured MUFU rate."""
     prof = res.get("_profile") or {}
     if not prof:
         return None
     name, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     share = ms / max(1e-9, sum(v[0] for v in prof.values()))
     avg_ms = ms / max(1, cnt)
-    clock = 2.07e9
     if name == "real_space":
-        lanes = FP32_LANES if precision == "fp32_mixed" else FP64_LANES
-        peak = SM_COUNT * lanes * clock / 1e12  # FMA-pipe Tops/s at the maximum SM clock
-        achieved = n_pairs_rc * PAIR_OPS / (avg_ms * 1e-3) / 1e12
+        fp32 = precision == "fp32_mixed"
+        peak = (pipes["fp32_flops"] if fp32 else pipes["fp64_flops"]) / 1e12
+        achieved = n_pairs_rc * PAIR_FLOPS / (avg_ms * 1e-3) / 1e12
+        sfu = n_pairs_rc * PAIR_SFU / (avg_ms * 1e-3)
         out = {"kernel": name, "bound": "alu", "achieved": round(achieved, 4),
                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-               "traffic": REAL32_TRAFFIC_BYTES if precision == "fp32_mixed" else REAL64_TRAFFIC_BYTES,
+               "traffic": REAL32_TRAFFIC_BYTES if fp32 else REAL64_TRAFFIC_BYTES,
                "traffic_unit": "DRAM bytes per launch (ncu, scaled from 120k atoms)",
-               "peak_source": f"{SM_COUNT} SMs x {lanes} lanes x 2.07 GHz",
-               "pairs_per_s": round(n_pairs_rc / (avg_ms * 1e-3), 1)}
+               "algorithmic": f"{PAIR_FLOPS} flop x {n_pairs_rc} directed pairs inside r_c "
+                              f"= {PAIR_FLOPS * n_pairs_rc / 1e9:.3f} GFLOP per launch (full list)",
+               "peak_source": f"qeq_measure_peaks: {'FP32' if fp32 else 'FP64'} FMA chains on "
+                              f"{pipes['sm_count']} SMs, CUDA events, best of 3 (measured)",
+               "sfu": {"achieved_ops_per_s": round(sfu, 1), "peak_ops_per_s": round(pipes["mufu_ops"], 1),
+                       "frac": round(sfu / pipes["mufu_ops"], 4), "per_pair": PAIR_SFU} if fp32 else None,
+               "pairs_per_s": round(n_pairs_rc / (avg_ms * 1e-3), 1),
+               "half_list_pairs_per_s": round(0.5 * n_pairs_rc / (avg_ms * 1e-3), 1),
+               "list_form": "full list: every unique pair evaluated from both rows, no atomics; "
+                            "half_list_pairs_per_s = unique pairs per second of the same launch"}
     else:
         gbs = peaks.get("hbm_gbs", 6800.0)
         out = {"kernel": name, "bound": "hbm", "achieved": None, "peak": gbs, "unit": "GB/s",
@@ -454,8 +536,30 @@ def count_pairs_within_rc(sysm, w):
     return int(np.count_nonzero(np.einsum("ij,ij->i", d, d) < R_CUT * R_CUT))
 
 
-def cpu_baseline(w):
-    """The oracle's shadow-step evaluation at full size, timed on the host cores."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or "unknown"."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(ln.split(":", 1) for ln in out.splitlines() if ":" in ln)
+        name = fields.get("Model name", "").strip()
+        vendor = fields.get("Vendor ID", "").strip()
+        if name:
+            return f"{vendor} {name}".strip()
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(w, q0, budget_s):
+    """The oracle's shadow step at full size on the host cores: the initial evaluation,
+    then whole steps until the budget is spent (at least one); value = timed steps/s."""
     from oracle import ewald, native, qeq
 
     def coul(R, x, need_field=True):
@@ -464,15 +568,22 @@ def cpu_baseline(w):
         return o["v"], o["E"]
 
     osys = qeq.ShadowSystem(coul, w.chi, w.eta, w.mass, rank=RANK, dt=DT, k_d=KD)
-    n0 = np.zeros(w.n_atoms)
-    t0 = time.perf_counter()
-    osys.evaluate(w.R, n0)
-    dt_s = time.perf_counter() - t0
-    return {"value": round(1.0 / dt_s, 5), "unit": UNIT, "cores": native.num_threads(),
-            "kind": "oracle",
-            "sample": f"one full shadow-step evaluation of the {w.n_atoms:,}-atom box "
-                      f"({RANK + 1} Coulomb applies: cell-list real space in C/OpenMP + numpy "
-                      f"PME {MESH}^3 + Krylov), {dt_s:.1f} s wall"}
+    t_start = time.perf_counter()
+    st = osys.init_state(w.R, initial_state(w, SEED + 1), q0)
+    times = []
+    while True:
+        t0 = time.perf_counter()
+        st = osys.step(st)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start + times[-1] > budget_s:
+            break
+    step_s = statistics.mean(times)
+    return {"value": round(1.0 / step_s, 5), "unit": UNIT, "cores": native.num_threads(),
+            "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"{len(times)} full shadow XL-BOMD steps of the {w.n_atoms:,}-atom box after "
+                      f"its initial evaluation ({RANK + 1} Coulomb applies per step: cell-list real "
+                      f"space in C/OpenMP + numpy PME {MESH}^3 + Krylov), "
+                      f"{time.perf_counter() - t_start:.1f} s wall, budget {budget_s:.0f} s"}
 
 
 def ours(args):
@@ -504,6 +615,9 @@ def ours(args):
     w = water_box(args.n_mol, seed=SEED + rank)
     stream = torch.cuda.Stream(device)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    # the pipe rates the real-space roofline divides by, measured on this GPU now
+    pipes = qg.qeq_measure_peaks(stream)
+    q0, solve_info = converged_charges(qg, w, device, stream)
 
     modes = ["fp32_mixed"] if args.no_fp64 else ["fp32_mixed", "fp64"]
     results = {}
@@ -511,7 +625,10 @@ def ours(args):
         if dist is not None:
             dist.barrier()
         results[m] = run_mode(qg, w, m, device, args.steps, args.warmup, stream, flush,
-                              profile=True)
+                              profile=True, q0=q0)
+    tol_run = None
+    if not args.no_tolerance_run:
+        tol_run = tolerance_steps(qg, w, device, args.steps, args.warmup, stream, flush, q0)
 
     head = results["fp32_mixed"]
     sysm, md = head["_sys"], head["_md"]
@@ -532,12 +649,12 @@ def ours(args):
 
     line = None
     if rank == 0:
-        roof = roofline(head, "fp32_mixed", n_pairs, peaks)
+        roof = roofline(head, "fp32_mixed", n_pairs, peaks, pipes)
         fp64 = None
         if "fp64" in results:
             r64 = results["fp64"]
             fp64 = {k: v for k, v in r64.items() if not k.startswith("_")}
-            fp64["roofline"] = roofline(r64, "fp64", n_pairs, peaks)
+            fp64["roofline"] = roofline(r64, "fp64", n_pairs, peaks, pipes)
         cfg = workload_config(args.n_mol)
         cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
         line = {
@@ -558,13 +675,23 @@ def ours(args):
             "fp64": fp64,
             "directed_pairs_within_rc": n_pairs,
             "precision_fp32_vs_fp64": precision,
+            "measured_pipes": {"fp32_tflops": round(pipes["fp32_flops"] / 1e12, 3),
+                               "fp64_tflops": round(pipes["fp64_flops"] / 1e12, 4),
+                               "mufu_tops": round(pipes["mufu_ops"] / 1e12, 4),
+                               "sm_count": pipes["sm_count"],
+                               "how": "qeq_measure_peaks: dependency chains on every SM, "
+                                      "CUDA events, best of 3"},
+            "initial_charges": {"method": "GMRES (FP64, Jacobi) to relative residual 1e-10",
+                                "iterations": solve_info["iterations"],
+                                "rel_residual": solve_info["rel_residual"]},
+            "tolerance_driven_step": tol_run,
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": head["gpu_launches"],
             "clocks": head["clocks"],
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(w, q0.cpu().numpy(), args.cpu_budget)
     for m in list(results):
         results[m]["_sys"].close()
     if dist is not None:
@@ -624,7 +751,8 @@ def reference(args):
         "data": "synthetic",
         "config": workload_config(args.n_mol),
         "cpu_baseline": {
-            "value": round(value, 5), "unit": UNIT, "cores": native.num_threads(), "kind": "oracle",
+            "value": round(value, 5), "unit": UNIT, "cores": native.num_threads(),
+            "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"{len(timed)} full shadow XL-BOMD steps of the {w.n_atoms:,}-atom box "
                       f"(FP64 oracle: C/OpenMP cell-list real space + numpy PME), "
                       f"capped at {budget_s:.0f} s total",
@@ -786,6 +914,9 @@ def main():
     ap.add_argument("--n-mol", type=int, default=N_MOL)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tolerance-run", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle work the cpu_baseline sample may spend")
     ap.add_argument("--reference-budget", type=float, default=200.0,
                     help="seconds of oracle work the reference arm may spend")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")

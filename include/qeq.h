@@ -375,7 +375,11 @@ int qeq_set_graphs(qeq_ctx *ctx, int on);
  * for other streams' work).  It returns 0, or non-zero to fail the call
  * (QEQ_ERR_INVALID).  qeq_set_short_range(ctx, NULL, NULL) restores the
  * parameter-selected term.  While a callback is set the step is not captured
- * into a CUDA graph (the callback may allocate or launch anything).
+ * into a CUDA graph (the callback may allocate or launch anything).  The call
+ * itself allocates nothing and queues no GPU work: the force buffer the
+ * callback writes belongs to the context from its creation.  Clearing or
+ * replacing a callback drops a captured step graph, which the next fixed-rank
+ * step re-captures.
  */
 typedef int (*qeq_short_fn)(void *user, int64_t n_atoms, const double *R, double *F, double *energy,
                             void *stream);
@@ -471,6 +475,18 @@ int qeq_selftest_pair64(qeq_ctx *ctx, int32_t which, const double *arg, double *
                         int32_t *in_table, int64_t n, void *stream);
 
 /*
+ * Diagnostic: measured throughput of the pipes the real-space pair sum is
+ * bound by, on the current device at its present clocks.  Writes host
+ * out4[0] FP32 FLOP/s (a fused multiply-add counts two), out4[1] FP64 FLOP/s,
+ * out4[2] special-function (MUFU reciprocal square root) operations/s and
+ * out4[3] the SM count (cudaDevAttrMultiProcessorCount).  Each rate is the
+ * best of three launches of a few milliseconds of independent dependency
+ * chains on every SM, timed with CUDA events on `stream`.  Allocates a small
+ * sink buffer and synchronises.  Errors go to qeq_last_error(NULL).
+ */
+int qeq_measure_peaks(double *out4, void *stream);
+
+/*
  * Bounds-checked build.  Compiled with -DQEQ_BOUNDS (libqeq_bounds.so), the
  * kernels check their data-dependent indices (list entries against the tile,
  * the sorted-order permutation, tile slots in the emit) and, where one fails,
@@ -508,6 +524,11 @@ const char *qeq_profile_phase_name(int phase);
 /* Host int64 out4[4]: this library's kernel launches (cuFFT excluded),
  * neighbour builds, Coulomb applies and cuFFT executions since creation. */
 int qeq_get_counters(const qeq_ctx *ctx, int64_t *out4);
+
+/* Host int64 out2[2]: shadow-step CUDA graphs captured, and shadow steps
+ * replayed from a captured graph, since creation (qeq_set_graphs).  Host only;
+ * QEQ_ERR_INVALID for a NULL argument. */
+int qeq_graph_stats(const qeq_ctx *ctx, int64_t *out2);
 
 #ifdef __cplusplus
 }

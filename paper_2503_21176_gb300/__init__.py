@@ -30,6 +30,8 @@ from ._lib import (  # noqa: F401
     qeq_destroy,
     qeq_get_counters,
     qeq_get_sizes,
+    qeq_graph_stats,
+    qeq_measure_peaks,
     qeq_last_error,
     qeq_neighbor_build,
     qeq_neighbor_displacement,
@@ -88,6 +90,25 @@ def make_params(n_atoms, box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(32, 32, 32)
 class System:
     """One periodic system on the current CUDA device, with apply outputs preallocated."""
 
+    short_range_error = None  # the exception of the last failing user short-range call
+    _short_cb = None
+
+    def _run(self, fn, *args):
+        """Call a library entry point; a failure caused by the user short-range model
+        is raised with that model's exception as its cause."""
+        try:
+            return fn(*args)
+        except QeqError as err:
+            cause = self.short_range_error
+            if cause is not None:
+                self.short_range_error = None
+                raise err from cause
+            raise
+
+    @property
+    def has_user_short_range(self) -> bool:
+        return self._short_cb is not None
+
     def __init__(self, params: qeq_params, device=None, stream=None):
         """stream=None: qeq_create; a torch.cuda.Stream: qeq_create_async on that stream."""
         self.params = params
@@ -127,6 +148,7 @@ class System:
         scalar tensor, run on the step's stream.  fn None restores the
         parameter-selected model.  Steps are not captured into graphs while it
         is set."""
+        self.short_range_error = None
         if fn is None:
             _lib.qeq_set_short_range(self.ctx, None)
             self._short_cb = None
@@ -140,6 +162,7 @@ class System:
             return torch.as_tensor(_Cai(), device=dev)
 
         def cb(user, n, R_ptr, F_ptr, E_ptr, stream_ptr):
+            self.short_range_error = None
             try:
                 st = torch.cuda.ExternalStream(stream_ptr, device=dev) if stream_ptr else \
                     torch.cuda.default_stream(dev)
@@ -182,7 +205,7 @@ class ShadowMD:
         self._st = md_state(self.R, self.V, self.F, self.Kf, self.n_hist, self.q, self.energies)
 
     def init(self, stream=None):
-        qeq_shadow_init(self.sys.ctx, self._prm, self._st, stream)
+        self.sys._run(qeq_shadow_init, self.sys.ctx, self._prm, self._st, stream)
 
     # order of the tensors in pack(): parameters, then the state the step advances,
     # then its results
@@ -215,9 +238,9 @@ class ShadowMD:
 
     def step(self, n_steps: int = 1, stream=None):
         if n_steps == 1:
-            qeq_shadow_step(self.sys.ctx, self._prm, self._st, stream)
+            self.sys._run(qeq_shadow_step, self.sys.ctx, self._prm, self._st, stream)
         else:
-            qeq_shadow_run(self.sys.ctx, self._prm, self._st, n_steps, stream)
+            self.sys._run(qeq_shadow_run, self.sys.ctx, self._prm, self._st, n_steps, stream)
 
     def energy_dict(self):
         e = self.energies.cpu().tolist()
@@ -232,7 +255,8 @@ class ShadowMD:
 
         torch.cuda.synchronize(self.sys.device)
         arrays = {k: getattr(self, k).cpu().numpy() for k in ck.STATE + ck.PARAMS}
-        ck.write(path, arrays, ck.system_signature(self.sys.params), step)
+        ck.write(path, arrays, ck.system_signature(self.sys.params, self.sys.has_user_short_range),
+                 step)
 
     @classmethod
     def resume(cls, system: System, path):
@@ -243,7 +267,8 @@ class ShadowMD:
         from . import checkpoint as ck
 
         arrays, signature, step = ck.read(path)
-        ck.check_signature(signature, ck.system_signature(system.params))
+        ck.check_signature(signature, ck.system_signature(system.params,
+                                                          system.has_user_short_range))
         t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=system.device).contiguous()
         md = cls(system, t(arrays["chi"]), t(arrays["eta"]), t(arrays["sigma"]), t(arrays["mass"]),
                  t(arrays["R"]), t(arrays["V"]), t(arrays["n_hist"][0]))
@@ -273,10 +298,12 @@ class BOMD:
         self._st = _lib._bo_state(self.R, self.V, self.F, self.q, self.energies)
 
     def init(self, stream=None):
-        return qeq_bomd_init(self.sys.ctx, self._prm, self._st, self.tol, self.max_iter, stream)
+        return self.sys._run(qeq_bomd_init, self.sys.ctx, self._prm, self._st, self.tol,
+                             self.max_iter, stream)
 
     def step(self, stream=None):
-        return qeq_bomd_step(self.sys.ctx, self._prm, self._st, self.tol, self.max_iter, stream)
+        return self.sys._run(qeq_bomd_step, self.sys.ctx, self._prm, self._st, self.tol,
+                             self.max_iter, stream)
 
     def energy_dict(self):
         e = self.energies.cpu().tolist()

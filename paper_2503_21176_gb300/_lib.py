@@ -174,7 +174,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_profile_phase_name.argtypes = [ctypes.c_int]
     L.qeq_profile_phase_name.restype = ctypes.c_char_p
     L.qeq_get_counters.argtypes = [P, P]
-    for name in ("qeq_profile_enable", "qeq_profile_read", "qeq_get_counters"):
+    L.qeq_graph_stats.argtypes = [P, P]
+    L.qeq_measure_peaks.argtypes = [P, P]
+    L.qeq_measure_peaks.restype = ctypes.c_int
+    for name in ("qeq_profile_enable", "qeq_profile_read", "qeq_get_counters", "qeq_graph_stats"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("qeq_create", "qeq_get_sizes", "qeq_neighbor_build", "qeq_neighbor_export",
                  "qeq_neighbor_displacement", "qeq_coulomb_apply", "qeq_shadow_init",
@@ -343,6 +346,25 @@ def qeq_get_counters(ctx):
 
     out = np.zeros(4, dtype=np.int64)
     _check(ctx, load().qeq_get_counters(ctx, out.ctypes.data_as(ctypes.c_void_p)))
+    return tuple(int(x) for x in out)
+
+
+def qeq_measure_peaks(stream=None) -> dict:
+    """Measured FP32 / FP64 FLOP/s, MUFU ops/s and the SM count of the current device."""
+    import numpy as np
+
+    out = np.zeros(4, dtype=np.float64)
+    _check(None, load().qeq_measure_peaks(out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return {"fp32_flops": float(out[0]), "fp64_flops": float(out[1]), "mufu_ops": float(out[2]),
+            "sm_count": int(out[3])}
+
+
+def qeq_graph_stats(ctx):
+    """(shadow-step graphs captured, steps replayed from a graph) since creation."""
+    import numpy as np
+
+    out = np.zeros(2, dtype=np.int64)
+    _check(ctx, load().qeq_graph_stats(ctx, out.ctypes.data_as(ctypes.c_void_p)))
     return tuple(int(x) for x in out)
 
 

@@ -31,9 +31,11 @@ _SCALARS = ("n_atoms", "alpha", "r_cut", "skin", "order", "precision", "krylov_r
             "short_range", "recip", "k_cut")
 
 
-def system_signature(params) -> dict:
-    """The trajectory-relevant fields of a qeq_params, as plain numbers."""
-    sig = {}
+def system_signature(params, user_short_range: bool = False) -> dict:
+    """The trajectory-relevant fields of a qeq_params, as plain numbers, and whether a
+    user short-range model replaced the parameter-selected one (a run resumed
+    without the model it was started with would change its potential)."""
+    sig = {"user_short_range": bool(user_short_range)}
     for k in _SCALARS:
         if hasattr(params, k):
             v = getattr(params, k)

@@ -383,7 +383,9 @@ static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_st
         ctx->launches = l0;
         ctx->applies = a0;
         for (int k = 0; k < 14; ++k) ctx->graph_key[k] = key[k];
+        ctx->graph_captures++;
     }
+    ctx->graph_replays++;
     ctx->launches += ctx->graph_launches;
     ctx->applies += ctx->p.krylov_rank + 1;
     return cuda_check(ctx, cudaGraphLaunch(ctx->step_exec, s), "graph launch");
@@ -403,10 +405,8 @@ QEQ_API int qeq_shadow_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
 
 QEQ_API int qeq_set_short_range(qeq_ctx *ctx, qeq_short_fn fn, void *user) {
     if (!ctx) return QEQ_ERR_INVALID;
-    if (fn && !ctx->F_short) {
-        const int rc = dev_alloc(ctx, (void **)&ctx->F_short, sizeof(double) * 3 * (size_t)ctx->n);
-        if (rc) return rc;
-    }
+    if (fn && !ctx->F_short)
+        return set_error(ctx, QEQ_ERR_UNSUPPORTED, "this context has no short-range buffer");
     ctx->short_fn = fn;
     ctx->short_user = fn ? user : nullptr;
     drop_graph(ctx);  // a captured step holds the previous short-range term
@@ -481,6 +481,13 @@ QEQ_API int qeq_profile_read(qeq_ctx *ctx, double *ms, int64_t *counts, int n_ph
 
 QEQ_API const char *qeq_profile_phase_name(int phase) {
     return (phase >= 0 && phase < kNumPhases) ? kPhaseNames[phase] : "";
+}
+
+QEQ_API int qeq_graph_stats(const qeq_ctx *ctx, int64_t *out2) {
+    if (!ctx || !out2) return QEQ_ERR_INVALID;
+    out2[0] = ctx->graph_captures;
+    out2[1] = ctx->graph_replays;
+    return QEQ_OK;
 }
 
 QEQ_API int qeq_get_counters(const qeq_ctx *ctx, int64_t *out4) {

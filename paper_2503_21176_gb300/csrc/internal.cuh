@@ -386,6 +386,8 @@ struct qeq_ctx {
     int graph_width = 0;
     int graph_tile = 0, graph_rows = 0;  // launch geometry of the real-space kernel at capture
     int64_t graph_launches = 0;      // this library's kernels inside the graph
+    int64_t graph_captures = 0;      // step graphs captured since creation
+    int64_t graph_replays = 0;       // step graph launches since creation
     bool use_graphs = true;
 
     // ---- tracing ----

@@ -430,10 +430,10 @@ int shadow_alloc(qeq_ctx *ctx) {
         int rc = dev_alloc(ctx, b.ptr, b.bytes);
         if (rc) return rc;
     }
-    if (ctx->p.short_range == QEQ_SHORT_WATER) {
-        int rc = dev_alloc(ctx, (void **)&ctx->F_short, sizeof(double) * 3 * n);
-        if (rc) return rc;
-    }
+    // every context holds the short-range force buffer, so that registering a user
+    // model later (qeq_set_short_range) never allocates or orders a new buffer
+    int rc = dev_alloc(ctx, (void **)&ctx->F_short, sizeof(double) * 3 * n);
+    if (rc) return rc;
     return QEQ_OK;
 }
 

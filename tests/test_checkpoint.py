@@ -63,3 +63,16 @@ def test_wrong_shapes_and_files_are_rejected(tmp_path):
     np.savez(other, meta=np.frombuffer(b'{"format": "something else"}', dtype=np.uint8))
     with pytest.raises(ValueError, match="not a shadow-MD checkpoint"):
         ck.read(other)
+
+
+def test_user_short_range_model_is_part_of_the_signature(tmp_path):
+    """A run started with a user short-range model cannot resume without one (or the
+    other way round): the potential would change under the trajectory."""
+    p = _params()
+    path = tmp_path / "md.npz"
+    ck.write(path, _arrays(12, p.dissipation_k), ck.system_signature(p, user_short_range=True),
+             step=3)
+    _, sig, _ = ck.read(path)
+    ck.check_signature(sig, ck.system_signature(_params(), user_short_range=True))
+    with pytest.raises(ValueError, match="user_short_range"):
+        ck.check_signature(sig, ck.system_signature(_params()))
