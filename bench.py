@@ -344,6 +344,42 @@ def tolerance_steps(qg, w, device, steps, warmup, stream, flush, q0, tol=0.1, ma
                     "kernel by kernel with one host read per added Krylov vector"}
 
 
+def neighbor_method_times(qg, w_full, device, stream, reps=3):
+    """Neighbour-build time of the brick search and of the per-atom search (the paper's
+    one-program-per-atom form, Sec. 3.1) on the bench box and on serving sizes."""
+    import torch
+
+    from workloads import water_box
+
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=device)
+    rows = []
+    for n_mol in (100, 1000, 6667, None):
+        w = w_full if n_mol is None else water_box(n_mol, seed=2600 + n_mol)
+        R = t(w.R)
+        row = {"atoms": w.n_atoms}
+        for method in ("brick", "atom"):
+            s = qg.System(qg.make_params(w.n_atoms, w.box, alpha=ALPHA, r_cut=R_CUT, skin=SKIN,
+                                         mesh=(8, 8, 8), order=ORDER, precision="fp32_mixed"),
+                          device=device.index)
+            qg.qeq_set_neighbor_method(s.ctx, method)
+            with torch.cuda.stream(stream):
+                s.neighbor_build(R, stream)  # list width settled
+                ms = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s.neighbor_build(R, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+            row[f"{method}_ms"] = round(min(ms), 4)
+            s.close()
+        rows.append(row)
+    return {"rows": rows, "r_list_A": R_CUT + SKIN,
+            "note": "whole qeq_neighbor_build (wrap, bin, sort, emit, one host read), CUDA events, "
+                    "best of 3; both searches write the same list"}
+
+
 def e2e_steps(qg, md, steps, stream, device):
     """Same step through the C ABI with the state kept in HOST memory: every step
     copies the whole MD state (R, V, F, K f, n history) and the per-atom parameters
@@ -629,6 +665,7 @@ def ours(args):
     tol_run = None
     if not args.no_tolerance_run:
         tol_run = tolerance_steps(qg, w, device, args.steps, args.warmup, stream, flush, q0)
+    nl_methods = None if args.no_extras else neighbor_method_times(qg, w, device, stream)
 
     head = results["fp32_mixed"]
     sysm, md = head["_sys"], head["_md"]
@@ -685,6 +722,7 @@ def ours(args):
                                 "iterations": solve_info["iterations"],
                                 "rel_residual": solve_info["rel_residual"]},
             "tolerance_driven_step": tol_run,
+            "neighbor_methods": nl_methods,
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": head["gpu_launches"],
@@ -915,6 +953,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tolerance-run", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra measurements (neighbour searches, serving sample)")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work the cpu_baseline sample may spend")
     ap.add_argument("--reference-budget", type=float, default=200.0,

@@ -126,6 +126,24 @@ typedef struct qeq_params {
 
 typedef struct qeq_ctx qeq_ctx;
 
+/*
+ * Accuracy-driven Ewald parameters.  The paper picks alpha and the mesh from a
+ * requested accuracy with the heuristics of OpenMM (Sec. 3.2, Sec. 3.3); this
+ * is that rule, as the OpenMM User Guide states it for PME:
+ *   alpha   = sqrt(-ln(2 delta)) / r_cut,
+ *   mesh[d] = the smallest K >= max(order, 2 alpha box[d] / (3 delta^(1/5)))
+ *             whose prime factors are all 2, 3, 5 or 7 (fast FFT sizes),
+ * and, for the explicit k-vector sum, k_cut = 2 alpha sqrt(-ln(2 delta)), where
+ * the reciprocal factor exp(-k^2 / 4 alpha^2) falls to the same 2 delta (this
+ * library's choice; OpenMM states no k-sum rule in this form).  delta is about
+ * the relative RMS error of the forces; the mesh rule assumes fifth-order
+ * B-splines (order 5), and lower orders give larger errors at small delta.
+ * Reads p->r_cut, p->box, p->order and writes p->alpha, p->mesh, p->k_cut.
+ * Host only.  QEQ_ERR_INVALID for delta outside (0, 0.5), a non-positive cutoff
+ * or box edge, or a mesh above 4096.
+ */
+int qeq_params_from_tolerance(qeq_params *p, double delta);
+
 /* Fill *p with the defaults: alpha 0.34, r_cut 8, skin 1, mesh 32^3, order 4,
  * FP64, Gaussian self-energy on, k_e 14.3996454784, rank 2, K_d 5, dt 0.5,
  * no short-range model.  The caller still sets n_atoms and box. */
@@ -184,6 +202,20 @@ int qeq_get_sizes(const qeq_ctx *ctx, int64_t *n_atoms, int32_t *width);
  * Returns QEQ_OK, or QEQ_ERR_NONFINITE for a non-finite coordinate.
  */
 int qeq_neighbor_build(qeq_ctx *ctx, const double *R, void *stream);
+
+/*
+ * Neighbour search used by qeq_neighbor_build (Sec. 3.1, Alg. 1).  Both write
+ * the same list: the same pair set, bit for bit, in the same three distance
+ * classes per row (only the order inside a class differs), so every other call
+ * is unaffected.  QEQ_NL_BRICK (the default): one block per brick of
+ * 2 x 2 x 2 cells, four lanes per row walking the candidate cells that the
+ * rows of a cell share.  QEQ_NL_ATOM: one thread per atom looping over the
+ * cells around its own, with a counting pass and a placing pass, the form of
+ * the paper's Triton kernel (one program per atom).  Host only; takes effect
+ * at the next build.  QEQ_ERR_INVALID for another value.
+ */
+enum qeq_nl_method { QEQ_NL_BRICK = 0, QEQ_NL_ATOM = 1 };
+int qeq_set_neighbor_method(qeq_ctx *ctx, int method);
 
 /*
  * Host only (touches no device): the cell and brick decomposition that
@@ -384,6 +416,32 @@ int qeq_set_graphs(qeq_ctx *ctx, int on);
 typedef int (*qeq_short_fn)(void *user, int64_t n_atoms, const double *R, double *F, double *energy,
                             void *stream);
 int qeq_set_short_range(qeq_ctx *ctx, qeq_short_fn fn, void *user);
+
+/*
+ * Batched shadow steps, for a server holding many systems at once.  One
+ * qeq_batch_step advances each of the n member contexts (ctxs[k] with its own
+ * parameters prms[k] and state sts[k], all on the current device, each set up
+ * by qeq_shadow_init) by one step of qeq_shadow_step.  Every member's integrator
+ * update and displacement check is queued on `stream`; ONE host
+ * synchronisation then reads all skin checks; members with an atom past
+ * skin / 2 rebuild their lists; and ONE CUDA graph, whose parallel branches are
+ * the members' captured evaluations and second half kicks, runs them all.
+ * Members that cannot replay a graph (tolerance-driven rank, user short-range
+ * callback, profiler on) are evaluated kernel by kernel on the same stream.
+ * The batch caches that parent graph and rebuilds it only when the member list
+ * (order included) or a member's captured step changes.  Each member runs the
+ * kernels of its own qeq_shadow_step, so results equal n separate steps.
+ * `stream` must not be the legacy default stream; the members' earlier work
+ * must be ordered before it (same stream, or an event).  A member appears at
+ * most once.  Synchronises once (plus once per rebuilding member).
+ * qeq_batch_stats: host int64 out2[2] = parent graphs built, graph launches.
+ */
+typedef struct qeq_batch qeq_batch;
+int qeq_batch_create(qeq_batch **out);
+void qeq_batch_destroy(qeq_batch *b);
+int qeq_batch_step(qeq_batch *b, int32_t n, qeq_ctx *const *ctxs, const qeq_md_params *prms,
+                   qeq_md_state *sts, void *stream);
+int qeq_batch_stats(const qeq_batch *b, int64_t *out2);
 
 /* Same as qeq_shadow_step repeated n_steps times. */
 int qeq_shadow_run(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, int32_t n_steps,

@@ -31,6 +31,7 @@ from ._lib import (  # noqa: F401
     qeq_get_counters,
     qeq_get_sizes,
     qeq_graph_stats,
+    qeq_set_neighbor_method,
     qeq_measure_peaks,
     qeq_last_error,
     qeq_neighbor_build,
@@ -40,6 +41,7 @@ from ._lib import (  # noqa: F401
     qeq_pair_table_eval,
     qeq_params,
     qeq_params_default,
+    qeq_params_from_tolerance,
     qeq_profile_enable,
     qeq_profile_phase_name,
     qeq_profile_read,

@@ -175,6 +175,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_profile_phase_name.restype = ctypes.c_char_p
     L.qeq_get_counters.argtypes = [P, P]
     L.qeq_graph_stats.argtypes = [P, P]
+    L.qeq_params_from_tolerance.argtypes = [ctypes.POINTER(qeq_params), ctypes.c_double]
+    L.qeq_params_from_tolerance.restype = ctypes.c_int
+    L.qeq_set_neighbor_method.argtypes = [P, ctypes.c_int]
+    L.qeq_set_neighbor_method.restype = ctypes.c_int
     L.qeq_measure_peaks.argtypes = [P, P]
     L.qeq_measure_peaks.restype = ctypes.c_int
     for name in ("qeq_profile_enable", "qeq_profile_read", "qeq_get_counters", "qeq_graph_stats"):
@@ -520,6 +524,23 @@ def qeq_neighbor_export_coo(ctx, capacity=None, stream=None):
                                                _stream(stream)))
     m = int(npairs.value)
     return pi[:m], pj[:m], code[:m]
+
+
+def qeq_params_from_tolerance(params: qeq_params, delta: float) -> qeq_params:
+    """Set params.alpha, params.mesh and params.k_cut from the error tolerance delta
+    (OpenMM's PME rule; see include/qeq.h).  Host only; returns params."""
+    _check(None, load().qeq_params_from_tolerance(ctypes.byref(params), float(delta)))
+    return params
+
+
+QEQ_NL_BRICK, QEQ_NL_ATOM = 0, 1
+
+
+def qeq_set_neighbor_method(ctx, method) -> None:
+    """Neighbour search of the next builds: "brick" (QEQ_NL_BRICK) or "atom" (QEQ_NL_ATOM)."""
+    if isinstance(method, str):
+        method = {"brick": QEQ_NL_BRICK, "atom": QEQ_NL_ATOM}[method]
+    _check(ctx, load().qeq_set_neighbor_method(ctx, int(method)))
 
 
 def qeq_set_graphs(ctx, on: bool) -> None:

@@ -1,6 +1,7 @@
 // Exported C entry points of include/qeq.h: parameter checks, context lifetime,
 // error reporting, and the thin wrappers around the neighbour, Coulomb and
 // shadow-step code.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -306,7 +307,8 @@ QEQ_API int qeq_coulomb_apply(qeq_ctx *ctx, const double *R, const double *q, co
     return coulomb_apply_impl(ctx, R, q, sigma, v, E, F, energy, field, (cudaStream_t)stream);
 }
 
-static int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *st) {
+namespace qeq {
+int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *st) {
     if (!ctx) return QEQ_ERR_INVALID;
     if (!prm || !st) return set_error(ctx, QEQ_ERR_INVALID, "NULL md params or state");
     if (!prm->chi || !prm->eta || !prm->sigma || !prm->mass)
@@ -316,6 +318,7 @@ static int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *
     ctx->err.clear();
     return QEQ_OK;
 }
+}  // namespace qeq
 
 QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
                             void *stream) {
@@ -337,57 +340,78 @@ QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
 // replayed.  The graph is re-captured when the state, parameter or neighbour-list
 // buffers it was recorded with change, or the launch capacities of the
 // real-space kernels (tile and brick size) grow.  It is not used with a tolerance-driven
-// Krylov rank (host reads), with the profiler on, or on the legacy default
-// stream (which cannot be captured).
-static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
-                               cudaStream_t s) {
-    const bool graphable = ctx->use_graphs && s != nullptr && !(ctx->p.krylov_tol > 0.0) &&
-                           !ctx->prof.on && !ctx->short_fn;
-    if (!graphable) {
-        int rc = shadow_evaluate(ctx, prm, st, s);
-        if (rc) return rc;
-        return shadow_finish(ctx, prm, st, true, s);
-    }
+// Krylov rank (host reads), with the profiler on, with a user short-range
+// callback, or on the legacy default stream (which cannot be captured).
+namespace qeq {
+
+std::atomic<uint64_t> g_graph_generation{0};
+
+bool step_graphable(const qeq_ctx *ctx, cudaStream_t s) {
+    return ctx->use_graphs && s != nullptr && !(ctx->p.krylov_tol > 0.0) && !ctx->prof.on &&
+           !ctx->short_fn;
+}
+
+
+int ensure_step_graph(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const void *key[14] = {st->R, st->V, st->F, st->Kf, st->n_hist, st->q, st->energies,
                            prm->chi, prm->eta, prm->sigma, prm->mass, ctx->nbr, ctx->tile_scratch,
                            nullptr};
     bool same = ctx->step_exec && ctx->graph_width == ctx->width &&
                 ctx->graph_tile == ctx->tile_cap && ctx->graph_rows == ctx->rows_cap;
     for (int k = 0; k < 14 && same; ++k) same = key[k] == ctx->graph_key[k];
-    if (!same) {
-        drop_graph(ctx);
-        const int64_t l0 = ctx->launches, a0 = ctx->applies;
-        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture begin");
-        int rc = shadow_evaluate(ctx, prm, st, s);
-        if (!rc) rc = shadow_finish(ctx, prm, st, true, s);
-        cudaGraph_t g = nullptr;
-        e = cudaStreamEndCapture(s, &g);
-        if (rc) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture end");
-        // node priorities on: the mesh chain's kernels keep the priority of the
-        // side stream they were captured on
-        e = cudaGraphInstantiate(&ctx->step_exec, g, cudaGraphInstantiateFlagUseNodePriority);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(g);
-            return cuda_check(ctx, e, "graph instantiate");
-        }
-        ctx->step_graph = g;
-        ctx->graph_width = ctx->width;
-        ctx->graph_tile = ctx->tile_cap;
-        ctx->graph_rows = ctx->rows_cap;
-        ctx->graph_launches = ctx->launches - l0;
-        ctx->launches = l0;
-        ctx->applies = a0;
-        for (int k = 0; k < 14; ++k) ctx->graph_key[k] = key[k];
-        ctx->graph_captures++;
+    if (same) return QEQ_OK;
+    drop_graph(ctx);
+    const int64_t l0 = ctx->launches, a0 = ctx->applies;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture begin");
+    int rc = shadow_evaluate(ctx, prm, st, s);
+    if (!rc) rc = shadow_finish(ctx, prm, st, true, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
     }
+    if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture end");
+    // node priorities on: the mesh chain's kernels keep the priority of the
+    // side stream they were captured on
+    e = cudaGraphInstantiate(&ctx->step_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_check(ctx, e, "graph instantiate");
+    }
+    ctx->step_graph = g;
+    ctx->graph_width = ctx->width;
+    ctx->graph_tile = ctx->tile_cap;
+    ctx->graph_rows = ctx->rows_cap;
+    ctx->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    ctx->applies = a0;
+    for (int k = 0; k < 14; ++k) ctx->graph_key[k] = key[k];
+    ctx->graph_captures++;
+    ctx->graph_gen = ++g_graph_generation;
+    return QEQ_OK;
+}
+
+// Counters of one replay of the step graph (the graph's kernels, m + 1 applies).
+void count_step_replay(qeq_ctx *ctx) {
     ctx->graph_replays++;
     ctx->launches += ctx->graph_launches;
     ctx->applies += ctx->p.krylov_rank + 1;
+}
+
+}  // namespace qeq
+
+static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st,
+                               cudaStream_t s) {
+    if (!step_graphable(ctx, s)) {
+        int rc = shadow_evaluate(ctx, prm, st, s);
+        if (rc) return rc;
+        return shadow_finish(ctx, prm, st, true, s);
+    }
+    int rc = ensure_step_graph(ctx, prm, st, s);
+    if (rc) return rc;
+    count_step_replay(ctx);
     return cuda_check(ctx, cudaGraphLaunch(ctx->step_exec, s), "graph launch");
 }
 
@@ -410,6 +434,50 @@ QEQ_API int qeq_set_short_range(qeq_ctx *ctx, qeq_short_fn fn, void *user) {
     ctx->short_fn = fn;
     ctx->short_user = fn ? user : nullptr;
     drop_graph(ctx);  // a captured step holds the previous short-range term
+    return QEQ_OK;
+}
+
+// Smallest n' >= n whose prime factors are all 2, 3, 5 or 7.
+static int64_t smooth_size(int64_t n) {
+    for (;; ++n) {
+        int64_t m = n;
+        for (int f : {2, 3, 5, 7})
+            while (m % f == 0) m /= f;
+        if (m == 1) return n;
+    }
+}
+
+QEQ_API int qeq_params_from_tolerance(qeq_params *p, double delta) {
+    if (!p) return set_error(nullptr, QEQ_ERR_INVALID, "params_from_tolerance: NULL params");
+    if (!(delta > 0.0 && delta < 0.5))
+        return set_error(nullptr, QEQ_ERR_INVALID, "params_from_tolerance: delta %g outside (0, 0.5)",
+                         delta);
+    if (!(p->r_cut > 0.0) || !std::isfinite(p->r_cut))
+        return set_error(nullptr, QEQ_ERR_INVALID, "params_from_tolerance: r_cut must be positive");
+    const double lg = std::sqrt(-std::log(2.0 * delta));
+    const double alpha = lg / p->r_cut;
+    int32_t mesh[3];
+    for (int d = 0; d < 3; ++d) {
+        if (!(p->box[d] > 0.0) || !std::isfinite(p->box[d]))
+            return set_error(nullptr, QEQ_ERR_INVALID, "params_from_tolerance: box[%d] invalid", d);
+        const double bound = 2.0 * alpha * p->box[d] / (3.0 * std::pow(delta, 0.2));
+        const int64_t k = smooth_size(std::max<int64_t>(std::max(4, p->order), (int64_t)std::ceil(bound)));
+        if (k > 4096)
+            return set_error(nullptr, QEQ_ERR_INVALID,
+                             "params_from_tolerance: mesh %lld on axis %d exceeds 4096", (long long)k, d);
+        mesh[d] = (int32_t)k;
+    }
+    p->alpha = alpha;
+    for (int d = 0; d < 3; ++d) p->mesh[d] = mesh[d];
+    p->k_cut = 2.0 * alpha * lg;
+    return QEQ_OK;
+}
+
+QEQ_API int qeq_set_neighbor_method(qeq_ctx *ctx, int method) {
+    if (!ctx) return QEQ_ERR_INVALID;
+    if (method != QEQ_NL_BRICK && method != QEQ_NL_ATOM)
+        return set_error(ctx, QEQ_ERR_INVALID, "unknown neighbour method %d", method);
+    ctx->nl_method = method;
     return QEQ_OK;
 }
 

@@ -163,7 +163,7 @@ struct RealArgs {
     // FP32 copies for k_real32, rounded once on the host: a double-to-float
     // conversion in the kernel runs on the FP64 pipe (1/64 rate on GB300), and
     // under register pressure the compiler re-derives such values inside the loop.
-    float alpha_f, rc2_f, tspa_f, c1_f, pal_f, Lx_f, Ly_f, Lz_f;
+    float alpha_f, rc2_f, tspa_f, c1_f, pal_f, Lx_f, Ly_f, Lz_f, ke_f;
     int fg_pieces;  // kept pieces of the FP64 pair-function tables (0: direct erfc path only)
     int gc_pieces;
     float pre_rc2_f;  // FP32 prefilter bound of the FP64 kernel (r_c^2 plus the FP32 error)
@@ -677,15 +677,16 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float qj, c
 // sigma) in shared memory (GTILE: in the block's slice of a global scratch
 // buffer), kTPR lanes per row, FP32 pair math with one exp per erfc shared with
 // the field term, FP32 sums (each lane about r_list^3 rho / 4 terms) and an FP32
-// shuffle combine of the lanes (no FP64 arithmetic before the final scaling).  smax_bits holds the float bits of max |sigma| over the atoms
-// (written by the gather of the same apply).
+// shuffle combine of the lanes; the row's sums, scaled by k_e, go out as one
+// float4 (v, E) per sorted atom.  smax_bits holds the float bits of max |sigma|
+// over the atoms (written by the gather of the same apply).
 template <bool FIELD, bool GTILE>
 __global__ void __launch_bounds__(kRealMaxThreads, QEQ_REAL_MIN_BLOCKS)
 k_real32(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32_t *__restrict__ tile_tot,
          const uint16_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
          const float4 *__restrict__ xq, const float *__restrict__ sg,
          const int32_t *__restrict__ smax_bits, int cap, unsigned char *__restrict__ gtile,
-         int32_t *__restrict__ flags, double *__restrict__ v_s, double *__restrict__ E_s) {
+         int32_t *__restrict__ flags, float4 *__restrict__ vE) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     unsigned char *base = GTILE ? gtile + (size_t)blockIdx.x * cap * kTile32Bytes : smem_raw;
@@ -745,14 +746,14 @@ k_real32(RealArgs a, BrickGeom g, const int4 *__restrict__ tile_tab, const int32
                 tz += __shfl_xor_sync(0xffffffffu, tz, o);
             }
         }
+        // the row's sums scaled by k_e, in FP32 (one 16-byte store; an FP64
+        // epilogue would run on GB300's 1/64-rate FP64 pipe at every row pass)
         if (act && sub == 0) {
             const int i = i0 + r;
-            v_s[i] = a.ke * (double)tv;
-            if (FIELD) {
-                E_s[3 * (size_t)i] = a.ke * (double)tx;
-                E_s[3 * (size_t)i + 1] = a.ke * (double)ty;
-                E_s[3 * (size_t)i + 2] = a.ke * (double)tz;
-            }
+            if (FIELD)
+                vE[i] = make_float4(a.ke_f * tv, a.ke_f * tx, a.ke_f * ty, a.ke_f * tz);
+            else
+                reinterpret_cast<float *>(vE)[4 * (size_t)i] = a.ke_f * tv;
         }
     }
 }
@@ -1082,6 +1083,8 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
              const double *__restrict__ q, const double *__restrict__ sigma,
              const T *__restrict__ sg_sorted, double *__restrict__ v_out, double *__restrict__ E_out,
              double *__restrict__ F_out, double *__restrict__ part) {
+    // FP32-mixed: the real-space kernel left (v, E) as one float4 per sorted atom
+    const float4 *vE32 = reinterpret_cast<const float4 *>(E_s);
     double e_tot = 0.0, e_real = 0.0, e_self = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const int4 b = sbase[i];
@@ -1125,14 +1128,32 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
             else
                 sc += a.gauss_coef / sigma[atom];
         }
-        const double vs = v_s[i];
+        double vs, esx = 0.0, esy = 0.0, esz = 0.0;
+        if constexpr (std::is_same<T, float>::value) {
+            if (FIELD) {
+                const float4 r4 = vE32[i];
+                vs = r4.x;
+                esx = r4.y;
+                esy = r4.z;
+                esz = r4.w;
+            } else {
+                vs = reinterpret_cast<const float *>(vE32)[4 * (size_t)i];
+            }
+        } else {
+            vs = v_s[i];
+            if (FIELD) {
+                esx = E_s[3 * (size_t)i];
+                esy = E_s[3 * (size_t)i + 1];
+                esz = E_s[3 * (size_t)i + 2];
+            }
+        }
         const double vself = sc * qa;
         const double v = vs + (double)vr + vself;
         v_out[atom] = v;
         if (FIELD) {
-            const double Ex = E_s[3 * (size_t)i] - a.sx * (double)gx;
-            const double Ey = E_s[3 * (size_t)i + 1] - a.sy * (double)gy;
-            const double Ez = E_s[3 * (size_t)i + 2] - a.sz * (double)gz;
+            const double Ex = esx - a.sx * (double)gx;
+            const double Ey = esy - a.sy * (double)gy;
+            const double Ez = esz - a.sz * (double)gz;
             if (E_out) {
                 E_out[3 * (size_t)atom] = Ex;
                 E_out[3 * (size_t)atom + 1] = Ey;
@@ -1681,6 +1702,7 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ra.tspa_f = (float)(kTwoOverSqrtPi * ra.alpha);
     ra.c1_f = (float)(-ra.alpha * ra.alpha * 1.4426950408889634);
     ra.pal_f = (float)(0.3275911 * ra.alpha);
+    ra.ke_f = (float)ra.ke;
     ra.Lx_f = (float)ra.Lx;
     ra.Ly_f = (float)ra.Ly;
     ra.Lz_f = (float)ra.Lz;
@@ -1733,14 +1755,16 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
             auto *x4 = (const float4 *)xq;
             auto *s1 = (const float *)sg;
             const int32_t *sm = ctx->d_flags + kFlagSigmaMax;
+            // FP32 partial sums in the E_s buffer (24 bytes per atom hold the 16)
+            auto *vE32 = (float4 *)ctx->E_s;
             if (need_field && !L.gtile)
-                k_real32<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<true, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, vE32);
             else if (need_field)
-                k_real32<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<true, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, vE32);
             else if (!L.gtile)
-                k_real32<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<false, false><<<grid, L.threads, L.smem, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, vE32);
             else
-                k_real32<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, ctx->v_s, ctx->E_s);
+                k_real32<false, true><<<grid, L.threads, 0, s>>>(ra, ctx->geom, ctx->tile_tab, ctx->tile_tot, ctx->nbr, ctx->cnt, x4, s1, sm, L.cap, gt, fl, vE32);
         }
     }
 

@@ -386,9 +386,11 @@ struct qeq_ctx {
     int graph_width = 0;
     int graph_tile = 0, graph_rows = 0;  // launch geometry of the real-space kernel at capture
     int64_t graph_launches = 0;      // this library's kernels inside the graph
+    uint64_t graph_gen = 0;          // process-wide generation of the current step graph
     int64_t graph_captures = 0;      // step graphs captured since creation
     int64_t graph_replays = 0;       // step graph launches since creation
     bool use_graphs = true;
+    int nl_method = QEQ_NL_BRICK;  // neighbour search (qeq_set_neighbor_method)
 
     // ---- tracing ----
     qeq::Profiler prof;
@@ -459,6 +461,15 @@ int shadow_alloc(qeq_ctx *ctx);
 void shadow_free(qeq_ctx *ctx);
 int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
 int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
+// The integrator half of shadow_advance: kick, drift and n update, then the
+// displacement kernel, all queued on s with no host synchronisation.
+int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
+// Step graphs (api.cu): whether the step of ctx on s can replay a graph, the
+// capture (or reuse) of that graph, and the counters of one replay.
+int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *st);
+bool step_graphable(const qeq_ctx *ctx, cudaStream_t s);
+int ensure_step_graph(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
+void count_step_replay(qeq_ctx *ctx);
 int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
                   cudaStream_t s);
 

@@ -389,6 +389,131 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
     }
 }
 
+// Per-atom search (qeq_set_neighbor_method QEQ_NL_ATOM): the form of the paper's
+// Triton neighbour kernel (Sec. 3.1), one thread per atom looping over the
+// cells around its own, written in this library's list format so that the
+// real-space kernels take either list.  First the tile table of every brick
+// (one warp a brick), then one thread per sorted atom: a counting pass over its
+// (2 reach + 1)^3 neighbour cells gives the sizes of the three distance
+// classes, and a placing pass writes each kept candidate at the next slot of
+// its class.  Both passes take the same pair decision as k_emit (FP32 outside
+// the band, FP64 with a fixed operation order inside), so the pair set is the
+// same bit for bit; only the order inside a class differs.
+__global__ void __launch_bounds__(32)
+k_tile_tables(BrickGeom g, const int32_t *__restrict__ cell_start, int4 *__restrict__ tile_tab,
+              int32_t *__restrict__ tile_tot, int32_t *__restrict__ flags) {
+    __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
+    const int64_t b = blockIdx.x;
+    tile_table(g, b, cell_start, t_start, t_base, t_code, &t_total);
+    __syncwarp();
+    for (int rb = threadIdx.x; rb < g.T; rb += 32)
+        tile_tab[b * g.T + rb] = make_int4(t_start[rb], t_base[rb], t_code[rb], 0);
+    if (threadIdx.x == 0) {
+        tile_tot[b] = t_total;
+        atomicMax(&flags[kFlagMaxTile], t_total);
+        atomicMax(&flags[kFlagMaxRows], cell_start[(b + 1) * g.bvol] - cell_start[b * g.bvol]);
+    }
+}
+
+// One candidate test of the per-atom search: keep (FP32 outside the band, FP64
+// inside) and the distance class from the FP32 squared distance.
+__device__ __forceinline__ bool atom_pair_keep(const EmitArgs &a, const double4_32a &xi,
+                                               const float4 &xf, const float4 &xj,
+                                               const double4_32a *__restrict__ xs64, int j,
+                                               int sx, int sy, int sz, float shx, float shy,
+                                               float shz, int &cls) {
+    const float dxf = (xj.x - xf.x) + shx;
+    const float dyf = (xj.y - xf.y) + shy;
+    const float dzf = (xj.z - xf.z) + shz;
+    const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+    cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
+    if (d2f < a.lo) return true;
+    if (d2f > a.hi) return false;
+    const double4_32a xj64 = xs64[j];
+    const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), image_shift(sx, a.Lx, a.L2x));
+    const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), image_shift(sy, a.Ly, a.L2y));
+    const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), image_shift(sz, a.Lz, a.L2z));
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 < a.rl2;
+}
+
+template <bool PLACE>
+__device__ __forceinline__ void atom_search(const EmitArgs &a, const BrickGeom &g, int i, int cx,
+                                            int cy, int cz, int64_t b, const double4_32a &xi,
+                                            const float4 &xf, const double4_32a *__restrict__ xs64,
+                                            const float4 *__restrict__ xs32,
+                                            const int32_t *__restrict__ cell_start,
+                                            const int4 *__restrict__ ttab, int (&k)[3],
+                                            uint16_t *__restrict__ nbr) {
+    const int bx = cx / g.B[0], by = cy / g.B[1], bz = cz / g.B[2];
+    for (int ox = -a.rx; ox <= a.rx; ++ox) {
+        const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
+        const int tx = floor_div(ux, g.B[0]) - bx + g.br[0];
+        const float shx = (float)sx * a.Lfx;
+        for (int oy = -a.ry; oy <= a.ry; ++oy) {
+            const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
+            const int ty = floor_div(uy, g.B[1]) - by + g.br[1];
+            const float shy = (float)sy * a.Lfy;
+            for (int oz = -a.rz; oz <= a.rz; ++oz) {
+                const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
+                const int tz = floor_div(uz, g.B[2]) - bz + g.br[2];
+                const float shz = (float)sz * a.Lfz;
+                const bool self_img = (sx == 0) && (sy == 0) && (sz == 0);
+                const int cn = cell_index(g, wx, wy, wz);
+                const int jb = cell_start[cn], je = cell_start[cn + 1];
+                const int tbase = PLACE ? ttab[(tx * g.td[1] + ty) * g.td[2] + tz].y : 0;
+                for (int j = jb; j < je; ++j) {
+                    if (self_img && j == i) continue;
+                    int cls;
+                    if (!atom_pair_keep(a, xi, xf, xs32[j], xs64, j, sx, sy, sz, shx, shy, shz, cls))
+                        continue;
+                    if (PLACE) {
+                        const int slot = k[cls]++;
+                        if (slot < a.width) nbr[list_index(slot, i, a.n)] = (uint16_t)(j + tbase);
+                    } else {
+                        ++k[cls];
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit_atom(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64,
+            const float4 *__restrict__ xs32, const int32_t *__restrict__ cell_s,
+            const int32_t *__restrict__ cell_start, const int4 *__restrict__ tile_tab,
+            const int32_t *__restrict__ tile_tot, uint16_t *__restrict__ nbr,
+            int32_t *__restrict__ cnt, int32_t *__restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int c = cell_s[i];
+    int cx, cy, cz;
+    cell_coords(g, c, cx, cy, cz);
+    const int64_t b = c / g.bvol;
+    const int total = tile_tot[b];
+    if (total > kMaxTileAtoms) {  // the host reports the oversized tile
+        cnt[i] = 0;
+        return;
+    }
+    const double4_32a xi = xs64[i];
+    const float4 xf = xs32[i];
+    const int4 *ttab = tile_tab + b * g.T;
+    int k[3] = {0, 0, 0};
+    atom_search<false>(a, g, i, cx, cy, cz, b, xi, xf, xs64, xs32, cell_start, ttab, k, nbr);
+    const int row_tot = k[0] + k[1] + k[2];
+    if (row_tot > a.width) {
+        cnt[i] = 0;
+        atomicMax(&flags[kFlagMaxRow], row_tot);
+        return;
+    }
+    int start[3] = {0, k[0], k[0] + k[1]};
+    atom_search<true>(a, g, i, cx, cy, cz, b, xi, xf, xs64, xs32, cell_start, ttab, start, nbr);
+    const int pad_end = (row_tot + kListStripe - 1) / kListStripe * kListStripe;
+    for (int q = row_tot; q < pad_end; ++q) nbr[list_index(q, i, a.n)] = (uint16_t)total;
+    cnt[i] = row_tot;
+}
+
 // COO scatter, one block per brick: sorted row i with entries k < cnt[i] goes to
 // slots offset[i] + k as (original i, original j, image code), so the pair order
 // is the list's.
@@ -579,7 +704,8 @@ void nl_free(qeq_ctx *ctx) {
     delete[] ctx->h_flags;
 }
 
-static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
+// Launches the pair emission of the selected search; returns the kernels launched.
+static int launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     EmitArgs a;
     a.n = (int)ctx->n;
     a.ncx = ctx->nc[0]; a.ncy = ctx->nc[1]; a.ncz = ctx->nc[2];
@@ -593,16 +719,26 @@ static void launch_emit(qeq_ctx *ctx, cudaStream_t s) {
     a.t_near = (float)(ctx->rl2 / 3.0);
     a.t_cut = (float)(ctx->p.r_cut * ctx->p.r_cut);
     a.width = ctx->width;
+    if (ctx->nl_method == QEQ_NL_ATOM) {
+        k_tile_tables<<<(unsigned)ctx->geom.nbricks, 32, 0, s>>>(ctx->geom, ctx->cell_start,
+                                                                 ctx->tile_tab, ctx->tile_tot,
+                                                                 ctx->d_flags);
+        k_emit_atom<<<(unsigned)((ctx->n + kEmitThreads - 1) / kEmitThreads), kEmitThreads, 0, s>>>(
+            a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->tile_tab,
+            ctx->tile_tot, ctx->nbr, ctx->cnt, ctx->d_flags);
+        return 2;
+    }
     k_emit<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
         a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr,
         ctx->nbr_scratch, ctx->cnt, ctx->tile_tab, ctx->tile_tot, ctx->d_flags);
+    return 1;
 }
 
 int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
     const int n = (int)ctx->n;
     ctx->gathered = false;  // the sorted order changes
     prof_begin(ctx, kPhNeighbor, s);
-    ctx->launches += 5;
+    ctx->launches += 4;
     cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s);
     cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kFlagBounds, s);  // the bounds flag persists
     k_wrap_bin<<<grid_for(n), kThreads, 0, s>>>(
@@ -614,7 +750,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
     k_cell_sort<<<grid_for(ctx->ncell * 32), kThreads, 0, s>>>(
         ctx->ncell, ctx->cell_start, ctx->tmp_list, R, ctx->wrap_off, ctx->perm, ctx->cell_s,
         ctx->xs64, ctx->xs32);
-    launch_emit(ctx, s);
+    ctx->launches += launch_emit(ctx, s);
     prof_end(ctx, s);
     for (int attempt = 0; attempt < 4; ++attempt) {
         cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int32_t) * kNumFlags,
@@ -643,9 +779,8 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
         }
         cudaMemsetAsync(ctx->d_flags, 0, sizeof(int32_t) * kFlagBounds, s);
         prof_begin(ctx, kPhNeighbor, s);
-        launch_emit(ctx, s);
+        ctx->launches += launch_emit(ctx, s);
         prof_end(ctx, s);
-        ctx->launches++;
     }
     // launch capacities of the real-space kernels (grown in steps, never shrunk).
     // Rows: 1.15 x the mean brick (a brick above it takes a second pass), at
