@@ -380,6 +380,32 @@ def neighbor_method_times(qg, w_full, device, stream, reps=3):
                     "best of 3; both searches write the same list"}
 
 
+def serving_sample(device, n_requests=128, rate=200.0):
+    """A reduced serving stream (the first requests of the 512-request Poisson stream):
+    FP32-mixed, MD steps batched across requests; throughput and p50 / p99 latency."""
+    from paper_2503_21176_gb300.serve import Server, request_from_box
+    from workloads import serving_stream
+
+    stream = serving_stream(n_requests=n_requests, rate=rate)
+    reqs = [request_from_box(r["rid"], r["kind"], r["box"], r["mesh"], V=r["V"], steps=r["steps"],
+                             arrival=r["arrival"], precision="fp32_mixed") for r in stream]
+    # warm-up: one request of each mesh size and kind (cuFFT plans, graph captures,
+    # pinned host blocks), then the stream in real time
+    seen, warm = set(), []
+    for r in reqs:
+        if (r.mesh, r.kind) not in seen:
+            seen.add((r.mesh, r.kind))
+            warm.append(r)
+    Server(device=device.index, max_inflight=8).serve(warm + reqs[:8], realtime=False)
+    _, st = Server(device=device.index, max_inflight=8).serve(reqs, realtime=True)
+    return {"requests": n_requests, "arrival_rate_per_s": rate, "precision": "fp32_mixed",
+            "atoms": "100-20,000 log-uniform", "kinds": "half 1 QEq evaluation, half 20 MD steps",
+            "throughput_req_per_s": st["throughput_req_per_s"],
+            "latency_ms_p50": st["latency_ms_p50"], "latency_ms_p99": st["latency_ms_p99"],
+            "failed": st["failed"], "max_concurrent": st["max_concurrent"],
+            "md_batching": st["md_batching"], "stage_ms_mean": st["stage_ms_mean"]}
+
+
 def e2e_steps(qg, md, steps, stream, device):
     """Same step through the C ABI with the state kept in HOST memory: every step
     copies the whole MD state (R, V, F, K f, n history) and the per-atom parameters
@@ -666,6 +692,7 @@ def ours(args):
     if not args.no_tolerance_run:
         tol_run = tolerance_steps(qg, w, device, args.steps, args.warmup, stream, flush, q0)
     nl_methods = None if args.no_extras else neighbor_method_times(qg, w, device, stream)
+    serving = None if (args.no_extras or rank != 0) else serving_sample(device)
 
     head = results["fp32_mixed"]
     sysm, md = head["_sys"], head["_md"]
@@ -723,6 +750,7 @@ def ours(args):
                                 "rel_residual": solve_info["rel_residual"]},
             "tolerance_driven_step": tol_run,
             "neighbor_methods": nl_methods,
+            "serving_sample": serving,
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": head["gpu_launches"],
@@ -819,14 +847,14 @@ def serve_bench(args):
                       "atoms": "100-20,000 log-uniform", "kinds": "half 1 QEq evaluation, half 20 MD steps",
                       "mesh": "smallest 2^k or 3*2^k with spacing <= 1.0 A", "r_c": 8.0,
                       "max_inflight": args.serve_inflight}}
-    for prec in ("fp32_mixed", "fp64"):
+    for prec, batch_md in (("fp32_mixed", True), ("fp32_mixed", False), ("fp64", True)):
         reqs = [request_from_box(r["rid"], r["kind"], r["box"], r["mesh"], V=r["V"],
                                  steps=r["steps"], arrival=r["arrival"], precision=prec)
                 for r in stream]
         # warm the library, the memory pool and cuFFT on a few requests first
-        Server(max_inflight=args.serve_inflight).serve(reqs[:8], realtime=False)
-        res, stats = Server(max_inflight=args.serve_inflight).serve(reqs, realtime=True)
-        out[prec] = stats
+        Server(max_inflight=args.serve_inflight, batch_md=batch_md).serve(reqs[:8], realtime=False)
+        res, stats = Server(max_inflight=args.serve_inflight, batch_md=batch_md).serve(reqs, realtime=True)
+        out[prec if batch_md else prec + "_unbatched"] = stats
     out["value"] = out["fp32_mixed"]["throughput_req_per_s"]
     print(json.dumps(out))
 

@@ -7,6 +7,7 @@ The compute path is ``libqeq.so`` (hand-written sm_103a CUDA behind the C ABI in
                   qeq_neighbor_build, qeq_coulomb_apply, qeq_shadow_step, ...)
 * ``System``   -- owns one context plus the output tensors of an apply
 * ``ShadowMD`` -- owns the caller-side state arrays of the shadow XL-BOMD step
+* ``ShadowBatch`` -- steps several ShadowMD systems at once (one sync, one graph)
 * ``autograd`` -- ``CoulombEnergy``, a torch.autograd.Function over the apply
 """
 
@@ -279,6 +280,42 @@ class ShadowMD:
         system.neighbor_build(md.R)
         torch.cuda.synchronize(system.device)
         return md, step
+
+
+class ShadowBatch:
+    """Advances several ShadowMD systems by one step each with qeq_batch_step: one host
+    synchronisation for all skin checks and one CUDA graph for all evaluations.  The
+    members' earlier work must be ordered before `stream`."""
+
+    def __init__(self):
+        self.h = _lib.qeq_batch_create()
+        self._key = None
+        self._arrays = None
+
+    def step(self, mds, stream=None):
+        if not mds:
+            return
+        key = tuple(id(md) for md in mds)
+        if key != self._key:  # the argument arrays change only with the member list
+            self._arrays = _lib.batch_arrays([md.sys.ctx for md in mds], [md._prm for md in mds],
+                                             [md._st for md in mds])
+            self._key = key
+        _lib.qeq_batch_step_arrays(self.h, self._arrays, stream)
+
+    def stats(self):
+        """(parent graphs built, graph launches)."""
+        return _lib.qeq_batch_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qeq_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class BOMD:

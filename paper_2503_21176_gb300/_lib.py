@@ -175,6 +175,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.qeq_profile_phase_name.restype = ctypes.c_char_p
     L.qeq_get_counters.argtypes = [P, P]
     L.qeq_graph_stats.argtypes = [P, P]
+    L.qeq_batch_create.argtypes = [ctypes.POINTER(P)]
+    L.qeq_batch_create.restype = ctypes.c_int
+    L.qeq_batch_destroy.argtypes = [P]
+    L.qeq_batch_destroy.restype = None
+    L.qeq_batch_step.argtypes = [P, ctypes.c_int32, P, P, P, P]
+    L.qeq_batch_step.restype = ctypes.c_int
+    L.qeq_batch_stats.argtypes = [P, P]
+    L.qeq_batch_stats.restype = ctypes.c_int
     L.qeq_params_from_tolerance.argtypes = [ctypes.POINTER(qeq_params), ctypes.c_double]
     L.qeq_params_from_tolerance.restype = ctypes.c_int
     L.qeq_set_neighbor_method.argtypes = [P, ctypes.c_int]
@@ -524,6 +532,55 @@ def qeq_neighbor_export_coo(ctx, capacity=None, stream=None):
                                                _stream(stream)))
     m = int(npairs.value)
     return pi[:m], pj[:m], code[:m]
+
+
+def qeq_batch_create():
+    h = ctypes.c_void_p()
+    _check(None, load().qeq_batch_create(ctypes.byref(h)))
+    return h
+
+
+def qeq_batch_destroy(h) -> None:
+    if h:
+        load().qeq_batch_destroy(h)
+
+
+def batch_arrays(ctxs, prms, sts):
+    """The C argument arrays of qeq_batch_step for one member list."""
+    n = len(ctxs)
+    if not (n == len(prms) == len(sts)):
+        raise ValueError("ctxs, prms and sts must have the same length")
+    c_arr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    p_arr = (qeq_md_params * n)(*prms)
+    s_arr = (qeq_md_state * n)(*sts)
+    return (n, c_arr, p_arr, s_arr, [ctypes.cast(a, ctypes.c_void_p) for a in (c_arr, p_arr, s_arr)])
+
+
+def qeq_batch_step_arrays(h, arrays, stream=None) -> None:
+    """qeq_batch_step with arrays from batch_arrays.  On failure the error message is the
+    failing member's, else the library's."""
+    n, c_arr, _, _, ptrs = arrays
+    rc = load().qeq_batch_step(h, n, ptrs[0], ptrs[1], ptrs[2], _stream(stream))
+    if rc != QEQ_OK:
+        for c in c_arr:
+            msg = load().qeq_last_error(c)
+            if msg:
+                raise QeqError(rc, msg.decode())
+        _check(None, rc)
+
+
+def qeq_batch_step(h, ctxs, prms, sts, stream=None) -> None:
+    """One batched shadow step of the member contexts (see include/qeq.h)."""
+    qeq_batch_step_arrays(h, batch_arrays(ctxs, prms, sts), stream)
+
+
+def qeq_batch_stats(h):
+    """(parent graphs built, graph launches) of a batch."""
+    import numpy as np
+
+    out = np.zeros(2, dtype=np.int64)
+    _check(None, load().qeq_batch_stats(h, out.ctypes.data_as(ctypes.c_void_p)))
+    return tuple(int(x) for x in out)
 
 
 def qeq_params_from_tolerance(params: qeq_params, delta: float) -> qeq_params:

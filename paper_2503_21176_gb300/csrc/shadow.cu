@@ -569,6 +569,17 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     return cuda_check(ctx, cudaGetLastError(), "shadow evaluate launch");
 }
 
+int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
+    const int n = (int)ctx->n;
+    prof_begin(ctx, kPhIntegrate, s);
+    k_advance<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
+                                              dissipation(ctx->p.dissipation_k), prm->mass, st->F,
+                                              st->Kf, st->R, st->V, st->n_hist, ctx->inv_m);
+    prof_end(ctx, s);
+    ctx->launches++;
+    return nl_displacement(ctx, st->R, s, nullptr);
+}
+
 int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);

@@ -14,6 +14,16 @@ list, mesh and n history resident on the device.  Then it copies the results
 back and retires its context on its own stream.  Latency is arrival to
 completion.  The loop reports p50 / p99 beside throughput.
 
+MD steps are batched across requests (batch_md, the default).  After its
+initial evaluation an MD request joins a stepper thread, which advances every
+member in lockstep with qeq_batch_step on its own stream: per step, one host
+synchronisation covers all members' skin checks and one CUDA graph launch runs
+all their evaluations as parallel branches (the graph is rebuilt only when the
+members change).  A request joins at the next step once its initial evaluation
+is done (a CUDA event orders it before the stepper's stream) and leaves when
+its steps are done (an event orders its download after them).  A failing
+batch step fails the requests stepped in it.
+
 Isolation: the work of a request touches only its own context and tensors,
 so its result does not depend on what runs beside it.  The only exception is
 the order of floating-point atomics in the PME spread.
@@ -30,7 +40,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import ShadowMD, System, make_params
+from . import ShadowBatch, ShadowMD, System, make_params
 
 
 @dataclass
@@ -96,9 +106,90 @@ def estimate_device_bytes(req: Request) -> int:
     return int(1.25 * total) + (4 << 20)
 
 
+class _Member:
+    """An MD request inside the batch stepper."""
+
+    def __init__(self, md, steps, ready):
+        self.md = md
+        self.remaining = int(steps)
+        self.ready = ready            # CUDA event: the request's set-up is done
+        self.done_event = None        # CUDA event on the stepper's stream after its last step
+        self.finished = threading.Event()
+        self.error = None
+
+
+class _BatchStepper:
+    """Advances every MD request in flight by one step per tick with qeq_batch_step."""
+
+    def __init__(self, device):
+        self.device = device
+        self.stream = torch.cuda.Stream(device)
+        self.batch = ShadowBatch()
+        self.cv = threading.Condition()
+        self.joining = []
+        self.members = []
+        self.stop = False
+        self.ticks = 0
+        self.member_steps = 0
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def submit(self, md, steps, ready) -> _Member:
+        m = _Member(md, steps, ready)
+        with self.cv:
+            self.joining.append(m)
+            self.cv.notify()
+        return m
+
+    def _run(self):
+        with torch.cuda.device(self.device):
+            while True:
+                with self.cv:
+                    while not (self.stop or self.joining or self.members):
+                        self.cv.wait()
+                    if self.stop and not self.joining and not self.members:
+                        return
+                    new, self.joining = self.joining, []
+                for m in new:
+                    self.stream.wait_event(m.ready)
+                self.members.extend(new)
+                try:
+                    self.batch.step([m.md for m in self.members], self.stream)
+                    self.ticks += 1
+                    self.member_steps += len(self.members)
+                except Exception as exc:  # every request of this step fails with it
+                    for m in self.members:
+                        m.error = f"{type(exc).__name__}: {exc}"
+                        m.remaining = 0
+                keep = []
+                for m in self.members:
+                    m.remaining -= 1
+                    if m.remaining <= 0:
+                        ev = torch.cuda.Event()
+                        ev.record(self.stream)
+                        m.done_event = ev
+                        m.finished.set()
+                    else:
+                        keep.append(m)
+                self.members = keep
+
+    def close_thread(self):
+        """Stop the thread once its members are done; the batch stays open for its stats."""
+        with self.cv:
+            self.stop = True
+            self.cv.notify()
+        self.thread.join()
+        torch.cuda.synchronize(self.device)
+
+
 class Server:
-    def __init__(self, device=0, max_inflight=8, hbm_budget=None, headroom=2 << 30):
+    batch_md = False  # set by __init__ (default on); subclasses with their own executor keep it off
+    _stepper = None
+
+    def __init__(self, device=0, max_inflight=8, hbm_budget=None, headroom=2 << 30, batch_md=True):
         self.device = torch.device("cuda", device)
+        self.batch_md = bool(batch_md)
+        self._stepper = None
         self.max_inflight = int(max_inflight)
         with torch.cuda.device(self.device):
             free, _ = torch.cuda.mem_get_info(self.device)
@@ -135,7 +226,16 @@ class Server:
                 md.init(stream)
                 marks.append(("init", time.perf_counter()))
                 if req.kind == "md" and req.steps > 0:
-                    md.step(req.steps, stream)
+                    if self._stepper is not None:
+                        ready = torch.cuda.Event()
+                        ready.record(stream)
+                        member = self._stepper.submit(md, req.steps, ready)
+                        member.finished.wait()
+                        if member.error:
+                            raise RuntimeError(member.error)
+                        stream.wait_event(member.done_event)
+                    else:
+                        md.step(req.steps, stream)
                     marks.append(("steps", time.perf_counter()))
                 out = [t.to("cpu", non_blocking=True) for t in (md.q, md.F, md.R, md.energies)]
                 stream.synchronize()
@@ -164,6 +264,8 @@ class Server:
         results = {}
         max_conc = 0
         pool = cf.ThreadPoolExecutor(max_workers=self.max_inflight)
+        if self.batch_md:
+            self._stepper = _BatchStepper(self.device)
         t0 = time.perf_counter()
         try:
             while pending or ready or inflight:
@@ -199,6 +301,14 @@ class Server:
                                                   error=f"{type(exc).__name__}: {exc}")
         finally:
             pool.shutdown(wait=True)
+            stepper, self._stepper = self._stepper, None
+            batching = None
+            if stepper is not None:
+                stepper.close_thread()
+                batching = {"batch_steps": stepper.ticks, "member_steps": stepper.member_steps,
+                            "mean_members_per_step": round(stepper.member_steps / max(1, stepper.ticks), 3),
+                            "parent_graphs_built": stepper.batch.stats()[0]}
+                stepper.batch.close()
         t_end = time.perf_counter()
         res = [results[r] for r in sorted(results)]
         ok = [r for r in res if r.error is None]
@@ -219,6 +329,7 @@ class Server:
             "stage_ms_mean": {k: mean([r.phases_ms.get(k, 0.0) for r in ok])
                               for k in ("upload", "create", "neighbor_build", "init", "steps",
                                         "download", "close")},
+            "md_batching": batching,
         }
         return res, stats
 

@@ -38,6 +38,10 @@ def test_results_alone_equal_results_in_mix(precision, tol):
     reqs = _requests(precision)
     mixed, stats = Server(max_inflight=4).serve(reqs, realtime=True)
     assert stats["requests"] == len(reqs) and stats["max_concurrent"] >= 2
+    # the MD requests were stepped by batched steps (one graph for the members of a step)
+    mb = stats["md_batching"]
+    assert mb["member_steps"] == sum(r.steps for r in reqs if r.kind == "md")
+    assert mb["batch_steps"] <= mb["member_steps"] and mb["parent_graphs_built"] >= 1
     alone = [Server(max_inflight=1).serve([r], realtime=False)[0][0] for r in reqs]
     for a, m in zip(alone, mixed):
         assert a.rid == m.rid
@@ -59,3 +63,17 @@ def test_admission_by_memory_budget():
     assert stats["max_concurrent"] >= 1
     with pytest.raises(MemoryError):
         Server(max_inflight=2, hbm_budget=1024).serve(reqs[:1])
+
+
+def test_batched_and_unbatched_md_agree():
+    """The same stream with MD steps batched across requests and stepped one request at
+    a time gives the same results (FP64: to the spread's atomic order)."""
+    cuda_or_skip()
+    from paper_2503_21176_gb300.serve import Server
+
+    reqs = _requests("fp64")
+    a, _ = Server(max_inflight=4, batch_md=True).serve(reqs, realtime=False)
+    b, sb = Server(max_inflight=4, batch_md=False).serve(reqs, realtime=False)
+    assert sb["md_batching"] is None
+    for x, y in zip(a, b):
+        assert rel_max(x.R, y.R) < 1e-10 and rel_max(x.q, y.q) < 1e-10
