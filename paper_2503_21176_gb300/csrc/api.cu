@@ -162,6 +162,13 @@ int create(const qeq_params *p, cudaStream_t stream, bool async_alloc, qeq_ctx *
     ctx->n = p->n_atoms;
     ctx->fp32 = p->precision == QEQ_FP32_MIXED;
     cudaGetDevice(&ctx->device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess &&
+        sms > 0) {
+        ctx->sm_count = sms;
+        ctx->red_grid = std::min(kRedBlocks, kRedPerSm * sms);
+    }
+    cudaGetLastError();
     rc = nl_configure(ctx);
     if (!rc) rc = nl_alloc(ctx);
     if (!rc) rc = coulomb_alloc(ctx);

@@ -1067,7 +1067,21 @@ struct GatherArgs {
     double sx, sy, sz;  // K / L per axis
     double self_coef;   // k_e * (-2 alpha / sqrt(pi))
     double gauss_coef;  // k_e * sqrt(2 / pi) when the Gaussian self-energy is on, else 0
+    float sx_f, sy_f, sz_f, self_coef_f, gauss_coef_f;  // FP32 copies (FP32-mixed epilogue)
 };
+
+// float -> double by rebuilding the IEEE-754 fields on the integer pipe: exact
+// for normal numbers (exponent rebiased from 127 to 1023, mantissa shifted by
+// 29 bits), zero for zero and subnormals, infinities and NaNs kept.  A
+// conversion instruction would run on GB300's 1/64-rate FP64 pipe.
+__device__ __forceinline__ double f32_to_f64_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long ed = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+    const unsigned long long bits = sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double(e == 0 ? sign : bits);
+}
 
 // ENERGY: accumulate the energy partial sums (only when the caller asked for
 // the energy parts).  The Gaussian self term k_e sqrt(2/pi) q / sigma takes 1 /
@@ -1120,6 +1134,35 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
             }
         }
         const int atom = perm[i];
+        if constexpr (std::is_same<T, float>::value && !ENERGY) {
+            // FP32-mixed MD-step epilogue, all in FP32: the real-space sums, the
+            // mesh part, the self terms and F = q E (with the sorted FP32 charge),
+            // each result widened to double on the integer pipe for the store
+            const float qf = f.w;
+            float scf = a.self_coef_f;
+            if (a.gauss_coef_f != 0.f) scf = fmaf(a.gauss_coef_f, __frcp_rn(sg_sorted[i]), scf);
+            if (FIELD) {
+                const float4 r4 = vE32[i];
+                v_out[atom] = f32_to_f64_bits(fmaf(scf, qf, r4.x + vr));
+                const float ex = fmaf(-a.sx_f, gx, r4.y);
+                const float ey = fmaf(-a.sy_f, gy, r4.z);
+                const float ez = fmaf(-a.sz_f, gz, r4.w);
+                if (E_out) {
+                    E_out[3 * (size_t)atom] = f32_to_f64_bits(ex);
+                    E_out[3 * (size_t)atom + 1] = f32_to_f64_bits(ey);
+                    E_out[3 * (size_t)atom + 2] = f32_to_f64_bits(ez);
+                }
+                if (F_out) {
+                    F_out[3 * (size_t)atom] = f32_to_f64_bits(qf * ex);
+                    F_out[3 * (size_t)atom + 1] = f32_to_f64_bits(qf * ey);
+                    F_out[3 * (size_t)atom + 2] = f32_to_f64_bits(qf * ez);
+                }
+            } else {
+                const float vsr = reinterpret_cast<const float *>(vE32)[4 * (size_t)i];
+                v_out[atom] = f32_to_f64_bits(fmaf(scf, qf, vsr + vr));
+            }
+            continue;
+        }
         const double qa = q[atom];
         double sc = a.self_coef;
         if (a.gauss_coef != 0.0) {
@@ -1182,10 +1225,11 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
     }
 }
 
-__global__ void k_finalize(const double *__restrict__ part, double *__restrict__ out) {
+// One block per slot: the sum of the slot's nb block partials, in a fixed order.
+__global__ void k_finalize(const double *__restrict__ part, int nb, double *__restrict__ out) {
     double s = 0.0;
     const double *p = part + (size_t)blockIdx.x * kRedBlocks;
-    for (int k = threadIdx.x; k < kRedBlocks; k += blockDim.x) s += p[k];
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) s += p[k];
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) out[blockIdx.x] = vals[0];
@@ -1550,7 +1594,7 @@ void launch_gather(qeq_ctx *ctx, const GatherArgs &ga, const int4 *sb, const voi
                    bool energy, cudaStream_t s) {
     const T *sgs = std::is_same<T, float>::value ? (const T *)ctx->sg32 : (const T *)ctx->sg64;
     if (energy)
-        k_gather_out<T, P, FIELD, true><<<kRedBlocks, kThreads, 0, s>>>(
+        k_gather_out<T, P, FIELD, true><<<ctx->red_grid, kThreads, 0, s>>>(
             ga, ctx->perm, sb, (const typename V4<T>::type *)sf, (const T *)ctx->mesh, ctx->v_s,
             ctx->E_s, q, sigma, sgs, v, E, F, ctx->part);
     else  // no partials: one thread per atom, every atom in flight at once
@@ -1642,8 +1686,8 @@ int pme_mesh_potential(qeq_ctx *ctx, double *energy4, cudaStream_t sp) {
     {
         const int K2h = ctx->K[2] / 2 + 1;
         if (energy4)
-            k_influence<T, true><<<kRedBlocks, kThreads, 0, sp>>>(
-                (int)ctx->meshc_n, K2h, ctx->K[2], (kRedBlocks * kThreads) % K2h,
+            k_influence<T, true><<<ctx->red_grid, kThreads, 0, sp>>>(
+                (int)ctx->meshc_n, K2h, ctx->K[2], (ctx->red_grid * kThreads) % K2h,
                 (typename C2<T>::type *)ctx->meshc, (const T *)ctx->G, ctx->part + 2 * kRedBlocks);
         else if (f64)
             k_influence_mul64<<<grid_for(ctx->meshc_n), kThreads, 0, sp>>>(
@@ -1774,7 +1818,7 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
         int rc = ewald_recip_and_combine(ctx, q, sigma, v, E, F, need_field, s);
         if (rc) return rc;
         if (energy4) {
-            k_finalize<<<4, kThreads, 0, s>>>(ctx->part, energy4);
+            k_finalize<<<4, kThreads, 0, s>>>(ctx->part, ctx->red_grid, energy4);
             ctx->launches++;
         }
         return cuda_check(ctx, cudaGetLastError(), "coulomb apply launch");
@@ -1788,6 +1832,11 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     ga.sz = ctx->K[2] / p.box[2];
     ga.self_coef = p.k_e * (-kTwoOverSqrtPi * p.alpha);
     ga.gauss_coef = p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0;
+    ga.sx_f = (float)ga.sx;
+    ga.sy_f = (float)ga.sy;
+    ga.sz_f = (float)ga.sz;
+    ga.self_coef_f = (float)ga.self_coef;
+    ga.gauss_coef_f = (float)ga.gauss_coef;
     prof_begin(ctx, kPhGatherOut, s);
     const bool energy = energy4 != nullptr;
     if (need_field)
@@ -1798,7 +1847,7 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
     prof_end(ctx, s);
     ctx->launches++;
     if (energy4) {
-        k_finalize<<<4, kThreads, 0, s>>>(ctx->part, energy4);
+        k_finalize<<<4, kThreads, 0, s>>>(ctx->part, ctx->red_grid, energy4);
         ctx->launches++;
     }
     return cuda_check(ctx, cudaGetLastError(), "coulomb apply launch");
@@ -1806,8 +1855,8 @@ int apply_t(qeq_ctx *ctx, const double *R, const double *q, const double *sigma,
 
 }  // namespace
 
-void launch_finalize(const double *part, int nslots, double *out, cudaStream_t s) {
-    k_finalize<<<nslots, kThreads, 0, s>>>(part, out);
+void launch_finalize(const qeq_ctx *ctx, const double *part, int nslots, double *out, cudaStream_t s) {
+    k_finalize<<<nslots, kThreads, 0, s>>>(part, ctx->red_grid, out);
 }
 
 // Process-wide pool of mesh side streams (high-priority, non-blocking) and

@@ -215,7 +215,7 @@ int ewald_recip_and_combine(qeq_ctx *ctx, const double *q, const double *sigma, 
         dim3 grid((nk + kThreads - 1) / kThreads, ctx->ewald_nchunk);
         k_sfac_partial<<<grid, kThreads, 0, s>>>(n, nk, (const double4_32a *)ctx->ewald_k, ctx->xq64,
                                                  (double2 *)ctx->ewald_partial);
-        k_sfac_reduce<<<kRedBlocks, kThreads, 0, s>>>(nk, ctx->ewald_nchunk,
+        k_sfac_reduce<<<ctx->red_grid, kThreads, 0, s>>>(nk, ctx->ewald_nchunk,
                                                       (const double4_32a *)ctx->ewald_k,
                                                       (const double2 *)ctx->ewald_partial,
                                                       (double2 *)ctx->ewald_S, ctx->part + 2 * kRedBlocks);
@@ -230,12 +230,12 @@ int ewald_recip_and_combine(qeq_ctx *ctx, const double *q, const double *sigma, 
     a.gauss_coef = p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0;
     prof_begin(ctx, kPhGatherOut, s);
     if (need_field)
-        k_ewald_out<true><<<kRedBlocks, kThreads, 0, s>>>(a, ctx->perm, ctx->xq64,
+        k_ewald_out<true><<<ctx->red_grid, kThreads, 0, s>>>(a, ctx->perm, ctx->xq64,
                                                           (const double4_32a *)ctx->ewald_k,
                                                           (const double2 *)ctx->ewald_S, ctx->v_s,
                                                           ctx->E_s, q, sigma, v, E, F, ctx->part);
     else
-        k_ewald_out<false><<<kRedBlocks, kThreads, 0, s>>>(a, ctx->perm, ctx->xq64,
+        k_ewald_out<false><<<ctx->red_grid, kThreads, 0, s>>>(a, ctx->perm, ctx->xq64,
                                                            (const double4_32a *)ctx->ewald_k,
                                                            (const double2 *)ctx->ewald_S, ctx->v_s,
                                                            ctx->E_s, q, sigma, v, nullptr, nullptr,

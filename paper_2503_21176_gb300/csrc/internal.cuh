@@ -23,14 +23,17 @@
 namespace qeq {
 
 constexpr int kThreads = 256;
-// Fixed reduction grid: QEQ_RED_BLOCKS blocks (a multiple of the 152 SMs of a
-// GB300).  Grid-stride kernels that reduce write one partial per block into a
-// [slot][kRedBlocks] table, and a one-block finalize sums each slot in a fixed
-// order (deterministic results).
+// Fixed reduction grid: grid-stride kernels that reduce run on the context's
+// red_grid blocks (kRedPerSm x the device's SM count from
+// cudaDevAttrMultiProcessorCount, read at creation: 304 on a 152-SM GB300) and
+// write one partial per block into a [slot][kRedBlocks] table; a finalize sums
+// each slot's red_grid partials in a fixed order, so results are deterministic
+// on a given device.  kRedBlocks is the table's stride and the largest grid.
 #ifndef QEQ_RED_BLOCKS
-#define QEQ_RED_BLOCKS 304
+#define QEQ_RED_BLOCKS 1024
 #endif
 constexpr int kRedBlocks = QEQ_RED_BLOCKS;
+constexpr int kRedPerSm = 2;
 constexpr int kMaxRank = 8;
 // Reduction slots: the largest user is the GMRES multi-dot (restart <= 64
 // vectors plus the norm); the Krylov normal equations need
@@ -386,6 +389,8 @@ struct qeq_ctx {
     int graph_width = 0;
     int graph_tile = 0, graph_rows = 0;  // launch geometry of the real-space kernel at capture
     int64_t graph_launches = 0;      // this library's kernels inside the graph
+    int red_grid = 2 * 152;          // blocks of the reduction grid (set at creation)
+    int sm_count = 152;              // SMs of the device (set at creation)
     uint64_t graph_gen = 0;          // process-wide generation of the current step graph
     int64_t graph_captures = 0;      // step graphs captured since creation
     int64_t graph_replays = 0;       // step graph launches since creation
@@ -454,7 +459,7 @@ int ewald_recip_and_combine(qeq_ctx *ctx, const double *q, const double *sigma, 
 
 // ---- reductions (coulomb.cu) ----
 // Sum nslots partial tables of kRedBlocks entries each, starting at part, into out[0..nslots).
-void launch_finalize(const double *part, int nslots, double *out, cudaStream_t s);
+void launch_finalize(const qeq_ctx *ctx, const double *part, int nslots, double *out, cudaStream_t s);
 
 // ---- shadow step (shadow.cu) ----
 int shadow_alloc(qeq_ctx *ctx);

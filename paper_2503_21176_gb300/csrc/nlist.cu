@@ -174,6 +174,7 @@ constexpr int kCellDiv = 2;
 #define QEQ_NL_UNROLL 1
 #endif
 constexpr int kEmitThreads = 128;
+constexpr int kEmitBlocksPerSm = 4;
 
 // s L for an image index s in [-2, 2]: exact in FP64 (a multiple of L by 0, 1 or
 // 2), selected without an FP64 multiply.
@@ -290,23 +291,29 @@ __device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, con
 // records the largest tile and brick for the real-space launch, and writes no
 // entry when the tile exceeds 16-bit indices.
 __global__ void __launch_bounds__(kEmitThreads)
-k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const float4 *__restrict__ xs32,
-       const int32_t *__restrict__ cell_s, const int32_t *__restrict__ cell_start,
-       uint16_t *__restrict__ nbr, uint32_t *__restrict__ scr, int32_t *__restrict__ cnt,
-       int4 *__restrict__ tile_tab, int32_t *__restrict__ tile_tot, int32_t *__restrict__ flags) {
+k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64,
+       const float4 *__restrict__ xs32, const int32_t *__restrict__ cell_s,
+       const int32_t *__restrict__ cell_start, uint16_t *__restrict__ nbr, uint32_t *__restrict__ scr,
+       int32_t *__restrict__ cnt, int4 *__restrict__ tile_tab, int32_t *__restrict__ tile_tot,
+       int32_t *__restrict__ flags) {
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
-    const int64_t b = blockIdx.x;
+    // nchunk blocks share a brick: chunk c takes the brick's groups of 32 rows
+    // c, c + nchunk, ... (more blocks in flight for boxes of few bricks)
+    const int64_t b = blockIdx.x / nchunk;
+    const int chunk = (int)(blockIdx.x - b * nchunk);
     if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, t_code, &t_total);
     __syncthreads();
-    // the tile table of the brick, for the real-space kernels of this list
-    for (int rb = threadIdx.x; rb < g.T; rb += blockDim.x)
-        tile_tab[b * g.T + rb] = make_int4(t_start[rb], t_base[rb], t_code[rb], 0);
-    if (threadIdx.x == 0) tile_tot[b] = t_total;
     const int i0 = t_start[g.center], i1 = cell_start[(b + 1) * g.bvol];
-    if (threadIdx.x == 0) {
-        atomicMax(&flags[kFlagMaxTile], t_total);
-        atomicMax(&flags[kFlagMaxRows], i1 - i0);
+    if (chunk == 0) {
+        // the tile table of the brick, for the real-space kernels of this list
+        for (int rb = threadIdx.x; rb < g.T; rb += blockDim.x)
+            tile_tab[b * g.T + rb] = make_int4(t_start[rb], t_base[rb], t_code[rb], 0);
+        if (threadIdx.x == 0) {
+            tile_tot[b] = t_total;
+            atomicMax(&flags[kFlagMaxTile], t_total);
+            atomicMax(&flags[kFlagMaxRows], i1 - i0);
+        }
     }
     const int dx = 2 * a.rx + 1, dy = 2 * a.ry + 1, dz = 2 * a.rz + 1;
     const int ncand = dx * dy * dz;
@@ -330,7 +337,8 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
     }
     __syncthreads();
     if (t_total > kMaxTileAtoms) {
-        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) cnt[i] = 0;
+        if (chunk == 0)
+            for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) cnt[i] = 0;
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -338,7 +346,8 @@ k_emit(EmitArgs a, BrickGeom g, const double4_32a *__restrict__ xs64, const floa
     const int nrows = i1 - i0;
     const int rows_per_warp = 32 / kEmitLanes;
     const int cap = a.width / kEmitLanes;
-    for (int r0 = warp * rows_per_warp; r0 < nrows; r0 += nw * rows_per_warp) {
+    for (int r0 = (chunk * nw + warp) * rows_per_warp; r0 < nrows;
+         r0 += nchunk * nw * rows_per_warp) {
         const int r = r0 + lane / kEmitLanes;
         const bool act = r < nrows;
         const int i = i0 + (act ? r : 0);
@@ -728,8 +737,17 @@ static int launch_emit(qeq_ctx *ctx, cudaStream_t s) {
             ctx->tile_tot, ctx->nbr, ctx->cnt, ctx->d_flags);
         return 2;
     }
-    k_emit<<<(unsigned)ctx->geom.nbricks, kEmitThreads, 0, s>>>(
-        a, ctx->geom, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr,
+    // blocks per brick: enough to put about kEmitBlocksPerSm blocks on every SM
+    // when the box has few bricks, at most one per 32 rows of the largest brick
+    // (from the previous build; 1.5 x the mean before the first)
+    const int64_t nb = ctx->geom.nbricks;
+    const int rows = ctx->max_rows > 0 ? ctx->max_rows
+                                       : (int)std::ceil(1.5 * (double)ctx->n / (double)nb);
+    const int64_t want = (int64_t)kEmitBlocksPerSm * ctx->sm_count;
+    const int nchunk = (int)std::max<int64_t>(
+        1, std::min<int64_t>((want + nb - 1) / nb, (rows + 31) / 32));
+    k_emit<<<(unsigned)(nb * nchunk), kEmitThreads, 0, s>>>(
+        a, ctx->geom, nchunk, ctx->xs64, ctx->xs32, ctx->cell_s, ctx->cell_start, ctx->nbr,
         ctx->nbr_scratch, ctx->cnt, ctx->tile_tab, ctx->tile_tot, ctx->d_flags);
     return 1;
 }
@@ -803,7 +821,7 @@ int nl_build(qeq_ctx *ctx, const double *R, cudaStream_t s) {
 
 int nl_displacement(qeq_ctx *ctx, const double *R, cudaStream_t s, double *max_disp2) {
     prof_begin(ctx, kPhIntegrate, s);
-    k_max_disp2<<<kRedBlocks, kThreads, 0, s>>>((int)ctx->n, R, ctx->R_build, ctx->part,
+    k_max_disp2<<<ctx->red_grid, kThreads, 0, s>>>((int)ctx->n, R, ctx->R_build, ctx->part,
                                                 ctx->scal + kScMaxDisp2, ctx->ticket);
     prof_end(ctx, s);
     ctx->launches += 1;

@@ -204,17 +204,17 @@ __global__ void k_normal_part(int n, const double *__restrict__ Rb, const double
         for (int k = 0; k < nO + M; ++k) part[k * kRedBlocks + blockIdx.x] = acc[k];
 }
 
-void launch_normal_part(int m, int n, const double *Rb, const double *f, double *part,
+void launch_normal_part(int grid, int m, int n, const double *Rb, const double *f, double *part,
                         cudaStream_t s) {
     switch (m) {
-        case 1: k_normal_part<1><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 2: k_normal_part<2><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 3: k_normal_part<3><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 4: k_normal_part<4><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 5: k_normal_part<5><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 6: k_normal_part<6><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 7: k_normal_part<7><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
-        default: k_normal_part<8><<<kRedBlocks, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 1: k_normal_part<1><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 2: k_normal_part<2><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 3: k_normal_part<3><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 4: k_normal_part<4><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 5: k_normal_part<5><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 6: k_normal_part<6><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        case 7: k_normal_part<7><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
+        default: k_normal_part<8><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
     }
 }
 
@@ -223,7 +223,7 @@ void launch_normal_part(int m, int n, const double *Rb, const double *f, double 
 // directions, e.g. f = 0, get c = 0), and write the evaluation's energies:
 // 1 shadow potential, 3 short range, 4 lambda, 5 sum q, 6 |f|, 7 applies.
 __global__ void k_normal_solve(int m, double q_tot, int applies, const double *__restrict__ part,
-                               double *__restrict__ scal, double *__restrict__ energies) {
+                               int nb, double *__restrict__ scal, double *__restrict__ energies) {
     __shared__ double sums[kMaxRank * (kMaxRank + 1) / 2 + kMaxRank];
     const int nO = m * (m + 1) / 2;
     // one warp per slot, lanes over the block partials in a fixed order
@@ -231,7 +231,7 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
     for (int k = warp; k < nO + m; k += nw) {
         double acc = 0.0;
         const double *p = part + (size_t)k * kRedBlocks;
-        for (int b = lane; b < kRedBlocks; b += 32) acc += p[b];
+        for (int b = lane; b < nb; b += 32) acc += p[b];
         acc = warp_sum(acc);
         if (lane == 0) sums[k] = acc;
     }
@@ -453,7 +453,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     double *nn = st->n_hist;  // n(t) is history slot 0
     double *part = ctx->part;
     double *scal = ctx->scal;
-    const int G = kRedBlocks;
+    const int G = ctx->red_grid;
     unsigned int *tk = ctx->ticket;
     auto fin = [&]() { ctx->launches += 1; };  // a reducing kernel (its last block finalizes)
 
@@ -499,8 +499,9 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     auto solve_rank = [&](int k, bool *done) -> int {
         const int nO = k * (k + 1) / 2;
         prof_begin(ctx, kPhShadow, s);
-        launch_normal_part(k, n, ctx->Rb, ctx->fvec, part, s);
-        k_normal_solve<<<1, kThreads, 0, s>>>(k, ctx->p.q_tot, k + 1, part, scal, st->energies);
+        launch_normal_part(ctx->red_grid, k, n, ctx->Rb, ctx->fvec, part, s);
+        k_normal_solve<<<1, kThreads, 0, s>>>(k, ctx->p.q_tot, k + 1, part, ctx->red_grid, scal,
+                                              st->energies);
         ctx->launches += 2;
         prof_end(ctx, s);
         (void)nO;
@@ -572,7 +573,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
 int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_advance<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
+    k_advance<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
                                               dissipation(ctx->p.dissipation_k), prm->mass, st->F,
                                               st->Kf, st->R, st->V, st->n_hist, ctx->inv_m);
     prof_end(ctx, s);
@@ -583,7 +584,7 @@ int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *s
 int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_advance<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
+    k_advance<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
                                               dissipation(ctx->p.dissipation_k), prm->mass, st->F,
                                               st->Kf, st->R, st->V, st->n_hist, ctx->inv_m);
     prof_end(ctx, s);
@@ -603,7 +604,7 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
                   cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_finish<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
+    k_finish<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
                                              ctx->inv_m, st->F, st->V, ctx->part, ctx->scal,
                                              st->energies, ctx->ticket);
     prof_end(ctx, s);

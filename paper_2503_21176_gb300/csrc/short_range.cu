@@ -134,12 +134,12 @@ int short_range_forces(qeq_ctx *ctx, const double *R, const double *, double *F_
                        double *e_slot, cudaStream_t s) {
     const int n = (int)ctx->n;
     const qeq_params &p = ctx->p;
-    k_water_intra<<<kRedBlocks, kThreads, 0, s>>>(n / 3, R, p.box[0], p.box[1], p.box[2], F_short,
+    k_water_intra<<<ctx->red_grid, kThreads, 0, s>>>(n / 3, R, p.box[0], p.box[1], p.box[2], F_short,
                                                   ctx->part);
-    k_water_lj<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->geom, ctx->cell_start, ctx->perm, ctx->nbr,
+    k_water_lj<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->geom, ctx->cell_start, ctx->perm, ctx->nbr,
                                                ctx->cnt, R, ctx->wrap_off, p.box[0], p.box[1],
                                                p.box[2], p.r_cut * p.r_cut, F_short, ctx->part);
-    launch_finalize(ctx->part, 2, e_slot, s);
+    launch_finalize(ctx, ctx->part, 2, e_slot, s);
     ctx->launches += 3;
     return cuda_check(ctx, cudaGetLastError(), "short-range launch");
 }

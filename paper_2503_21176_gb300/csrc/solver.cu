@@ -200,13 +200,13 @@ int cgs2(qeq_ctx *ctx, int n1, int nv, double *w, std::vector<double> &h, double
     const int off2 = kMaxDots + 2;
     for (int pass = 0; pass < 2; ++pass) {
         double *dst = dh + (pass == 0 ? 0 : off2);
-        k_multi_dot<<<kRedBlocks, kThreads, 0, s>>>(n1, nv, ctx->gmV, w, part);
-        launch_finalize(part, nv, dst, s);
-        k_subtract<<<kRedBlocks, kThreads, 0, s>>>(n1, nv, ctx->gmV, dst, w);
+        k_multi_dot<<<ctx->red_grid, kThreads, 0, s>>>(n1, nv, ctx->gmV, w, part);
+        launch_finalize(ctx, part, nv, dst, s);
+        k_subtract<<<ctx->red_grid, kThreads, 0, s>>>(n1, nv, ctx->gmV, dst, w);
         ctx->launches += 3;
     }
-    k_multi_dot<<<kRedBlocks, kThreads, 0, s>>>(n1, 0, ctx->gmV, w, part);
-    launch_finalize(part, 1, dh + 2 * off2, s);
+    k_multi_dot<<<ctx->red_grid, kThreads, 0, s>>>(n1, 0, ctx->gmV, w, part);
+    launch_finalize(ctx, part, 1, dh + 2 * off2, s);
     ctx->launches += 2;
     std::vector<double> hb(2 * off2 + 1);
     cudaError_t e = cudaMemcpyAsync(hb.data(), dh, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, s);
@@ -224,13 +224,13 @@ int precond_apply(qeq_ctx *ctx, const double *R, const double *u, const double *
                   const double *x, double *y, cudaStream_t s, bool same_R) {
     const int n = (int)ctx->n;
     double *z = ctx->gmZ;
-    k_precond<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->gmDinv, x, z);
+    k_precond<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->gmDinv, x, z);
     ctx->launches++;
     int rc = coulomb_apply_impl(ctx, R, z, sigma, ctx->phi, nullptr, nullptr, nullptr, false, s,
                                 same_R);
     if (rc) return rc;
-    k_bordered_apply<<<kRedBlocks, kThreads, 0, s>>>(n, u, ctx->phi, z, y, ctx->part);
-    launch_finalize(ctx->part, 1, ctx->gmH + 2 * (kMaxDots + 2) + 1, s);
+    k_bordered_apply<<<ctx->red_grid, kThreads, 0, s>>>(n, u, ctx->phi, z, y, ctx->part);
+    launch_finalize(ctx, ctx->part, 1, ctx->gmH + 2 * (kMaxDots + 2) + 1, s);
     k_set_last<<<1, 32, 0, s>>>(n, ctx->gmH + 2 * (kMaxDots + 2) + 1, y);
     ctx->launches += 3;
     return QEQ_OK;
@@ -243,16 +243,16 @@ int plain_apply(qeq_ctx *ctx, const double *R, const double *u, const double *si
     int rc = coulomb_apply_impl(ctx, R, x, sigma, ctx->phi, nullptr, nullptr, nullptr, false, s,
                                 same_R);
     if (rc) return rc;
-    k_bordered_apply<<<kRedBlocks, kThreads, 0, s>>>(n, u, ctx->phi, x, y, ctx->part);
-    launch_finalize(ctx->part, 1, ctx->gmH + 2 * (kMaxDots + 2) + 1, s);
+    k_bordered_apply<<<ctx->red_grid, kThreads, 0, s>>>(n, u, ctx->phi, x, y, ctx->part);
+    launch_finalize(ctx, ctx->part, 1, ctx->gmH + 2 * (kMaxDots + 2) + 1, s);
     k_set_last<<<1, 32, 0, s>>>(n, ctx->gmH + 2 * (kMaxDots + 2) + 1, y);
     ctx->launches += 3;
     return QEQ_OK;
 }
 
 double host_norm(qeq_ctx *ctx, const double *x, int n1, cudaStream_t s, int *rc) {
-    k_multi_dot<<<kRedBlocks, kThreads, 0, s>>>(n1, 0, ctx->gmV, x, ctx->part);
-    launch_finalize(ctx->part, 1, ctx->gmH, s);
+    k_multi_dot<<<ctx->red_grid, kThreads, 0, s>>>(n1, 0, ctx->gmV, x, ctx->part);
+    launch_finalize(ctx, ctx->part, 1, ctx->gmH, s);
     ctx->launches += 2;
     double v = 0.0;
     cudaError_t e = cudaMemcpyAsync(&v, ctx->gmH, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -274,14 +274,14 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
     int rc = solver_alloc(ctx, restart);
     if (rc) return rc;
     const qeq_params &p = ctx->p;
-    k_jacobi<<<kRedBlocks, kThreads, 0, s>>>(n, u, sigma, p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0,
+    k_jacobi<<<ctx->red_grid, kThreads, 0, s>>>(n, u, sigma, p.gaussian_self ? p.k_e * kSqrtTwoOverPi : 0.0,
                                              ctx->gmDinv);
     ctx->launches++;
     double *w = ctx->gmW;       // A z, then the residual / Arnoldi work vector
     double *bvec = ctx->gmW + n1;
     // |b| with b = [-chi; q_tot]  (residual of A z = 0)
     cudaMemsetAsync(w, 0, sizeof(double) * n1, s);
-    k_residual<<<kRedBlocks, kThreads, 0, s>>>(n, p.q_tot, chi, w, bvec);
+    k_residual<<<ctx->red_grid, kThreads, 0, s>>>(n, p.q_tot, chi, w, bvec);
     ctx->launches++;
     double bnorm = host_norm(ctx, bvec, n1, s, &rc);
     if (rc) return rc;
@@ -294,13 +294,13 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
         rc = plain_apply(ctx, R, u, sigma, z, w, s, applies > 0);
         if (rc) return rc;
         ++applies;
-        k_residual<<<kRedBlocks, kThreads, 0, s>>>(n, p.q_tot, chi, w, w);
+        k_residual<<<ctx->red_grid, kThreads, 0, s>>>(n, p.q_tot, chi, w, w);
         ctx->launches++;
         const double beta = host_norm(ctx, w, n1, s, &rc);
         if (rc) return rc;
         relres = beta / bnorm;
         if (relres <= tol || iters >= max_iter || !(beta > 0.0)) break;
-        k_scale<<<kRedBlocks, kThreads, 0, s>>>(n1, 1.0 / beta, w, ctx->gmV);
+        k_scale<<<ctx->red_grid, kThreads, 0, s>>>(n1, 1.0 / beta, w, ctx->gmV);
         ctx->launches++;
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
@@ -318,7 +318,7 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
             for (int k = 0; k <= j; ++k) H[(size_t)k * restart + j] = h[k];
             H[(size_t)(j + 1) * restart + j] = hn;
             if (hn > 0.0) {
-                k_scale<<<kRedBlocks, kThreads, 0, s>>>(n1, 1.0 / hn, vnext, vnext);
+                k_scale<<<ctx->red_grid, kThreads, 0, s>>>(n1, 1.0 / hn, vnext, vnext);
                 ctx->launches++;
             }
             // apply the previous rotations to column j, then a new one
@@ -354,7 +354,7 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         rc = cuda_check(ctx, e, "gmres update");
         if (rc) return rc;
-        k_update_solution<<<kRedBlocks, kThreads, 0, s>>>(n, j, ctx->gmV, ctx->gmH, ctx->gmDinv, z);
+        k_update_solution<<<ctx->red_grid, kThreads, 0, s>>>(n, j, ctx->gmV, ctx->gmH, ctx->gmDinv, z);
         ctx->launches++;
         if ((relres <= tol || iters >= max_iter) && !final_check) break;
         if (relres <= tol || iters >= max_iter) {
@@ -362,7 +362,7 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
             rc = plain_apply(ctx, R, u, sigma, z, w, s, applies > 0);
             if (rc) return rc;
             ++applies;
-            k_residual<<<kRedBlocks, kThreads, 0, s>>>(n, p.q_tot, chi, w, w);
+            k_residual<<<ctx->red_grid, kThreads, 0, s>>>(n, p.q_tot, chi, w, w);
             ctx->launches++;
             relres = host_norm(ctx, w, n1, s, &rc) / bnorm;
             if (rc) return rc;
@@ -405,7 +405,7 @@ __global__ void k_kick_drift(int n, double dt, double mass_unit, const double *_
 int bomd_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_kick_drift<<<kRedBlocks, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, prm->mass, st->F,
+    k_kick_drift<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, prm->mass, st->F,
                                                  st->R, st->V, ctx->inv_m);
     prof_end(ctx, s);
     ctx->launches++;
@@ -445,10 +445,10 @@ int bomd_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, doub
                             true, s, true);
     if (rc) return rc;
     local.applies += 1;
-    k_bo_forces<<<kRedBlocks, kThreads, 0, s>>>(
+    k_bo_forces<<<ctx->red_grid, kThreads, 0, s>>>(
         n, st->q, ctx->E_n, has_short(ctx) ? ctx->F_short : nullptr, st->F);
-    k_bo_energy_part<<<kRedBlocks, kThreads, 0, s>>>(n, st->q, prm->chi, prm->eta, ctx->v_n, ctx->part);
-    launch_finalize(ctx->part, 4, scal + 128, s);
+    k_bo_energy_part<<<ctx->red_grid, kThreads, 0, s>>>(n, st->q, prm->chi, prm->eta, ctx->v_n, ctx->part);
+    launch_finalize(ctx, ctx->part, 4, scal + 128, s);
     k_bo_energies<<<1, 1, 0, s>>>(scal + 128, scal + 126, local.lambda, local.rel_residual,
                                   (double)local.applies, st->energies);
     ctx->launches += 5;
