@@ -42,18 +42,6 @@ template <> struct C2<float> { using type = float2; };
 // gather_in: sorted copies of the inputs
 // ---------------------------------------------------------------------------
 
-// Double to float by truncation toward zero on the integer pipe (GB300 runs
-// FP64 conversions on its 1/64-rate FP64 pipe): relative error below 2^-23,
-// magnitudes below 2^-126 become zero.  Valid for |x| < 2^128.
-__device__ __forceinline__ float f64_to_f32_trunc(double x) {
-    const int hi = __double2hiint(x);
-    const unsigned lo = (unsigned)__double2loint(x);
-    const int sign = hi & (int)0x80000000;
-    const int ex = ((hi >> 20) & 0x7FF) - 1023 + 127;
-    if (ex <= 0) return __int_as_float(sign);
-    return __int_as_float(sign | (ex << 23) | ((hi & 0xFFFFF) << 3) | (int)(lo >> 29));
-}
-
 // floor(u) and the fraction u - floor(u) of u < 2^31.  For u >= 0 both come
 // from the bits of u (the fraction exact in 64-bit fixed point, then truncated
 // to float); a negative u (an atom that left the box through its lower face
@@ -1070,18 +1058,6 @@ struct GatherArgs {
     float sx_f, sy_f, sz_f, self_coef_f, gauss_coef_f;  // FP32 copies (FP32-mixed epilogue)
 };
 
-// float -> double by rebuilding the IEEE-754 fields on the integer pipe: exact
-// for normal numbers (exponent rebiased from 127 to 1023, mantissa shifted by
-// 29 bits), zero for zero and subnormals, infinities and NaNs kept.  A
-// conversion instruction would run on GB300's 1/64-rate FP64 pipe.
-__device__ __forceinline__ double f32_to_f64_bits(float x) {
-    const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xffu;
-    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-    const unsigned long long ed = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
-    const unsigned long long bits = sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double(e == 0 ? sign : bits);
-}
 
 // ENERGY: accumulate the energy partial sums (only when the caller asked for
 // the energy parts).  The Gaussian self term k_e sqrt(2/pi) q / sigma takes 1 /
@@ -1143,23 +1119,23 @@ k_gather_out(GatherArgs a, const int32_t *__restrict__ perm, const int4 *__restr
             if (a.gauss_coef_f != 0.f) scf = fmaf(a.gauss_coef_f, __frcp_rn(sg_sorted[i]), scf);
             if (FIELD) {
                 const float4 r4 = vE32[i];
-                v_out[atom] = f32_to_f64_bits(fmaf(scf, qf, r4.x + vr));
+                v_out[atom] = f32_to_f64_exact(fmaf(scf, qf, r4.x + vr));
                 const float ex = fmaf(-a.sx_f, gx, r4.y);
                 const float ey = fmaf(-a.sy_f, gy, r4.z);
                 const float ez = fmaf(-a.sz_f, gz, r4.w);
                 if (E_out) {
-                    E_out[3 * (size_t)atom] = f32_to_f64_bits(ex);
-                    E_out[3 * (size_t)atom + 1] = f32_to_f64_bits(ey);
-                    E_out[3 * (size_t)atom + 2] = f32_to_f64_bits(ez);
+                    E_out[3 * (size_t)atom] = f32_to_f64_exact(ex);
+                    E_out[3 * (size_t)atom + 1] = f32_to_f64_exact(ey);
+                    E_out[3 * (size_t)atom + 2] = f32_to_f64_exact(ez);
                 }
                 if (F_out) {
-                    F_out[3 * (size_t)atom] = f32_to_f64_bits(qf * ex);
-                    F_out[3 * (size_t)atom + 1] = f32_to_f64_bits(qf * ey);
-                    F_out[3 * (size_t)atom + 2] = f32_to_f64_bits(qf * ez);
+                    F_out[3 * (size_t)atom] = f32_to_f64_exact(qf * ex);
+                    F_out[3 * (size_t)atom + 1] = f32_to_f64_exact(qf * ey);
+                    F_out[3 * (size_t)atom + 2] = f32_to_f64_exact(qf * ez);
                 }
             } else {
                 const float vsr = reinterpret_cast<const float *>(vE32)[4 * (size_t)i];
-                v_out[atom] = f32_to_f64_bits(fmaf(scf, qf, vsr + vr));
+                v_out[atom] = f32_to_f64_exact(fmaf(scf, qf, vsr + vr));
             }
             continue;
         }

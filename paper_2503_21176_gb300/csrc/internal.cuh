@@ -32,8 +32,11 @@ constexpr int kThreads = 256;
 #ifndef QEQ_RED_BLOCKS
 #define QEQ_RED_BLOCKS 1024
 #endif
+#ifndef QEQ_RED_PER_SM
+#define QEQ_RED_PER_SM 2
+#endif
 constexpr int kRedBlocks = QEQ_RED_BLOCKS;
-constexpr int kRedPerSm = 2;
+constexpr int kRedPerSm = QEQ_RED_PER_SM;
 constexpr int kMaxRank = 8;
 // Reduction slots: the largest user is the GMRES multi-dot (restart <= 64
 // vectors plus the norm); the Krylov normal equations need
@@ -520,6 +523,30 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
         }
     }
     __syncthreads();
+}
+
+// Conversions between float and double on the integer pipe: GB300 runs the
+// conversion instructions on its 1/64-rate FP64 pipe.
+// Double to float by truncation toward zero: relative error below 2^-23,
+// magnitudes below 2^-126 become zero.  Valid for |x| < 2^128.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int sign = hi & (int)0x80000000;
+    const int ex = ((hi >> 20) & 0x7FF) - 1023 + 127;
+    if (ex <= 0) return __int_as_float(sign);
+    return __int_as_float(sign | (ex << 23) | ((hi & 0xFFFFF) << 3) | (int)(lo >> 29));
+}
+// Float to double by rebuilding the IEEE-754 fields: exact for normal numbers
+// (exponent rebiased from 127 to 1023, mantissa shifted by 29 bits), zero for
+// zero and subnormals, infinities and NaNs kept.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long ed = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+    const unsigned long long bits = sign | (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double(e == 0 ? sign : bits);
 }
 
 // Grid reduction without a second launch.  Every block has written its NV

@@ -37,14 +37,37 @@ constexpr int S_OM = 48;    // O (kMaxRank^2, row-major) then g = R^T f (kMaxRan
 constexpr int S_KE = 120;   // kinetic energy
 constexpr int S_RES = 121;  // relative least-squares residual |R c - f| / |f| of the kernel update
 constexpr int S_SHORT = 126;  // short-range energy: intramolecular, Lennard-Jones
+// Scalars derived once by the last block of the reduction that produces them
+// (an FP64 divide or square root in every thread would occupy GB300's 1/64-rate
+// FP64 pipe for each of the grid's 77,824 threads).
+constexpr int S_LAMV = 122;  // lambda = -(Q_tot + S1) / S2
+constexpr int S_INVF = 123;  // 1 / |f|  (0 for f = 0)
+constexpr int S_MUV = 124;   // mu = -sum (Phi w) / u / S2
+constexpr int S_INVN = 125;  // 1 / |x| of the last normalising dot
 
-__global__ void k_lambda_part(int n, const double *__restrict__ chi, const double *__restrict__ u,
-                              const double *__restrict__ v, double *__restrict__ inv_u,
-                              double *__restrict__ part, double *__restrict__ out,
+// 1 / x for positive normal x without an FP64 divide: an FP32 reciprocal of x
+// (truncated to float on the integer pipe) refined by two Newton-Raphson steps
+// y <- y + y (1 - x y) in FP64.  Each step squares the relative error, so the
+// seed's 2^-22 becomes about 2^-88: the result is within an ulp or so of 1 / x.
+__device__ __forceinline__ double recip_nr(double x) {
+    const float xf = f64_to_f32_trunc(x);
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
+    double y = f32_to_f64_exact(yf);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+__global__ void k_lambda_part(int n, double q_tot, const double *__restrict__ chi,
+                              const double *__restrict__ u, const double *__restrict__ v,
+                              double *__restrict__ inv_u, double *__restrict__ part,
+                              double *__restrict__ out, double *__restrict__ scal,
                               unsigned int *__restrict__ ticket) {
     double s1 = 0.0, s2 = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double iu = 1.0 / u[i];
+        const double iu = recip_nr(u[i]);
         inv_u[i] = iu;
         s1 += (chi[i] + v[i]) * iu;
         s2 += iu;
@@ -55,7 +78,8 @@ __global__ void k_lambda_part(int n, const double *__restrict__ chi, const doubl
         part[blockIdx.x] = vals[0];
         part[kRedBlocks + blockIdx.x] = vals[1];
     }
-    finalize_last_block<2>(part, out, ticket);
+    if (finalize_last_block<2>(part, out, ticket) && threadIdx.x == 0)
+        scal[S_LAMV] = -(q_tot + out[0]) / out[1];
 }
 
 __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
@@ -64,7 +88,7 @@ __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
                           const double *__restrict__ nn, const double *__restrict__ scal,
                           double *__restrict__ q, double *__restrict__ f, double *__restrict__ part,
                           double *__restrict__ out, unsigned int *__restrict__ ticket) {
-    const double lam = -(q_tot + scal[S_LAM]) / scal[S_LAM + 1];
+    const double lam = scal[S_LAMV];
     double a[6] = {0, 0, 0, 0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double qi = -(chi[i] + v[i] + lam) * inv_u[i];
@@ -81,7 +105,10 @@ __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
     block_sum<6>(a);
     if (threadIdx.x == 0)
         for (int k = 0; k < 6; ++k) part[k * kRedBlocks + blockIdx.x] = a[k];
-    finalize_last_block<6>(part, out, ticket);
+    if (finalize_last_block<6>(part, out, ticket) && threadIdx.x == 0) {
+        const double nf = sqrt(out[0]);
+        out[S_INVF - S_CHG] = nf > 0.0 ? 1.0 / nf : 0.0;
+    }
 }
 
 // F = q E[n] + n E[f] (+ F_short); w_1 = f / |f|; Phi w_1 = Phi f / |f| (in place);
@@ -93,8 +120,7 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
                             double *__restrict__ F, double *__restrict__ w1,
                             double *__restrict__ phi, double *__restrict__ part,
                             double *__restrict__ out, unsigned int *__restrict__ ticket) {
-    const double nf = sqrt(scal[S_CHG]);
-    const double inv = nf > 0.0 ? 1.0 / nf : 0.0;
+    const double inv = scal[S_INVF];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
 #pragma unroll
@@ -111,7 +137,8 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
-    finalize_last_block<1>(part, out, ticket);
+    if (finalize_last_block<1>(part, out, ticket) && threadIdx.x == 0)
+        out[S_MUV - S_MU] = -out[0] / out[S_LAM + 1 - S_MU];
 }
 
 __global__ void k_mu_part(int n, const double *__restrict__ phi, const double *__restrict__ inv_u,
@@ -123,7 +150,8 @@ __global__ void k_mu_part(int n, const double *__restrict__ phi, const double *_
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
-    finalize_last_block<1>(part, out, ticket);
+    if (finalize_last_block<1>(part, out, ticket) && threadIdx.x == 0)
+        out[S_MUV - S_MU] = -out[0] / out[S_LAM + 1 - S_MU];
 }
 
 // r = J w = -(Phi w + mu) / u - w with mu = -(sum Phi w / u) / sum 1 / u.
@@ -134,7 +162,7 @@ __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *
                            double *__restrict__ r, double *__restrict__ wnext,
                            const double *__restrict__ w0, double *__restrict__ part,
                            double *__restrict__ out, unsigned int *__restrict__ ticket) {
-    const double mu = -scal[S_MU] / scal[S_LAM + 1];
+    const double mu = scal[S_MUV];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double ri = -(phi[i] + mu) * inv_u[i] - w[i];
@@ -154,7 +182,7 @@ __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *
 
 // x -= scal[S_DOT] * y, then partial of <z, x> (z may alias x for the norm)
 __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double *__restrict__ y,
-                           double *x, const double *z, double *__restrict__ part,
+                           double *x, const double *z, bool norm, double *__restrict__ part,
                            double *__restrict__ out, unsigned int *__restrict__ ticket) {
     const double a = scal[S_DOT];
     double s = 0.0;
@@ -166,12 +194,15 @@ __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double 
     double vals[1] = {s};
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
-    finalize_last_block<1>(part, out, ticket);
+    // norm: out is |x|^2, and the last block derives 1 / |x| for k_normalize
+    if (finalize_last_block<1>(part, out, ticket) && norm && threadIdx.x == 0) {
+        const double nv = sqrt(out[0]);
+        out[S_INVN - S_DOT] = nv > 0.0 ? 1.0 / nv : 0.0;
+    }
 }
 
 __global__ void k_normalize(int n, const double *__restrict__ scal, double *__restrict__ x) {
-    const double nv = sqrt(scal[S_DOT]);
-    const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+    const double inv = scal[S_INVN];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         x[i] *= inv;
 }
@@ -358,7 +389,7 @@ __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
                           double *__restrict__ V, double *__restrict__ hist,
                           double *__restrict__ inv_m_out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double inv_m = 1.0 / (mass[i] * mass_unit);
+        const double inv_m = recip_nr(mass[i] * mass_unit);
         inv_m_out[i] = inv_m;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -471,7 +502,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     if (rc) return rc;
     // 2. lambda and q[n] (Eq. diag_linear_qeq); 1/u kept for the rest of the evaluation
     prof_begin(ctx, kPhShadow, s);
-    k_lambda_part<<<G, kThreads, 0, s>>>(n, prm->chi, u, ctx->v_n, ctx->inv_u, part, scal + S_LAM, tk);
+    k_lambda_part<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u, part,
+                                          scal + S_LAM, scal, tk);
     fin();
     k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn, scal,
                                      st->q, ctx->fvec, part, scal + S_CHG, tk);
@@ -533,7 +565,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
-            k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, part, scal + S_DOT, tk);
+            k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, j + 1 == k, part, scal + S_DOT,
+                                              tk);
             fin();
         }
         k_normalize<<<G, kThreads, 0, s>>>(n, scal, Wk);
