@@ -339,7 +339,7 @@ QEQ_API int qeq_shadow_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state
     }
     rc = shadow_evaluate(ctx, prm, st, s);
     if (rc) return rc;
-    return shadow_finish(ctx, prm, st, false, s);
+    return shadow_finish(ctx, prm, st, false, s, true);
 }
 
 // The evaluation and the second half kick of a fixed-rank shadow step contain
@@ -372,7 +372,7 @@ int ensure_step_graph(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, 
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_check(ctx, e, "graph capture begin");
     int rc = shadow_evaluate(ctx, prm, st, s);
-    if (!rc) rc = shadow_finish(ctx, prm, st, true, s);
+    if (!rc) rc = shadow_finish(ctx, prm, st, true, s, true);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     if (rc) {
@@ -414,7 +414,7 @@ static int evaluate_and_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_st
     if (!step_graphable(ctx, s)) {
         int rc = shadow_evaluate(ctx, prm, st, s);
         if (rc) return rc;
-        return shadow_finish(ctx, prm, st, true, s);
+        return shadow_finish(ctx, prm, st, true, s, true);
     }
     int rc = ensure_step_graph(ctx, prm, st, s);
     if (rc) return rc;
@@ -673,7 +673,7 @@ QEQ_API int qeq_bomd_init(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *
     }
     rc = bomd_evaluate(ctx, prm, st, tol, max_iter, info, s);
     if (rc) return rc;
-    return shadow_finish(ctx, prm, st, false, s);
+    return shadow_finish(ctx, prm, st, false, s, false);
 }
 
 QEQ_API int qeq_bomd_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, double tol,
@@ -685,6 +685,6 @@ QEQ_API int qeq_bomd_step(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *
     cudaStream_t s = (cudaStream_t)stream;
     rc = bomd_advance(ctx, prm, st, s);
     if (!rc) rc = bomd_evaluate(ctx, prm, st, tol, max_iter, info, s);
-    if (!rc) rc = shadow_finish(ctx, prm, st, true, s);
+    if (!rc) rc = shadow_finish(ctx, prm, st, true, s, false);
     return rc;
 }

@@ -156,7 +156,7 @@ QEQ_API int qeq_batch_step(qeq_batch *b, int32_t n, qeq_ctx *const *ctxs, const 
             graphed.push_back(c);
         } else {
             rc = shadow_evaluate(c, &prms[k], &sts[k], s);
-            if (!rc) rc = shadow_finish(c, &prms[k], &sts[k], true, s);
+            if (!rc) rc = shadow_finish(c, &prms[k], &sts[k], true, s, true);
             if (rc) return rc;
         }
     }

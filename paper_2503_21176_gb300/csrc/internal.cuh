@@ -394,6 +394,7 @@ struct qeq_ctx {
     int64_t graph_launches = 0;      // this library's kernels inside the graph
     int red_grid = 2 * 152;          // blocks of the reduction grid (set at creation)
     int sm_count = 152;              // SMs of the device (set at creation)
+    int kf_rank = 0;                 // Krylov vectors of the last shadow evaluation
     uint64_t graph_gen = 0;          // process-wide generation of the current step graph
     int64_t graph_captures = 0;      // step graphs captured since creation
     int64_t graph_replays = 0;       // step graph launches since creation
@@ -478,8 +479,10 @@ int check_md(qeq_ctx *ctx, const qeq_md_params *prm, const qeq_md_state *st);
 bool step_graphable(const qeq_ctx *ctx, cudaStream_t s);
 int ensure_step_graph(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s);
 void count_step_replay(qeq_ctx *ctx);
+// Second half kick (kick), kinetic and total energies, and with kf the kernel
+// update Kf = W c of the preceding shadow evaluation.
 int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
-                  cudaStream_t s);
+                  cudaStream_t s, bool kf);
 
 // ---- regular QEq / BO-MD (solver.cu) ----
 int solver_alloc(qeq_ctx *ctx, int restart);
@@ -579,6 +582,43 @@ __device__ __forceinline__ bool finalize_last_block(const double *part, double *
     }
     __syncthreads();
     return true;
+}
+
+// Grid maximum of non-negative values without a second launch: block maxima
+// into part[blockIdx.x], and the last block to arrive (ticket counter, reset to
+// 0) writes the maximum of them to *out.
+__device__ __forceinline__ void max_last_block(double m, double *part, double *out,
+                                               unsigned int *ticket) {
+    __shared__ double sh[kThreads / 32];
+    __shared__ bool is_last;
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) v = fmax(v, __ldcg(part + k));
+    v = warp_max(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
+        t = warp_max(t);
+        if (threadIdx.x == 0) {
+            *out = t;
+            *ticket = 0u;
+        }
+    }
 }
 
 // NVTX range over a library entry point (host side: a timeline tool shows where

@@ -564,36 +564,7 @@ __global__ void k_max_disp2(int n, const double *__restrict__ R, const double *_
         if (!(d2 == d2)) d2 = INFINITY;
         m = fmax(m, d2);
     }
-    __shared__ double sh[kThreads / 32];
-    __shared__ bool is_last;
-    m = warp_max(m);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
-        t = warp_max(t);
-        if (threadIdx.x == 0) part[blockIdx.x] = t;
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    double v = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) v = fmax(v, __ldcg(part + k));
-    v = warp_max(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double t = threadIdx.x < kThreads / 32 ? sh[threadIdx.x] : 0.0;
-        t = warp_max(t);
-        if (threadIdx.x == 0) {
-            *out = t;
-            *ticket = 0u;
-        }
-    }
+    max_last_block(m, part, out, ticket);
 }
 
 }  // namespace

@@ -207,54 +207,14 @@ __global__ void k_normalize(int n, const double *__restrict__ scal, double *__re
         x[i] *= inv;
 }
 
-// partials of O_ab = <R_a, R_b> (a <= b) and g_a = <R_a, f>; the rank M is a
-// template parameter so that the accumulators stay in registers.
-template <int M>
-__global__ void k_normal_part(int n, const double *__restrict__ Rb, const double *__restrict__ f,
-                              double *__restrict__ part) {
-    constexpr int nO = M * (M + 1) / 2;
-    double acc[nO + M];
-#pragma unroll
-    for (int k = 0; k < nO + M; ++k) acc[k] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double r[M];
-#pragma unroll
-        for (int a = 0; a < M; ++a) r[a] = Rb[(size_t)a * n + i];
-        const double fi = f[i];
-        int k = 0;
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-#pragma unroll
-            for (int b = a; b < M; ++b) acc[k++] += r[a] * r[b];
-#pragma unroll
-        for (int a = 0; a < M; ++a) acc[nO + a] += r[a] * fi;
-    }
-    block_sum<nO + M>(acc);
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < nO + M; ++k) part[k * kRedBlocks + blockIdx.x] = acc[k];
-}
-
-void launch_normal_part(int grid, int m, int n, const double *Rb, const double *f, double *part,
-                        cudaStream_t s) {
-    switch (m) {
-        case 1: k_normal_part<1><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 2: k_normal_part<2><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 3: k_normal_part<3><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 4: k_normal_part<4><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 5: k_normal_part<5><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 6: k_normal_part<6><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        case 7: k_normal_part<7><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-        default: k_normal_part<8><<<grid, kThreads, 0, s>>>(n, Rb, f, part); break;
-    }
-}
-
 // One block: sum the partials of O = R^T R and g = R^T f in fixed order, solve
 // O c = g (m x m) by Gaussian elimination with partial pivoting (singular
-// directions, e.g. f = 0, get c = 0), and write the evaluation's energies:
-// 1 shadow potential, 3 short range, 4 lambda, 5 sum q, 6 |f|, 7 applies.
-__global__ void k_normal_solve(int m, double q_tot, int applies, const double *__restrict__ part,
-                               int nb, double *__restrict__ scal, double *__restrict__ energies) {
+// directions get c = 0), and write c, the residual estimate and the energies.
+// The partials of other blocks of the same launch are read through L2 (ldcg).
+__device__ __forceinline__ void normal_solve_block(int m, double q_tot, int applies,
+                                                   const double *__restrict__ part, int nb,
+                                                   double *__restrict__ scal,
+                                                   double *__restrict__ energies) {
     __shared__ double sums[kMaxRank * (kMaxRank + 1) / 2 + kMaxRank];
     const int nO = m * (m + 1) / 2;
     // one warp per slot, lanes over the block partials in a fixed order
@@ -262,7 +222,7 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
     for (int k = warp; k < nO + m; k += nw) {
         double acc = 0.0;
         const double *p = part + (size_t)k * kRedBlocks;
-        for (int b = lane; b < nb; b += 32) acc += p[b];
+        for (int b = lane; b < nb; b += 32) acc += __ldcg(p + b);
         acc = warp_sum(acc);
         if (lane == 0) sums[k] = acc;
     }
@@ -324,6 +284,64 @@ __global__ void k_normal_solve(int m, double q_tot, int applies, const double *_
     energies[7] = (double)applies;
 }
 
+// partials of O_ab = <R_a, R_b> (a <= b) and g_a = <R_a, f>; the rank M is a
+// template parameter so that the accumulators stay in registers.
+template <int M>
+__global__ void k_normal_part(int n, const double *__restrict__ Rb, const double *__restrict__ f,
+                              double *__restrict__ part, double q_tot, int applies,
+                              double *__restrict__ scal, double *__restrict__ energies,
+                              unsigned int *__restrict__ ticket) {
+    constexpr int nO = M * (M + 1) / 2;
+    double acc[nO + M];
+#pragma unroll
+    for (int k = 0; k < nO + M; ++k) acc[k] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double r[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) r[a] = Rb[(size_t)a * n + i];
+        const double fi = f[i];
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = a; b < M; ++b) acc[k++] += r[a] * r[b];
+#pragma unroll
+        for (int a = 0; a < M; ++a) acc[nO + a] += r[a] * fi;
+    }
+    block_sum<nO + M>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < nO + M; ++k) part[k * kRedBlocks + blockIdx.x] = acc[k];
+    // the last block to arrive solves the normal equations
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    normal_solve_block(M, q_tot, applies, part, (int)gridDim.x, scal, energies);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+void launch_normal_part(int grid, int m, int n, const double *Rb, const double *f, double *part,
+                        double q_tot, int applies, double *scal, double *energies,
+                        unsigned int *ticket, cudaStream_t s) {
+#define QEQ_NP_ARGS n, Rb, f, part, q_tot, applies, scal, energies, ticket
+    switch (m) {
+        case 1: k_normal_part<1><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 2: k_normal_part<2><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 3: k_normal_part<3><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 4: k_normal_part<4><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 5: k_normal_part<5><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 6: k_normal_part<6><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 7: k_normal_part<7><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        default: k_normal_part<8><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+    }
+#undef QEQ_NP_ARGS
+}
+
+
 // partial of |R c - f|^2 for the current c (rank m): the least-squares residual of
 // the kernel update, computed directly (the normal-equation identity
 // |f|^2 - c.R^T f cancels catastrophically once the residual is small)
@@ -342,16 +360,6 @@ __global__ void k_ls_residual(int n, int m, const double *__restrict__ Rb,
     block_sum<1>(vals);
     if (threadIdx.x == 0) part[blockIdx.x] = vals[0];
     finalize_last_block<1>(part, out, ticket);
-}
-
-__global__ void k_kf(int n, int m, const double *__restrict__ Wb, const double *__restrict__ scal,
-                     double *__restrict__ Kf) {
-    const double *c = scal + S_OM + kMaxRank * kMaxRank;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int a = 0; a < m; ++a) s += c[a] * Wb[(size_t)a * n + i];
-        Kf[i] = s;
-    }
 }
 
 struct Dissipation {
@@ -382,21 +390,32 @@ Dissipation dissipation(int kd) {
 }
 
 // Half kick + drift of R; n_{t+1} = 2 n_t - n_{t-1} - kappa Kf + alpha sum_k c_k n_{t-k};
-// history shifted in place (each thread owns one atom's column).
+// history shifted in place (each thread owns one atom's column).  The same pass
+// finds the largest squared displacement since the last neighbour build (the
+// skin check) into *max_d2.
 __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
                           const double *__restrict__ mass, const double *__restrict__ F,
                           const double *__restrict__ Kf, double *__restrict__ R,
                           double *__restrict__ V, double *__restrict__ hist,
-                          double *__restrict__ inv_m_out) {
+                          double *__restrict__ inv_m_out, const double *__restrict__ R0,
+                          double *__restrict__ part, double *__restrict__ max_d2,
+                          unsigned int *__restrict__ ticket) {
+    double mx = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double inv_m = recip_nr(mass[i] * mass_unit);
         inv_m_out[i] = inv_m;
+        double d2 = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double vi = V[3 * (size_t)i + d] + 0.5 * dt * F[3 * (size_t)i + d] * inv_m;
             V[3 * (size_t)i + d] = vi;
-            R[3 * (size_t)i + d] += dt * vi;
+            const double r = R[3 * (size_t)i + d] + dt * vi;
+            R[3 * (size_t)i + d] = r;
+            const double dd = r - R0[3 * (size_t)i + d];
+            d2 += dd * dd;
         }
+        if (!(d2 == d2)) d2 = INFINITY;
+        mx = fmax(mx, d2);
         double h[kMaxHist];
         for (int k = 0; k <= dis.kd; ++k) h[k] = hist[(size_t)k * n + i];
         double acc = 0.0;
@@ -405,16 +424,25 @@ __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
         for (int k = dis.kd; k >= 1; --k) hist[(size_t)k * n + i] = h[k - 1];
         hist[i] = nn;
     }
+    max_last_block(mx, part, max_d2, ticket);
 }
 
-// optional second half kick, then partial of the kinetic energy
+// optional second half kick, then partial of the kinetic energy; with kf_rank > 0
+// also the kernel update Kf = W c of the evaluation (c from the normal equations)
 __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
                          const double *__restrict__ mass, const double *__restrict__ inv_m,
-                         const double *__restrict__ F, double *__restrict__ V,
+                         const double *__restrict__ F, double *__restrict__ V, int kf_rank,
+                         const double *__restrict__ Wb, double *__restrict__ Kf,
                          double *__restrict__ part, double *__restrict__ scal,
                          double *__restrict__ energies, unsigned int *__restrict__ ticket) {
+    const double *c = scal + S_OM + kMaxRank * kMaxRank;
     double ke = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (kf_rank > 0) {
+            double kfi = 0.0;
+            for (int a = 0; a < kf_rank; ++a) kfi += c[a] * Wb[(size_t)a * n + i];
+            Kf[i] = kfi;
+        }
         const double mi = mass[i] * mass_unit;
         double v2 = 0.0;
 #pragma unroll
@@ -531,10 +559,9 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     auto solve_rank = [&](int k, bool *done) -> int {
         const int nO = k * (k + 1) / 2;
         prof_begin(ctx, kPhShadow, s);
-        launch_normal_part(ctx->red_grid, k, n, ctx->Rb, ctx->fvec, part, s);
-        k_normal_solve<<<1, kThreads, 0, s>>>(k, ctx->p.q_tot, k + 1, part, ctx->red_grid, scal,
-                                              st->energies);
-        ctx->launches += 2;
+        launch_normal_part(ctx->red_grid, k, n, ctx->Rb, ctx->fvec, part, ctx->p.q_tot, k + 1, scal,
+                           st->energies, tk, s);
+        ctx->launches += 1;
         prof_end(ctx, s);
         (void)nO;
         *done = true;
@@ -595,36 +622,31 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         rc = solve_rank(m, &done);
         if (rc) return rc;
     }
-    // 6. Kf = W c
-    prof_begin(ctx, kPhShadow, s);
-    k_kf<<<G, kThreads, 0, s>>>(n, m_used, ctx->Wb, scal, st->Kf);
-    ctx->launches++;
-    prof_end(ctx, s);
+    // 6. Kf = W c is formed by the finish kernel that follows every evaluation
+    ctx->kf_rank = m_used;
     return cuda_check(ctx, cudaGetLastError(), "shadow evaluate launch");
 }
 
 int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_advance<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
-                                              dissipation(ctx->p.dissipation_k), prm->mass, st->F,
-                                              st->Kf, st->R, st->V, st->n_hist, ctx->inv_m);
+    k_advance<<<ctx->red_grid, kThreads, 0, s>>>(
+        n, ctx->p.dt, ctx->p.mass_unit, dissipation(ctx->p.dissipation_k), prm->mass, st->F,
+        st->Kf, st->R, st->V, st->n_hist, ctx->inv_m, ctx->R_build, ctx->part,
+        ctx->scal + kScMaxDisp2, ctx->ticket);
     prof_end(ctx, s);
     ctx->launches++;
-    return nl_displacement(ctx, st->R, s, nullptr);
+    return cuda_check(ctx, cudaGetLastError(), "advance launch");
 }
 
 int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
-    const int n = (int)ctx->n;
-    prof_begin(ctx, kPhIntegrate, s);
-    k_advance<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit,
-                                              dissipation(ctx->p.dissipation_k), prm->mass, st->F,
-                                              st->Kf, st->R, st->V, st->n_hist, ctx->inv_m);
-    prof_end(ctx, s);
-    ctx->launches++;
-    double d2 = 0.0;
-    int rc = nl_displacement(ctx, st->R, s, &d2);
+    int rc = shadow_advance_queue(ctx, prm, st, s);
     if (rc) return rc;
+    cudaMemcpyAsync(ctx->h_scal + kScMaxDisp2, ctx->scal + kScMaxDisp2, sizeof(double),
+                    cudaMemcpyDeviceToHost, s);
+    rc = cuda_check(ctx, cudaStreamSynchronize(s), "displacement check");
+    if (rc) return rc;
+    const double d2 = ctx->h_scal[kScMaxDisp2];
     const double half = 0.5 * ctx->p.skin;
     if (!(d2 <= half * half)) {
         rc = nl_build(ctx, st->R, s);
@@ -634,12 +656,13 @@ int shadow_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cud
 }
 
 int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool kick,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool kf) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
+    const int rank = kf && st->Kf ? ctx->kf_rank : 0;
     k_finish<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
-                                             ctx->inv_m, st->F, st->V, ctx->part, ctx->scal,
-                                             st->energies, ctx->ticket);
+                                             ctx->inv_m, st->F, st->V, rank, ctx->Wb, st->Kf,
+                                             ctx->part, ctx->scal, st->energies, ctx->ticket);
     prof_end(ctx, s);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "shadow finish launch");
