@@ -203,85 +203,67 @@ struct EmitArgs {
 // run the same iteration of the real-space kernel then hold neighbours of the
 // same class, so its distance branches (cutoff test, Gaussian correction) agree
 // across the warp.
-// Lanes per row in the emit: lane s of a row tests candidates s, s + 4, ... of
-// the row's candidate stream (its cell's (2 reach + 1)^3 neighbour cells,
-// concatenated).  Rows of one cell have the same stream, so the 8 rows of a warp
-// (mostly one cell of about 9 atoms) walk it in lockstep.
+// Lanes per row in the emit: lane s of a row tests atoms s, s + 4, ... of each
+// of the row's candidate cells (its cell's (2 reach + 1)^3 neighbour cells).
+// Rows of one cell visit the same cells, so the 8 rows of a warp (mostly one
+// cell of about 9 atoms) walk them in lockstep and share each candidate load.
 constexpr int kEmitLanes = 4;
 constexpr int kMaxBrickCells = 8;
 constexpr int kCenterCode = 62;  // image code of the zero shift
 
-// The candidate stream of one lane: cell k of the table, candidate j in it.
-struct Cursor {
-    int k, j;
-    int4 ct;  // (first sorted atom, end, tile base, image code) of cell k
-};
-
-__device__ __forceinline__ bool cursor_fix(Cursor &c, const int4 *__restrict__ tab, int ncand) {
-    while (c.j >= c.ct.y) {
-        const int over = c.j - c.ct.y;
-        if (++c.k >= ncand) return false;
-        c.ct = tab[c.k];
-        c.j = c.ct.x + over;
-    }
-    return true;
-}
-
-// The test pass over a lane's candidate stream.  Lane s appends each kept
-// entry, with its distance class in bits 16-17, to its own slots 4 m + s of the
-// 32-bit scratch list (m < cap = width / 4), and counts each class; counts keep
-// running past cap (an overflow, reported for the regrowth).  The FP64 decision
-// is taken only inside the band [lo, hi] of the FP32 distance.
-__device__ __forceinline__ void emit_stream(const EmitArgs &a, int i, int s, const int4 *__restrict__ tab,
-                                            int ncand, const double4_32a &xi, const float4 &xf,
-                                            const double4_32a *__restrict__ xs64,
-                                            const float4 *__restrict__ xs32, int cap, int (&c)[3],
-                                            uint32_t *__restrict__ scr, int t_total,
-                                            int32_t *__restrict__ flags) {
-    Cursor cu;
-    cu.k = 0;
-    cu.ct = tab[0];
-    cu.j = cu.ct.x + s;
-    int code = -1;
-    int m = 0;
-    float shx = 0.f, shy = 0.f, shz = 0.f;
-    while (cursor_fix(cu, tab, ncand)) {
-        if (cu.ct.w != code) {
-            code = cu.ct.w;
-            shx = (float)(code / 25 - 2) * a.Lfx;
-            shy = (float)((code / 5) % 5 - 2) * a.Lfy;
-            shz = (float)(code % 5 - 2) * a.Lfz;
+// The test pass of one lane, as a double loop: over the row's candidate cells
+// (one table entry and one image shift per cell, the shift folded into the
+// row's own position), and over each cell's atoms with stride kEmitLanes (lane
+// s takes atoms s, s + 4, ...).  The decision is FP32 outside the band [lo, hi]
+// and FP64 with a fixed operation order inside it; the distance class comes
+// from the FP32 d^2.  A kept entry goes, with its class in bits 16-17, to the
+// lane's slots 4 m + s of the 32-bit scratch list (m < cap = width / 4), and the
+// classes are counted; counts keep running past cap (an overflow, reported for
+// the regrowth).
+__device__ __forceinline__ void emit_cells(const EmitArgs &a, int i, int s, const int4 *__restrict__ tab,
+                                           const float4 *__restrict__ shtab, int ncand,
+                                           const double4_32a &xi, const float4 &xf,
+                                           const double4_32a *__restrict__ xs64,
+                                           const float4 *__restrict__ xs32, int cap, int (&c)[3],
+                                           uint32_t *__restrict__ scr, int t_total,
+                                           int32_t *__restrict__ flags) {
+    // this lane's scratch slots 4 m + s of row i: stripe m / 4, word m % 4
+    const size_t stripe = (size_t)a.n * kListStripe;
+    size_t base = (size_t)i * kListStripe + (size_t)s * 4u;
+    int m = 0, near = 0, inside = 0;
+    for (int k = 0; k < ncand; ++k) {
+        const int4 ct = tab[k];
+        const float4 sh = shtab[ct.w];
+        const float px = xf.x - sh.x, py = xf.y - sh.y, pz = xf.z - sh.z;
+        const bool home = ct.w == kCenterCode;
+        for (int j = ct.x + s; j < ct.y; j += kEmitLanes) {
+            const float4 xj = xs32[j];
+            const float dxf = xj.x - px, dyf = xj.y - py, dzf = xj.z - pz;
+            const float d2f = fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf));
+            if (d2f > a.hi) continue;
+            if (home && j == i) continue;
+            if (!(d2f < a.lo)) {
+                const int code = ct.w;
+                const double4_32a xj64 = xs64[j];
+                const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), image_shift(code / 25 - 2, a.Lx, a.L2x));
+                const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), image_shift((code / 5) % 5 - 2, a.Ly, a.L2y));
+                const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), image_shift(code % 5 - 2, a.Lz, a.L2z));
+                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                if (!(d2 < a.rl2)) continue;
+            }
+            const int e = j + ct.z;
+            if (!QEQ_IN_BOUNDS((unsigned)e < (unsigned)t_total, flags, kSiteEmitTile)) continue;
+            const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
+            near += cls == 0;
+            inside += cls == 1;
+            if (m < cap) scr[base + (m & 3)] = (uint32_t)e | ((uint32_t)cls << 16);
+            ++m;
+            if ((m & 3) == 0) base += stripe;
         }
-        const int j = cu.j;
-        cu.j += kEmitLanes;
-        if (code == kCenterCode && j == i) continue;
-        const float4 xj = xs32[j];
-        const float dxf = (xj.x - xf.x) + shx;
-        const float dyf = (xj.y - xf.y) + shy;
-        const float dzf = (xj.z - xf.z) + shz;
-        const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-        bool keep;
-        if (d2f < a.lo) {
-            keep = true;
-        } else if (d2f > a.hi) {
-            keep = false;
-        } else {
-            const double4_32a xj64 = xs64[j];
-            const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), image_shift(code / 25 - 2, a.Lx, a.L2x));
-            const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), image_shift((code / 5) % 5 - 2, a.Ly, a.L2y));
-            const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), image_shift(code % 5 - 2, a.Lz, a.L2z));
-            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            keep = d2 < a.rl2;
-        }
-        if (!keep) continue;
-        if (!QEQ_IN_BOUNDS((unsigned)(j + cu.ct.z) < (unsigned)t_total, flags, kSiteEmitTile)) continue;
-        const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
-        if (m < cap) scr[list_index(kEmitLanes * m + s, i, a.n)] = (uint32_t)(j + cu.ct.z) | ((uint32_t)cls << 16);
-        ++m;
-        c[0] += cls == 0;
-        c[1] += cls == 1;
-        c[2] += cls == 2;
     }
+    c[0] = near;
+    c[1] = inside;
+    c[2] = m - near - inside;
 }
 
 // One block per brick.  Warp 0 builds the tile table, then the block builds the
@@ -298,11 +280,15 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
        int32_t *__restrict__ flags) {
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
+    __shared__ float4 shtab[kMaxTileBricks];  // image shift s L of each code (sx + 2) * 25 + ...
     // nchunk blocks share a brick: chunk c takes the brick's groups of 32 rows
     // c, c + nchunk, ... (more blocks in flight for boxes of few bricks)
     const int64_t b = blockIdx.x / nchunk;
     const int chunk = (int)(blockIdx.x - b * nchunk);
     if (threadIdx.x < 32) tile_table(g, b, cell_start, t_start, t_base, t_code, &t_total);
+    for (int code = threadIdx.x; code < 125; code += blockDim.x)
+        shtab[code] = make_float4((float)(code / 25 - 2) * a.Lfx, (float)((code / 5) % 5 - 2) * a.Lfy,
+                                  (float)(code % 5 - 2) * a.Lfz, 0.f);
     __syncthreads();
     const int i0 = t_start[g.center], i1 = cell_start[(b + 1) * g.bvol];
     if (chunk == 0) {
@@ -354,7 +340,8 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
         int c[3] = {0, 0, 0};
         if (act) {
             const int4 *tab = ctab[cell_s[i] - (int)(b * g.bvol)];
-            emit_stream(a, i, s, tab, ncand, xs64[i], xs32[i], xs64, xs32, cap, c, scr, t_total, flags);
+            emit_cells(a, i, s, tab, shtab, ncand, xs64[i], xs32[i], xs64, xs32, cap, c, scr, t_total,
+                       flags);
         }
         const int mine = c[0] + c[1] + c[2];
         // this lane's first row slot in each class: the classes in order, and in

@@ -97,7 +97,11 @@ def test_fp32_band_covers_the_fp32_error(L, r_cut):
     dx32 = [(xj32[:, k] - xi32[:, k]) + sh32[:, k] for k in range(3)]
     d2_plain = (dx32[0] * dx32[0] + dx32[1] * dx32[1]) + dx32[2] * dx32[2]
     d2_fused = _fma32(dx32[2], dx32[2], _fma32(dx32[1], dx32[1], dx32[0] * dx32[0]))
-    for d2f in (d2_plain, d2_fused):
+    # the cell-by-cell emit folds the shift into the row's position first:
+    # d = x_j - (x_i - s L), then d^2 with fused multiply-adds
+    dxs = [xj32[:, k] - (xi32[:, k] - sh32[:, k]) for k in range(3)]
+    d2_shifted = _fma32(dxs[2], dxs[2], _fma32(dxs[1], dxs[1], dxs[0] * dxs[0]))
+    for d2f in (d2_plain, d2_fused, d2_shifted):
         below, above = d2f < lo, d2f > hi
         assert below.any() and above.any() and (~below & ~above).any()
         assert np.all(keep64[below]), "FP32 kept a pair the FP64 test drops"
