@@ -19,7 +19,9 @@ initial evaluation an MD request joins a stepper thread, which advances every
 member in lockstep with qeq_batch_step on its own stream: per step, one host
 synchronisation covers all members' skin checks and one CUDA graph launch runs
 all their evaluations as parallel branches (the graph is rebuilt only when the
-members change).  A request joins at the next step once its initial evaluation
+members change).  Systems below `batch_split_atoms` atoms and larger ones go to
+two steppers (two threads, two streams), so that a small system never waits in
+lockstep for the step of a large one.  A request joins at the next step once its initial evaluation
 is done (a CUDA event orders it before the stepper's stream) and leaves when
 its steps are done (an event orders its download after them).  A failing
 batch step fails the requests stepped in it.
@@ -186,9 +188,11 @@ class Server:
     batch_md = False  # set by __init__ (default on); subclasses with their own executor keep it off
     _stepper = None
 
-    def __init__(self, device=0, max_inflight=8, hbm_budget=None, headroom=2 << 30, batch_md=True):
+    def __init__(self, device=0, max_inflight=8, hbm_budget=None, headroom=2 << 30, batch_md=True,
+                 batch_split_atoms=4000):
         self.device = torch.device("cuda", device)
         self.batch_md = bool(batch_md)
+        self.batch_split_atoms = int(batch_split_atoms)
         self._stepper = None
         self.max_inflight = int(max_inflight)
         with torch.cuda.device(self.device):
@@ -229,7 +233,8 @@ class Server:
                     if self._stepper is not None:
                         ready = torch.cuda.Event()
                         ready.record(stream)
-                        member = self._stepper.submit(md, req.steps, ready)
+                        stepper = self._stepper[req.n_atoms >= self.batch_split_atoms]
+                        member = stepper.submit(md, req.steps, ready)
                         member.finished.wait()
                         if member.error:
                             raise RuntimeError(member.error)
@@ -265,7 +270,7 @@ class Server:
         max_conc = 0
         pool = cf.ThreadPoolExecutor(max_workers=self.max_inflight)
         if self.batch_md:
-            self._stepper = _BatchStepper(self.device)
+            self._stepper = (_BatchStepper(self.device), _BatchStepper(self.device))
         t0 = time.perf_counter()
         try:
             while pending or ready or inflight:
@@ -301,14 +306,19 @@ class Server:
                                                   error=f"{type(exc).__name__}: {exc}")
         finally:
             pool.shutdown(wait=True)
-            stepper, self._stepper = self._stepper, None
+            steppers, self._stepper = self._stepper, None
             batching = None
-            if stepper is not None:
-                stepper.close_thread()
-                batching = {"batch_steps": stepper.ticks, "member_steps": stepper.member_steps,
-                            "mean_members_per_step": round(stepper.member_steps / max(1, stepper.ticks), 3),
-                            "parent_graphs_built": stepper.batch.stats()[0]}
-                stepper.batch.close()
+            if steppers is not None:
+                for st in steppers:
+                    st.close_thread()
+                ticks = sum(st.ticks for st in steppers)
+                member_steps = sum(st.member_steps for st in steppers)
+                batching = {"batch_steps": ticks, "member_steps": member_steps,
+                            "mean_members_per_step": round(member_steps / max(1, ticks), 3),
+                            "parent_graphs_built": sum(st.batch.stats()[0] for st in steppers),
+                            "steppers": "below / from %d atoms" % self.batch_split_atoms}
+                for st in steppers:
+                    st.batch.close()
         t_end = time.perf_counter()
         res = [results[r] for r in sorted(results)]
         ok = [r for r in res if r.error is None]
