@@ -105,3 +105,44 @@ def test_batch_rejects_bad_members():
     assert np.isfinite(md.energy_dict()["total"])
     batch.close()
     s.close()
+
+
+def test_batch_with_mixed_precision_members():
+    """FP32-mixed and FP64 members in one batch: each follows its own separate steps
+    (FP64 to 1e-10; FP32-mixed to the rounding order of its float mesh atomics)."""
+    qg = cuda_or_skip()
+    stream = torch.cuda.Stream()
+    batch = qg.ShadowBatch()
+    pairs = []
+    for n_mol, seed, prec in ((50, 91, "fp32_mixed"), (120, 92, "fp64"), (200, 93, "fp32_mixed")):
+        made = []
+        for _ in range(2):
+            w = water_box(n_mol, seed=seed)
+            K = serving_mesh_size(w.box[0])
+            p = qg.make_params(w.n_atoms, w.box, alpha=0.34, r_cut=8.0, skin=1.0, mesh=(K, K, K),
+                               order=4, precision=prec, krylov_rank=2, dt=0.5)
+            s = qg.System(p)
+            md = qg.ShadowMD(s, dev_tensor(w.chi), dev_tensor(w.eta), dev_tensor(w.sigma),
+                             dev_tensor(w.mass), dev_tensor(w.R), dev_tensor(_maxwell(w, 0.02585, seed)),
+                             torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda"))
+            made.append((s, md))
+        pairs.append((prec, made))
+    with torch.cuda.stream(stream):
+        for _, made in pairs:
+            for s, md in made:
+                md.init(stream)
+        for _ in range(6):
+            batch.step([made[0][1] for _, made in pairs], stream)
+            for _, made in pairs:
+                made[1][1].step(1, stream)
+        stream.synchronize()
+    for prec, made in pairs:
+        a, b = _state(made[0][1]), _state(made[1][1])
+        if prec == "fp64":
+            _same(a, b)
+        else:
+            assert np.abs(a[0] - b[0]).max() < 1e-6 and rel_max(a[1], b[1]) < 1e-5
+            assert abs(a[3] - b[3]) < 1e-7 * abs(b[3])
+        for s, _ in made:
+            s.close()
+    batch.close()
