@@ -133,7 +133,11 @@ __global__ void k_gather_q(int n, const int32_t *__restrict__ perm, const double
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (!QEQ_IN_BOUNDS((unsigned)perm[i] < (unsigned)n, flags, kSiteGatherPerm)) return;
-    const T qa = (T)q[perm[i]];
+    T qa;
+    if constexpr (std::is_same<T, float>::value)
+        qa = f64_to_f32_trunc(q[perm[i]]);  // as k_gather_in, on the integer pipe
+    else
+        qa = q[perm[i]];
     xq[i].w = qa;
     sfrac[i].w = qa;
 }
@@ -876,7 +880,6 @@ __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, 
 struct SpreadWin {
     int K0, K1, K2;
     int E0, E1, E2;      // window extent (E2 a multiple of 4)
-    double X0, X1, X2;   // mesh points per brick and axis
     int vec;             // K2 % 4 == 0: vector flush allowed
     float wmax;          // upper bound of one atom's weight at one mesh point
 };
@@ -906,8 +909,10 @@ k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
     const int64_t b = blockIdx.x;
     const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
     const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
-    const int lo0 = (int)floor(bx * w.X0) - (P - 1), lo1 = (int)floor(by * w.X1) - (P - 1);
-    const int lo2 = ((int)floor(bz * w.X2) - (P - 1)) & ~3;
+    // first mesh point of the brick: floor(b K / nb) per axis, in integers (exact;
+    // an FP64 multiply and floor would wait on GB300's 1/64-rate FP64 pipe)
+    const int lo0 = bx * w.K0 / g.nb[0] - (P - 1), lo1 = by * w.K1 / g.nb[1] - (P - 1);
+    const int lo2 = (bz * w.K2 / g.nb[2] - (P - 1)) & ~3;
     const int nwin = w.E0 * w.E1 * w.E2;
     const int a0 = cell_start[b * g.bvol], a1 = cell_start[(b + 1) * g.bvol];
     float qs = 0.f;
@@ -1530,9 +1535,6 @@ SpreadWin spread_window(const qeq_ctx *ctx, int P, size_t elem, size_t *nbytes) 
     const double X[3] = {g.B[0] * ctx->cw[0] * ctx->K[0] / ctx->p.box[0],
                          g.B[1] * ctx->cw[1] * ctx->K[1] / ctx->p.box[1],
                          g.B[2] * ctx->cw[2] * ctx->K[2] / ctx->p.box[2]};
-    w.X0 = X[0];
-    w.X1 = X[1];
-    w.X2 = X[2];
     // base = floor(K x / L) of the brick's atoms lies in [floor(b X), floor((b + 1) X)],
     // floor((b + 1) X) - floor(b X) <= ceil(X), and the support reaches P - 1
     // points below: ceil(X) + P points per axis, up to 3 more below z from the

@@ -179,9 +179,12 @@ constexpr int kEmitBlocksPerSm = 4;
 // s L for an image index s in [-2, 2]: exact in FP64 (a multiple of L by 0, 1 or
 // 2), selected without an FP64 multiply.
 __device__ __forceinline__ double image_shift(int s, double L, double L2) {
-    const double a = (s == 1 || s == -1) ? L : L2;
-    const double m = s < 0 ? -a : a;
-    return s == 0 ? 0.0 : m;
+    // selected and negated on the integer pipe (sign bit flipped): the compiler
+    // hoists this out of the candidate loops, and FP64 selects or negations
+    // there would occupy GB300's 1/64-rate FP64 pipe once per cell
+    const long long a = __double_as_longlong((s == 1 || s == -1) ? L : L2);
+    const long long m = s < 0 ? (a ^ (long long)0x8000000000000000ull) : a;
+    return __longlong_as_double(s == 0 ? 0ll : m);
 }
 
 struct EmitArgs {
