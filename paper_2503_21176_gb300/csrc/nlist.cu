@@ -214,6 +214,23 @@ constexpr int kEmitLanes = 4;
 constexpr int kMaxBrickCells = 8;
 constexpr int kCenterCode = 62;  // image code of the zero shift
 
+// The exact decision inside the FP32 band: d = (xw_j - xw_i) + s L per axis and
+// d^2 = (dx dx + dy dy) + dz dz, each operation explicitly rounded.  Not inlined,
+// and reading the arguments from the block's shared copy: inlined, the selection
+// of its image shifts was hoisted into the per-cell prologue of the candidate
+// loop and ran for every cell (the band holds a few candidates per row), about a
+// quarter of the emit's instructions.
+__device__ __noinline__ bool band_keep(const EmitArgs *ap, int code, const double4_32a *pj,
+                                       const double4_32a *pi) {
+    const EmitArgs &a = *ap;
+    const double4_32a xj64 = *pj, xi = *pi;
+    const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), image_shift(code / 25 - 2, a.Lx, a.L2x));
+    const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), image_shift((code / 5) % 5 - 2, a.Ly, a.L2y));
+    const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), image_shift(code % 5 - 2, a.Lz, a.L2z));
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 < a.rl2;
+}
+
 // The test pass of one lane, as a double loop: over the row's candidate cells
 // (one table entry and one image shift per cell, the shift folded into the
 // row's own position), and over each cell's atoms with stride kEmitLanes (lane
@@ -223,9 +240,10 @@ constexpr int kCenterCode = 62;  // image code of the zero shift
 // lane's slots 4 m + s of the 32-bit scratch list (m < cap = width / 4), and the
 // classes are counted; counts keep running past cap (an overflow, reported for
 // the regrowth).
-__device__ __forceinline__ void emit_cells(const EmitArgs &a, int i, int s, const int4 *__restrict__ tab,
+__device__ __forceinline__ void emit_cells(const EmitArgs &a, const EmitArgs *sa, int i, int s,
+                                           const int4 *__restrict__ tab,
                                            const float4 *__restrict__ shtab, int ncand,
-                                           const double4_32a &xi, const float4 &xf,
+                                           const float4 &xf,
                                            const double4_32a *__restrict__ xs64,
                                            const float4 *__restrict__ xs32, int cap, int (&c)[3],
                                            uint32_t *__restrict__ scr, int t_total,
@@ -245,15 +263,7 @@ __device__ __forceinline__ void emit_cells(const EmitArgs &a, int i, int s, cons
             const float d2f = fmaf(dzf, dzf, fmaf(dyf, dyf, dxf * dxf));
             if (d2f > a.hi) continue;
             if (home && j == i) continue;
-            if (!(d2f < a.lo)) {
-                const int code = ct.w;
-                const double4_32a xj64 = xs64[j];
-                const double dx = __dadd_rn(__dsub_rn(xj64.x, xi.x), image_shift(code / 25 - 2, a.Lx, a.L2x));
-                const double dy = __dadd_rn(__dsub_rn(xj64.y, xi.y), image_shift((code / 5) % 5 - 2, a.Ly, a.L2y));
-                const double dz = __dadd_rn(__dsub_rn(xj64.z, xi.z), image_shift(code % 5 - 2, a.Lz, a.L2z));
-                const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                if (!(d2 < a.rl2)) continue;
-            }
+            if (!(d2f < a.lo) && !band_keep(sa, ct.w, xs64 + j, xs64 + i)) continue;
             const int e = j + ct.z;
             if (!QEQ_IN_BOUNDS((unsigned)e < (unsigned)t_total, flags, kSiteEmitTile)) continue;
             const int cls = (d2f >= a.t_near) + (d2f >= a.t_cut);
@@ -284,6 +294,8 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
     __shared__ float4 shtab[kMaxTileBricks];  // image shift s L of each code (sx + 2) * 25 + ...
+    __shared__ EmitArgs sargs;  // the band decision's copy of the arguments
+    if (threadIdx.x == 0) sargs = a;
     // nchunk blocks share a brick: chunk c takes the brick's groups of 32 rows
     // c, c + nchunk, ... (more blocks in flight for boxes of few bricks)
     const int64_t b = blockIdx.x / nchunk;
@@ -343,7 +355,7 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
         int c[3] = {0, 0, 0};
         if (act) {
             const int4 *tab = ctab[cell_s[i] - (int)(b * g.bvol)];
-            emit_cells(a, i, s, tab, shtab, ncand, xs64[i], xs32[i], xs64, xs32, cap, c, scr, t_total,
+            emit_cells(a, &sargs, i, s, tab, shtab, ncand, xs32[i], xs64, xs32, cap, c, scr, t_total,
                        flags);
         }
         const int mine = c[0] + c[1] + c[2];

@@ -65,6 +65,7 @@ __global__ void k_lambda_part(int n, double q_tot, const double *__restrict__ ch
                               double *__restrict__ inv_u, double *__restrict__ part,
                               double *__restrict__ out, double *__restrict__ scal,
                               unsigned int *__restrict__ ticket) {
+    pdl_begin();
     double s1 = 0.0, s2 = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double iu = recip_nr(u[i]);
@@ -88,6 +89,7 @@ __global__ void k_charges(int n, double q_tot, const double *__restrict__ chi,
                           const double *__restrict__ nn, const double *__restrict__ scal,
                           double *__restrict__ q, double *__restrict__ f, double *__restrict__ part,
                           double *__restrict__ out, unsigned int *__restrict__ ticket) {
+    pdl_begin();
     const double lam = scal[S_LAMV];
     double a[6] = {0, 0, 0, 0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -120,6 +122,7 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
                             double *__restrict__ F, double *__restrict__ w1,
                             double *__restrict__ phi, double *__restrict__ part,
                             double *__restrict__ out, unsigned int *__restrict__ ticket) {
+    pdl_begin();
     const double inv = scal[S_INVF];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -144,6 +147,7 @@ __global__ void k_forces_w1(int n, const double *__restrict__ q, const double *_
 __global__ void k_mu_part(int n, const double *__restrict__ phi, const double *__restrict__ inv_u,
                           double *__restrict__ part, double *__restrict__ out,
                           unsigned int *__restrict__ ticket) {
+    pdl_begin();
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         s += phi[i] * inv_u[i];
@@ -162,6 +166,7 @@ __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *
                            double *__restrict__ r, double *__restrict__ wnext,
                            const double *__restrict__ w0, double *__restrict__ part,
                            double *__restrict__ out, unsigned int *__restrict__ ticket) {
+    pdl_begin();
     const double mu = scal[S_MUV];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -184,6 +189,7 @@ __global__ void k_jacobian(int n, const double *__restrict__ phi, const double *
 __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double *__restrict__ y,
                            double *x, const double *z, bool norm, double *__restrict__ part,
                            double *__restrict__ out, unsigned int *__restrict__ ticket) {
+    pdl_begin();
     const double a = scal[S_DOT];
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -202,6 +208,7 @@ __global__ void k_axpy_dot(int n, const double *__restrict__ scal, const double 
 }
 
 __global__ void k_normalize(int n, const double *__restrict__ scal, double *__restrict__ x) {
+    pdl_begin();
     const double inv = scal[S_INVN];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         x[i] *= inv;
@@ -291,6 +298,7 @@ __global__ void k_normal_part(int n, const double *__restrict__ Rb, const double
                               double *__restrict__ part, double q_tot, int applies,
                               double *__restrict__ scal, double *__restrict__ energies,
                               unsigned int *__restrict__ ticket) {
+    pdl_begin();
     constexpr int nO = M * (M + 1) / 2;
     double acc[nO + M];
 #pragma unroll
@@ -329,14 +337,14 @@ void launch_normal_part(int grid, int m, int n, const double *Rb, const double *
                         unsigned int *ticket, cudaStream_t s) {
 #define QEQ_NP_ARGS n, Rb, f, part, q_tot, applies, scal, energies, ticket
     switch (m) {
-        case 1: k_normal_part<1><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        case 2: k_normal_part<2><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        case 3: k_normal_part<3><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        case 4: k_normal_part<4><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        case 5: k_normal_part<5><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        case 6: k_normal_part<6><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        case 7: k_normal_part<7><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
-        default: k_normal_part<8><<<grid, kThreads, 0, s>>>(QEQ_NP_ARGS); break;
+        case 1: launch_pdl(k_normal_part<1>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 2: launch_pdl(k_normal_part<2>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 3: launch_pdl(k_normal_part<3>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 4: launch_pdl(k_normal_part<4>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 5: launch_pdl(k_normal_part<5>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 6: launch_pdl(k_normal_part<6>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 7: launch_pdl(k_normal_part<7>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        default: launch_pdl(k_normal_part<8>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
     }
 #undef QEQ_NP_ARGS
 }
@@ -349,6 +357,7 @@ __global__ void k_ls_residual(int n, int m, const double *__restrict__ Rb,
                               const double *__restrict__ f, const double *__restrict__ scal,
                               double *__restrict__ part, double *__restrict__ out,
                               unsigned int *__restrict__ ticket) {
+    pdl_begin();
     const double *c = scal + S_OM + kMaxRank * kMaxRank;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -400,6 +409,7 @@ __global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
                           double *__restrict__ inv_m_out, const double *__restrict__ R0,
                           double *__restrict__ part, double *__restrict__ max_d2,
                           unsigned int *__restrict__ ticket) {
+    pdl_begin();
     double mx = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double inv_m = recip_nr(mass[i] * mass_unit);
@@ -435,6 +445,7 @@ __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
                          const double *__restrict__ Wb, double *__restrict__ Kf,
                          double *__restrict__ part, double *__restrict__ scal,
                          double *__restrict__ energies, unsigned int *__restrict__ ticket) {
+    pdl_begin();
     const double *c = scal + S_OM + kMaxRank * kMaxRank;
     double ke = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -530,10 +541,10 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     if (rc) return rc;
     // 2. lambda and q[n] (Eq. diag_linear_qeq); 1/u kept for the rest of the evaluation
     prof_begin(ctx, kPhShadow, s);
-    k_lambda_part<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u, part,
+    launch_pdl(k_lambda_part, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u, part,
                                           scal + S_LAM, scal, tk);
     fin();
-    k_charges<<<G, kThreads, 0, s>>>(n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn, scal,
+    launch_pdl(k_charges, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn, scal,
                                      st->q, ctx->fvec, part, scal + S_CHG, tk);
     fin();
     prof_end(ctx, s);
@@ -544,12 +555,12 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     // 4. forces, w_1, r_1 (and, when m > 1, the start of w_2)
     const bool adaptive = ctx->p.krylov_tol > 0.0;
     prof_begin(ctx, kPhShadow, s);
-    k_forces_w1<<<G, kThreads, 0, s>>>(n, st->q, nn, ctx->E_n, ctx->E_f,
+    launch_pdl(k_forces_w1, G, kThreads, 0, s, n, st->q, nn, ctx->E_n, ctx->E_f,
                                        has_short(ctx) ? ctx->F_short : nullptr,
                                        ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb, ctx->phi, part,
                                        scal + S_MU, tk);
     fin();
-    k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
+    launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
                                       m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part,
                                       scal + S_DOT, tk);
     ctx->launches++;
@@ -566,7 +577,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         (void)nO;
         *done = true;
         if (!adaptive || k == m) return QEQ_OK;
-        k_ls_residual<<<G, kThreads, 0, s>>>(n, k, ctx->Rb, ctx->fvec, scal, part, scal + S_RES, tk);
+        launch_pdl(k_ls_residual, G, kThreads, 0, s, n, k, ctx->Rb, ctx->fvec, scal, part, scal + S_RES, tk);
         fin();
         double hv[2] = {0.0, 0.0};  // |R c - f|^2 and |f|^2
         cudaError_t e = cudaMemcpyAsync(&hv[0], scal + S_RES, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -592,21 +603,21 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
-            k_axpy_dot<<<G, kThreads, 0, s>>>(n, scal, wj, Wk, znext, j + 1 == k, part, scal + S_DOT,
+            launch_pdl(k_axpy_dot, G, kThreads, 0, s, n, scal, wj, Wk, znext, j + 1 == k, part, scal + S_DOT,
                                               tk);
             fin();
         }
-        k_normalize<<<G, kThreads, 0, s>>>(n, scal, Wk);
+        launch_pdl(k_normalize, G, kThreads, 0, s, n, scal, Wk);
         ctx->launches++;
         prof_end(ctx, s);
         rc = coulomb_apply_impl(ctx, st->R, Wk, prm->sigma, ctx->phi, nullptr, nullptr, nullptr,
                                 false, s, true);
         if (rc) return rc;
         prof_begin(ctx, kPhShadow, s);
-        k_mu_part<<<G, kThreads, 0, s>>>(n, ctx->phi, ctx->inv_u, part, scal + S_MU, tk);
+        launch_pdl(k_mu_part, G, kThreads, 0, s, n, ctx->phi, ctx->inv_u, part, scal + S_MU, tk);
         fin();
         const bool more = k + 1 < m;
-        k_jacobian<<<G, kThreads, 0, s>>>(n, ctx->phi, Wk, ctx->inv_u, scal, ctx->Rb + (size_t)k * n,
+        launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, Wk, ctx->inv_u, scal, ctx->Rb + (size_t)k * n,
                                           more ? ctx->Wb + (size_t)(k + 1) * n : nullptr, ctx->Wb,
                                           part, scal + S_DOT, tk);
         ctx->launches++;
@@ -630,7 +641,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
 int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    k_advance<<<ctx->red_grid, kThreads, 0, s>>>(
+    launch_pdl(k_advance, ctx->red_grid, kThreads, 0, s, 
         n, ctx->p.dt, ctx->p.mass_unit, dissipation(ctx->p.dissipation_k), prm->mass, st->F,
         st->Kf, st->R, st->V, st->n_hist, ctx->inv_m, ctx->R_build, ctx->part,
         ctx->scal + kScMaxDisp2, ctx->ticket);
@@ -660,7 +671,7 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
     const int rank = kf && st->Kf ? ctx->kf_rank : 0;
-    k_finish<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
+    launch_pdl(k_finish, ctx->red_grid, kThreads, 0, s, n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
                                              ctx->inv_m, st->F, st->V, rank, ctx->Wb, st->Kf,
                                              ctx->part, ctx->scal, st->energies, ctx->ticket);
     prof_end(ctx, s);
