@@ -373,7 +373,7 @@ struct qeq_ctx {
     qeq_short_fn short_fn = nullptr;  // user short-range model (qeq_set_short_range)
     void *short_user = nullptr;
     double *inv_u = nullptr;   // [N] 1 / u of the current evaluation
-    double *inv_m = nullptr;   // [N] 1 / (m * mass_unit) of the current step
+    double *half_kick = nullptr;  // [N] dt / (2 m mass_unit) of the current step
 
     // ---- GMRES solver of the regular QEq (solver.cu) ----
     double *gmV = nullptr;     // [restart + 1][N + 1] Arnoldi basis

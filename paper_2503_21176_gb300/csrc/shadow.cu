@@ -374,6 +374,9 @@ __global__ void k_ls_residual(int n, int m, const double *__restrict__ Rb,
 struct Dissipation {
     double kappa, alpha;
     double c[kMaxHist];
+    // the update's coefficients of n_{t-k} with 2 n_t - n_{t-1} folded in:
+    // w_0 = 2 + alpha c_0, w_1 = alpha c_1 - 1, w_k = alpha c_k (k >= 2)
+    double w[kMaxHist];
     int kd;
 };
 
@@ -394,53 +397,69 @@ Dissipation dissipation(int kd) {
         case 6: d.kappa = 1.84; d.alpha = 5.5e-3; c = c6; break;
         default: d.kappa = 1.86; d.alpha = 1.6e-3; c = c7; break;
     }
-    for (int k = 0; k <= kd; ++k) d.c[k] = c[k];
+    for (int k = 0; k <= kd; ++k) {
+        d.c[k] = c[k];
+        d.w[k] = d.alpha * c[k] + (k == 0 ? 2.0 : (k == 1 ? -1.0 : 0.0));
+    }
     return d;
 }
 
-// Half kick + drift of R; n_{t+1} = 2 n_t - n_{t-1} - kappa Kf + alpha sum_k c_k n_{t-k};
-// history shifted in place (each thread owns one atom's column).  The same pass
-// finds the largest squared displacement since the last neighbour build (the
-// skin check) into *max_d2.
-__global__ void k_advance(int n, double dt, double mass_unit, Dissipation dis,
+// |x| as a float truncated toward zero (at most 2^-23 low) on the integer pipe,
+// +inf from 2^100 up and for infinities and NaNs: the skin check's
+// displacement components.
+__device__ __forceinline__ float disp_f32(double x) {
+    const int hi = __double2hiint(x) & 0x7fffffff;
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ex = (hi >> 20) - 1023 + 127;
+    if (ex <= 0) return 0.0f;
+    if (ex >= 227) return __int_as_float(0x7f800000);
+    return __int_as_float((ex << 23) | ((hi & 0xFFFFF) << 3) | (int)(lo >> 29));
+}
+
+// Half kick + drift of R; n_{t+1} = 2 n_t - n_{t-1} - kappa Kf + alpha sum_k c_k n_{t-k}
+// (with the folded coefficients w); history shifted in place (each thread owns
+// one atom's column).  half_kick = dt / (2 m) is written for the finish.  The
+// same pass finds the largest squared displacement since the last neighbour
+// build (the skin check) into *max_d2: the FP64 differences truncated to FP32 and
+// the FP32 sum scaled by 1 + 2^-20, so it is never below the exact value and a
+// rebuild is never late (GB300 runs FP64 at 1/64 of the FP32 rate).
+__global__ void k_advance(int n, double dt, double half_dt, double mass_unit, Dissipation dis,
                           const double *__restrict__ mass, const double *__restrict__ F,
                           const double *__restrict__ Kf, double *__restrict__ R,
                           double *__restrict__ V, double *__restrict__ hist,
-                          double *__restrict__ inv_m_out, const double *__restrict__ R0,
+                          double *__restrict__ half_kick, const double *__restrict__ R0,
                           double *__restrict__ part, double *__restrict__ max_d2,
                           unsigned int *__restrict__ ticket) {
     pdl_begin();
-    double mx = 0.0;
+    float mx = 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double inv_m = recip_nr(mass[i] * mass_unit);
-        inv_m_out[i] = inv_m;
-        double d2 = 0.0;
+        const double hk = half_dt * recip_nr(mass[i] * mass_unit);
+        half_kick[i] = hk;
+        float d2 = 0.0f;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double vi = V[3 * (size_t)i + d] + 0.5 * dt * F[3 * (size_t)i + d] * inv_m;
+            const double vi = fma(F[3 * (size_t)i + d], hk, V[3 * (size_t)i + d]);
             V[3 * (size_t)i + d] = vi;
-            const double r = R[3 * (size_t)i + d] + dt * vi;
+            const double r = fma(dt, vi, R[3 * (size_t)i + d]);
             R[3 * (size_t)i + d] = r;
-            const double dd = r - R0[3 * (size_t)i + d];
-            d2 += dd * dd;
+            const float dd = disp_f32(r - R0[3 * (size_t)i + d]);
+            d2 = fmaf(dd, dd, d2);
         }
-        if (!(d2 == d2)) d2 = INFINITY;
-        mx = fmax(mx, d2);
+        mx = fmaxf(mx, d2 * (1.0f + 0x1p-20f));
         double h[kMaxHist];
         for (int k = 0; k <= dis.kd; ++k) h[k] = hist[(size_t)k * n + i];
-        double acc = 0.0;
-        for (int k = 0; k <= dis.kd; ++k) acc += dis.c[k] * h[k];
-        const double nn = 2.0 * h[0] - h[1] - dis.kappa * Kf[i] + dis.alpha * acc;
+        double nn = -dis.kappa * Kf[i];
+        for (int k = 0; k <= dis.kd; ++k) nn = fma(dis.w[k], h[k], nn);
         for (int k = dis.kd; k >= 1; --k) hist[(size_t)k * n + i] = h[k - 1];
         hist[i] = nn;
     }
-    max_last_block(mx, part, max_d2, ticket);
+    max_last_block(f32_to_f64_exact(mx), part, max_d2, ticket);
 }
 
 // optional second half kick, then partial of the kinetic energy; with kf_rank > 0
 // also the kernel update Kf = W c of the evaluation (c from the normal equations)
-__global__ void k_finish(int n, double dt, double mass_unit, bool kick,
-                         const double *__restrict__ mass, const double *__restrict__ inv_m,
+__global__ void k_finish(int n, double half_mass_unit, bool kick,
+                         const double *__restrict__ mass, const double *__restrict__ half_kick,
                          const double *__restrict__ F, double *__restrict__ V, int kf_rank,
                          const double *__restrict__ Wb, double *__restrict__ Kf,
                          double *__restrict__ part, double *__restrict__ scal,
@@ -454,18 +473,17 @@ __global__ void k_finish(int n, double dt, double mass_unit, bool kick,
             for (int a = 0; a < kf_rank; ++a) kfi += c[a] * Wb[(size_t)a * n + i];
             Kf[i] = kfi;
         }
-        const double mi = mass[i] * mass_unit;
         double v2 = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             double vi = V[3 * (size_t)i + d];
             if (kick) {
-                vi += 0.5 * dt * F[3 * (size_t)i + d] * inv_m[i];
+                vi = fma(F[3 * (size_t)i + d], half_kick[i], vi);
                 V[3 * (size_t)i + d] = vi;
             }
-            v2 += vi * vi;
+            v2 = fma(vi, vi, v2);
         }
-        ke += 0.5 * mi * v2;
+        ke = fma(half_mass_unit * mass[i], v2, ke);
     }
     double vals[1] = {ke};
     block_sum<1>(vals);
@@ -494,7 +512,7 @@ int shadow_alloc(qeq_ctx *ctx) {
         {(void **)&ctx->Wb, sizeof(double) * (size_t)m * n},
         {(void **)&ctx->Rb, sizeof(double) * (size_t)m * n},
         {(void **)&ctx->inv_u, sizeof(double) * n},
-        {(void **)&ctx->inv_m, sizeof(double) * n},
+        {(void **)&ctx->half_kick, sizeof(double) * n},
     };
     for (auto &b : bufs) {
         int rc = dev_alloc(ctx, b.ptr, b.bytes);
@@ -509,7 +527,7 @@ int shadow_alloc(qeq_ctx *ctx) {
 
 void shadow_free(qeq_ctx *ctx) {
     void *ptrs[] = {ctx->v_n, ctx->E_n, ctx->phi, ctx->E_f, ctx->fvec, ctx->Wb,
-                    ctx->Rb,  ctx->F_short, ctx->inv_u, ctx->inv_m};
+                    ctx->Rb,  ctx->F_short, ctx->inv_u, ctx->half_kick};
     for (void *p : ptrs) dev_free(ctx, p);
 }
 
@@ -541,11 +559,11 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     if (rc) return rc;
     // 2. lambda and q[n] (Eq. diag_linear_qeq); 1/u kept for the rest of the evaluation
     prof_begin(ctx, kPhShadow, s);
-    launch_pdl(k_lambda_part, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u, part,
-                                          scal + S_LAM, scal, tk);
+    launch_pdl(k_lambda_part, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u,
+               part, scal + S_LAM, scal, tk);
     fin();
-    launch_pdl(k_charges, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn, scal,
-                                     st->q, ctx->fvec, part, scal + S_CHG, tk);
+    launch_pdl(k_charges, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn,
+               scal, st->q, ctx->fvec, part, scal + S_CHG, tk);
     fin();
     prof_end(ctx, s);
     // 3. Phi f, E[f]
@@ -556,13 +574,11 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     const bool adaptive = ctx->p.krylov_tol > 0.0;
     prof_begin(ctx, kPhShadow, s);
     launch_pdl(k_forces_w1, G, kThreads, 0, s, n, st->q, nn, ctx->E_n, ctx->E_f,
-                                       has_short(ctx) ? ctx->F_short : nullptr,
-                                       ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb, ctx->phi, part,
-                                       scal + S_MU, tk);
+               has_short(ctx) ? ctx->F_short : nullptr, ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb,
+               ctx->phi, part, scal + S_MU, tk);
     fin();
     launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
-                                      m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part,
-                                      scal + S_DOT, tk);
+               m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part, scal + S_DOT, tk);
     ctx->launches++;
     prof_end(ctx, s);
     // normal equations, m x m solve and energies for rank k; with a tolerance, the
@@ -577,7 +593,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         (void)nO;
         *done = true;
         if (!adaptive || k == m) return QEQ_OK;
-        launch_pdl(k_ls_residual, G, kThreads, 0, s, n, k, ctx->Rb, ctx->fvec, scal, part, scal + S_RES, tk);
+        launch_pdl(k_ls_residual, G, kThreads, 0, s, n, k, ctx->Rb, ctx->fvec, scal, part,
+                   scal + S_RES, tk);
         fin();
         double hv[2] = {0.0, 0.0};  // |R c - f|^2 and |f|^2
         cudaError_t e = cudaMemcpyAsync(&hv[0], scal + S_RES, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -603,8 +620,8 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
-            launch_pdl(k_axpy_dot, G, kThreads, 0, s, n, scal, wj, Wk, znext, j + 1 == k, part, scal + S_DOT,
-                                              tk);
+            launch_pdl(k_axpy_dot, G, kThreads, 0, s, n, scal, wj, Wk, znext, j + 1 == k, part,
+                       scal + S_DOT, tk);
             fin();
         }
         launch_pdl(k_normalize, G, kThreads, 0, s, n, scal, Wk);
@@ -617,9 +634,9 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         launch_pdl(k_mu_part, G, kThreads, 0, s, n, ctx->phi, ctx->inv_u, part, scal + S_MU, tk);
         fin();
         const bool more = k + 1 < m;
-        launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, Wk, ctx->inv_u, scal, ctx->Rb + (size_t)k * n,
-                                          more ? ctx->Wb + (size_t)(k + 1) * n : nullptr, ctx->Wb,
-                                          part, scal + S_DOT, tk);
+        launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, Wk, ctx->inv_u, scal,
+                   ctx->Rb + (size_t)k * n, more ? ctx->Wb + (size_t)(k + 1) * n : nullptr, ctx->Wb,
+                   part, scal + S_DOT, tk);
         ctx->launches++;
         prof_end(ctx, s);
         m_used = k + 1;
@@ -641,10 +658,10 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
 int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    launch_pdl(k_advance, ctx->red_grid, kThreads, 0, s, 
-        n, ctx->p.dt, ctx->p.mass_unit, dissipation(ctx->p.dissipation_k), prm->mass, st->F,
-        st->Kf, st->R, st->V, st->n_hist, ctx->inv_m, ctx->R_build, ctx->part,
-        ctx->scal + kScMaxDisp2, ctx->ticket);
+    launch_pdl(k_advance, ctx->red_grid, kThreads, 0, s, n, ctx->p.dt, 0.5 * ctx->p.dt,
+               ctx->p.mass_unit, dissipation(ctx->p.dissipation_k), prm->mass, st->F, st->Kf, st->R,
+               st->V, st->n_hist, ctx->half_kick, ctx->R_build, ctx->part, ctx->scal + kScMaxDisp2,
+               ctx->ticket);
     prof_end(ctx, s);
     ctx->launches++;
     return cuda_check(ctx, cudaGetLastError(), "advance launch");
@@ -671,9 +688,9 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
     const int rank = kf && st->Kf ? ctx->kf_rank : 0;
-    launch_pdl(k_finish, ctx->red_grid, kThreads, 0, s, n, ctx->p.dt, ctx->p.mass_unit, kick, prm->mass,
-                                             ctx->inv_m, st->F, st->V, rank, ctx->Wb, st->Kf,
-                                             ctx->part, ctx->scal, st->energies, ctx->ticket);
+    launch_pdl(k_finish, ctx->red_grid, kThreads, 0, s, n, 0.5 * ctx->p.mass_unit, kick, prm->mass,
+               ctx->half_kick, st->F, st->V, rank, ctx->Wb, st->Kf, ctx->part, ctx->scal,
+               st->energies, ctx->ticket);
     prof_end(ctx, s);
     ctx->launches += 1;
     return cuda_check(ctx, cudaGetLastError(), "shadow finish launch");

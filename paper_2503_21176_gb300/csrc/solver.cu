@@ -384,16 +384,16 @@ int gmres_solve(qeq_ctx *ctx, const double *R, const double *chi, const double *
 
 namespace {
 
-// Velocity-Verlet half kick and drift; 1 / (m mass_unit) kept for the second kick.
+// Velocity-Verlet half kick and drift; dt / (2 m mass_unit) kept for the second kick.
 __global__ void k_kick_drift(int n, double dt, double mass_unit, const double *__restrict__ mass,
                              const double *__restrict__ F, double *__restrict__ R,
-                             double *__restrict__ V, double *__restrict__ inv_m_out) {
+                             double *__restrict__ V, double *__restrict__ half_kick) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double inv_m = 1.0 / (mass[i] * mass_unit);
-        inv_m_out[i] = inv_m;
+        const double hk = 0.5 * dt / (mass[i] * mass_unit);
+        half_kick[i] = hk;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double vi = V[3 * (size_t)i + d] + 0.5 * dt * F[3 * (size_t)i + d] * inv_m;
+            const double vi = fma(F[3 * (size_t)i + d], hk, V[3 * (size_t)i + d]);
             V[3 * (size_t)i + d] = vi;
             R[3 * (size_t)i + d] += dt * vi;
         }
@@ -406,7 +406,7 @@ int bomd_advance(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaS
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
     k_kick_drift<<<ctx->red_grid, kThreads, 0, s>>>(n, ctx->p.dt, ctx->p.mass_unit, prm->mass, st->F,
-                                                 st->R, st->V, ctx->inv_m);
+                                                 st->R, st->V, ctx->half_kick);
     prof_end(ctx, s);
     ctx->launches++;
     double d2 = 0.0;
