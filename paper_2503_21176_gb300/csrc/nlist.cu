@@ -231,10 +231,11 @@ __device__ __noinline__ bool band_keep(const EmitArgs *ap, int code, const doubl
     return d2 < a.rl2;
 }
 
-// The test pass of one lane, as a double loop: over the row's candidate cells
-// (one table entry and one image shift per cell, the shift folded into the
-// row's own position), and over each cell's atoms with stride kEmitLanes (lane
-// s takes atoms s, s + 4, ...).  The decision is FP32 outside the band [lo, hi]
+// The test pass of one lane, as a double loop: over the row's candidate ranges
+// (its cell's neighbour cells, merged where they continue one sorted range; one
+// table entry and one image shift per range, the shift folded into the row's
+// own position), and over each range's atoms with stride kEmitLanes (lane s
+// takes atoms s, s + 4, ...).  The decision is FP32 outside the band [lo, hi]
 // and FP64 with a fixed operation order inside it; the distance class comes
 // from the FP32 d^2.  A kept entry goes, with its class in bits 16-17, to the
 // lane's slots 4 m + s of the 32-bit scratch list (m < cap = width / 4), and the
@@ -294,6 +295,7 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
     __shared__ int t_start[kMaxTileBricks], t_base[kMaxTileBricks], t_code[kMaxTileBricks], t_total;
     __shared__ int4 ctab[kMaxBrickCells][kMaxTileBricks];
     __shared__ float4 shtab[kMaxTileBricks];  // image shift s L of each code (sx + 2) * 25 + ...
+    __shared__ int nrange[kMaxBrickCells];  // table entries (ranges) of each cell
     __shared__ EmitArgs sargs;  // the band decision's copy of the arguments
     if (threadIdx.x == 0) sargs = a;
     // nchunk blocks share a brick: chunk c takes the brick's groups of 32 rows
@@ -337,6 +339,23 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
                                  (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2));
     }
     __syncthreads();
+    // each cell's table as ranges: consecutive entries that continue one sorted
+    // range in the same tile brick under the same image shift merge, and empty
+    // cells drop out
+    if (threadIdx.x < g.bvol) {
+        int4 *row = ctab[threadIdx.x];
+        int m = 0;
+        for (int k = 0; k < ncand; ++k) {
+            const int4 e = row[k];
+            if (e.x == e.y) continue;
+            if (m > 0 && row[m - 1].y == e.x && row[m - 1].z == e.z && row[m - 1].w == e.w)
+                row[m - 1].y = e.y;
+            else
+                row[m++] = e;
+        }
+        nrange[threadIdx.x] = m;
+    }
+    __syncthreads();
     if (t_total > kMaxTileAtoms) {
         if (chunk == 0)
             for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) cnt[i] = 0;
@@ -354,9 +373,9 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
         const int i = i0 + (act ? r : 0);
         int c[3] = {0, 0, 0};
         if (act) {
-            const int4 *tab = ctab[cell_s[i] - (int)(b * g.bvol)];
-            emit_cells(a, &sargs, i, s, tab, shtab, ncand, xs32[i], xs64, xs32, cap, c, scr, t_total,
-                       flags);
+            const int lc = cell_s[i] - (int)(b * g.bvol);
+            emit_cells(a, &sargs, i, s, ctab[lc], shtab, nrange[lc], xs32[i], xs64, xs32, cap, c, scr,
+                       t_total, flags);
         }
         const int mine = c[0] + c[1] + c[2];
         // this lane's first row slot in each class: the classes in order, and in
