@@ -364,7 +364,8 @@ int ensure_step_graph(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, 
                            prm->chi, prm->eta, prm->sigma, prm->mass, ctx->nbr, ctx->tile_scratch,
                            nullptr};
     bool same = ctx->step_exec && ctx->graph_width == ctx->width &&
-                ctx->graph_tile == ctx->tile_cap && ctx->graph_rows == ctx->rows_cap;
+                ctx->graph_tile == ctx->tile_cap && ctx->graph_rows == ctx->rows_cap &&
+                ctx->graph_pdl == ctx->pdl;
     for (int k = 0; k < 14 && same; ++k) same = key[k] == ctx->graph_key[k];
     if (same) return QEQ_OK;
     drop_graph(ctx);
@@ -391,6 +392,7 @@ int ensure_step_graph(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, 
     ctx->graph_width = ctx->width;
     ctx->graph_tile = ctx->tile_cap;
     ctx->graph_rows = ctx->rows_cap;
+    ctx->graph_pdl = ctx->pdl;
     ctx->graph_launches = ctx->launches - l0;
     ctx->launches = l0;
     ctx->applies = a0;

@@ -122,8 +122,12 @@ QEQ_API int qeq_batch_step(qeq_batch *b, int32_t n, qeq_ctx *const *ctxs, const 
     }
     int rc = reserve_host(b, n);
     if (rc) return rc;
-    // 1. every member's kick, drift and n update, and its displacement check
+    // 1. every member's kick, drift and n update, and its displacement check.
+    //    A member's kernels run beside the other members' (parallel branches of
+    //    the parent graph), so none waits on the device for its predecessor
+    //    (pdl off: its step graph is captured again without the attribute)
     for (int32_t k = 0; k < n; ++k) {
+        ctxs[k]->pdl = false;
         rc = shadow_advance_queue(ctxs[k], &prms[k], &sts[k], s);
         if (rc) return rc;
         cudaMemcpyAsync(&b->h_d2[k], ctxs[k]->scal + kScMaxDisp2, sizeof(double),

@@ -400,6 +400,8 @@ struct qeq_ctx {
     int64_t graph_replays = 0;       // step graph launches since creation
     bool use_graphs = true;
     int nl_method = QEQ_NL_BRICK;  // neighbour search (qeq_set_neighbor_method)
+    bool pdl = true;       // shadow-step kernels by programmatic dependent launch
+    bool graph_pdl = true; // ... as the captured step graph launches them
 
     // ---- tracing ----
     qeq::Profiler prof;
@@ -514,18 +516,24 @@ __device__ __forceinline__ double warp_max(double v) {
 // kernel calls it first, before any access to memory; without the launch
 // attribute both instructions do nothing.  Inside a captured graph the
 // dependency becomes a programmatic edge.  The shadow-step kernels use it (a
-// chain of short grid-stride kernels: about 0.9 us per boundary).  The Coulomb
-// apply kernels do not: there the mesh chain runs on a side stream beside the
-// real-space kernel, and the early-launched successor's waiting blocks took SM
-// resources from it (the step graph ran 85 us slower).
+// chain of short grid-stride kernels: about 0.9 us per boundary) when their
+// context steps on its own (pdl true).  Where other work runs beside them the
+// early-launched successor's waiting blocks take SM resources from it: the
+// Coulomb apply kernels, whose mesh chain runs on a side stream beside the
+// real-space kernel, do not use it (the step graph ran 85 us slower), nor do
+// the members of a batched step, whose evaluations are parallel branches of
+// one graph (FP64 serving steps ran 5% slower).
 __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+#ifndef QEQ_PDL
+#define QEQ_PDL 1  // 0: the same kernels launched without the attribute
+#endif
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, Args... args) {
+inline cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                              size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr.val.programmaticStreamSerializationAllowed = 1;
@@ -535,7 +543,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = QEQ_PDL && pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 

@@ -332,19 +332,19 @@ __global__ void k_normal_part(int n, const double *__restrict__ Rb, const double
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-void launch_normal_part(int grid, int m, int n, const double *Rb, const double *f, double *part,
-                        double q_tot, int applies, double *scal, double *energies,
+void launch_normal_part(bool pdl, int grid, int m, int n, const double *Rb, const double *f,
+                        double *part, double q_tot, int applies, double *scal, double *energies,
                         unsigned int *ticket, cudaStream_t s) {
 #define QEQ_NP_ARGS n, Rb, f, part, q_tot, applies, scal, energies, ticket
     switch (m) {
-        case 1: launch_pdl(k_normal_part<1>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        case 2: launch_pdl(k_normal_part<2>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        case 3: launch_pdl(k_normal_part<3>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        case 4: launch_pdl(k_normal_part<4>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        case 5: launch_pdl(k_normal_part<5>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        case 6: launch_pdl(k_normal_part<6>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        case 7: launch_pdl(k_normal_part<7>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
-        default: launch_pdl(k_normal_part<8>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 1: launch_pdl(pdl, k_normal_part<1>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 2: launch_pdl(pdl, k_normal_part<2>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 3: launch_pdl(pdl, k_normal_part<3>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 4: launch_pdl(pdl, k_normal_part<4>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 5: launch_pdl(pdl, k_normal_part<5>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 6: launch_pdl(pdl, k_normal_part<6>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        case 7: launch_pdl(pdl, k_normal_part<7>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
+        default: launch_pdl(pdl, k_normal_part<8>, grid, kThreads, 0, s, QEQ_NP_ARGS); break;
     }
 #undef QEQ_NP_ARGS
 }
@@ -559,10 +559,10 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     if (rc) return rc;
     // 2. lambda and q[n] (Eq. diag_linear_qeq); 1/u kept for the rest of the evaluation
     prof_begin(ctx, kPhShadow, s);
-    launch_pdl(k_lambda_part, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u,
+    launch_pdl(ctx->pdl, k_lambda_part, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->v_n, ctx->inv_u,
                part, scal + S_LAM, scal, tk);
     fin();
-    launch_pdl(k_charges, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn,
+    launch_pdl(ctx->pdl, k_charges, G, kThreads, 0, s, n, ctx->p.q_tot, prm->chi, u, ctx->inv_u, ctx->v_n, nn,
                scal, st->q, ctx->fvec, part, scal + S_CHG, tk);
     fin();
     prof_end(ctx, s);
@@ -573,11 +573,11 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     // 4. forces, w_1, r_1 (and, when m > 1, the start of w_2)
     const bool adaptive = ctx->p.krylov_tol > 0.0;
     prof_begin(ctx, kPhShadow, s);
-    launch_pdl(k_forces_w1, G, kThreads, 0, s, n, st->q, nn, ctx->E_n, ctx->E_f,
+    launch_pdl(ctx->pdl, k_forces_w1, G, kThreads, 0, s, n, st->q, nn, ctx->E_n, ctx->E_f,
                has_short(ctx) ? ctx->F_short : nullptr, ctx->fvec, ctx->inv_u, scal, st->F, ctx->Wb,
                ctx->phi, part, scal + S_MU, tk);
     fin();
-    launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
+    launch_pdl(ctx->pdl, k_jacobian, G, kThreads, 0, s, n, ctx->phi, ctx->Wb, ctx->inv_u, scal, ctx->Rb,
                m > 1 ? ctx->Wb + (size_t)n : nullptr, ctx->Wb, part, scal + S_DOT, tk);
     ctx->launches++;
     prof_end(ctx, s);
@@ -586,14 +586,14 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
     auto solve_rank = [&](int k, bool *done) -> int {
         const int nO = k * (k + 1) / 2;
         prof_begin(ctx, kPhShadow, s);
-        launch_normal_part(ctx->red_grid, k, n, ctx->Rb, ctx->fvec, part, ctx->p.q_tot, k + 1, scal,
+        launch_normal_part(ctx->pdl, ctx->red_grid, k, n, ctx->Rb, ctx->fvec, part, ctx->p.q_tot, k + 1, scal,
                            st->energies, tk, s);
         ctx->launches += 1;
         prof_end(ctx, s);
         (void)nO;
         *done = true;
         if (!adaptive || k == m) return QEQ_OK;
-        launch_pdl(k_ls_residual, G, kThreads, 0, s, n, k, ctx->Rb, ctx->fvec, scal, part,
+        launch_pdl(ctx->pdl, k_ls_residual, G, kThreads, 0, s, n, k, ctx->Rb, ctx->fvec, scal, part,
                    scal + S_RES, tk);
         fin();
         double hv[2] = {0.0, 0.0};  // |R c - f|^2 and |f|^2
@@ -620,21 +620,21 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
         for (int j = 0; j < k; ++j) {
             const double *wj = ctx->Wb + (size_t)j * n;
             const double *znext = (j + 1 < k) ? ctx->Wb + (size_t)(j + 1) * n : Wk;
-            launch_pdl(k_axpy_dot, G, kThreads, 0, s, n, scal, wj, Wk, znext, j + 1 == k, part,
+            launch_pdl(ctx->pdl, k_axpy_dot, G, kThreads, 0, s, n, scal, wj, Wk, znext, j + 1 == k, part,
                        scal + S_DOT, tk);
             fin();
         }
-        launch_pdl(k_normalize, G, kThreads, 0, s, n, scal, Wk);
+        launch_pdl(ctx->pdl, k_normalize, G, kThreads, 0, s, n, scal, Wk);
         ctx->launches++;
         prof_end(ctx, s);
         rc = coulomb_apply_impl(ctx, st->R, Wk, prm->sigma, ctx->phi, nullptr, nullptr, nullptr,
                                 false, s, true);
         if (rc) return rc;
         prof_begin(ctx, kPhShadow, s);
-        launch_pdl(k_mu_part, G, kThreads, 0, s, n, ctx->phi, ctx->inv_u, part, scal + S_MU, tk);
+        launch_pdl(ctx->pdl, k_mu_part, G, kThreads, 0, s, n, ctx->phi, ctx->inv_u, part, scal + S_MU, tk);
         fin();
         const bool more = k + 1 < m;
-        launch_pdl(k_jacobian, G, kThreads, 0, s, n, ctx->phi, Wk, ctx->inv_u, scal,
+        launch_pdl(ctx->pdl, k_jacobian, G, kThreads, 0, s, n, ctx->phi, Wk, ctx->inv_u, scal,
                    ctx->Rb + (size_t)k * n, more ? ctx->Wb + (size_t)(k + 1) * n : nullptr, ctx->Wb,
                    part, scal + S_DOT, tk);
         ctx->launches++;
@@ -658,7 +658,7 @@ int shadow_evaluate(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cu
 int shadow_advance_queue(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, cudaStream_t s) {
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
-    launch_pdl(k_advance, ctx->red_grid, kThreads, 0, s, n, ctx->p.dt, 0.5 * ctx->p.dt,
+    launch_pdl(ctx->pdl, k_advance, ctx->red_grid, kThreads, 0, s, n, ctx->p.dt, 0.5 * ctx->p.dt,
                ctx->p.mass_unit, dissipation(ctx->p.dissipation_k), prm->mass, st->F, st->Kf, st->R,
                st->V, st->n_hist, ctx->half_kick, ctx->R_build, ctx->part, ctx->scal + kScMaxDisp2,
                ctx->ticket);
@@ -688,7 +688,7 @@ int shadow_finish(qeq_ctx *ctx, const qeq_md_params *prm, qeq_md_state *st, bool
     const int n = (int)ctx->n;
     prof_begin(ctx, kPhIntegrate, s);
     const int rank = kf && st->Kf ? ctx->kf_rank : 0;
-    launch_pdl(k_finish, ctx->red_grid, kThreads, 0, s, n, 0.5 * ctx->p.mass_unit, kick, prm->mass,
+    launch_pdl(ctx->pdl, k_finish, ctx->red_grid, kThreads, 0, s, n, 0.5 * ctx->p.mass_unit, kick, prm->mass,
                ctx->half_kick, st->F, st->V, rank, ctx->Wb, st->Kf, ctx->part, ctx->scal,
                st->energies, ctx->ticket);
     prof_end(ctx, s);

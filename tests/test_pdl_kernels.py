@@ -19,7 +19,7 @@ def _sources():
 def _launched():
     names = set()
     for text in _sources().values():
-        for m in re.finditer(r"launch_pdl\(\s*(k_\w+)", text):
+        for m in re.finditer(r"launch_pdl\(\s*[^,()]+,\s*(k_\w+)", text):
             names.add(m.group(1))
     return names
 
