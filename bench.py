@@ -406,15 +406,22 @@ def serving_sample(device, n_requests=128, rate=200.0):
             "md_batching": st["md_batching"], "stage_ms_mean": st["stage_ms_mean"]}
 
 
-def e2e_steps(qg, md, steps, stream, device):
+def e2e_steps(qg, md, steps, stream, device, chunks=8):
     """Same step through the C ABI with the state kept in HOST memory: every step
     copies the whole MD state (R, V, F, K f, n history) and the per-atom parameters
     from pinned host memory to the device, runs the step, and copies the advanced
     state, the charges and the energies back to pinned host memory, all inside the
-    timed region.  The step works on one contiguous device buffer (ShadowMD.pack),
-    so each direction is one copy; two host buffers alternate (the results of step
-    k are the inputs of step k + 1), so the trajectory stays on the host with no
-    host copy."""
+    timed region.  The step works on one contiguous device buffer (ShadowMD.pack);
+    two host buffers alternate (the results of step k are the inputs of step
+    k + 1), so the trajectory lives on the host with no host copy.
+
+    The host link is full duplex, so the two directions overlap: the state goes
+    down (D2H) in `chunks` pieces on one copy stream and each piece comes back up
+    (H2D, as step k + 1's input) on another as soon as it has landed, behind an
+    event; the parameters go up once step k's compute is done.  Step k + 1 starts
+    when all of its input has arrived, so every byte still makes the round trip
+    through host memory.  The host reads step k's energies from its host buffer
+    (their copy is complete once step k + 1's skin check has synchronised)."""
     import torch
 
     dev_buf, (n_par, n_state, n_res) = md.pack()
@@ -422,22 +429,58 @@ def e2e_steps(qg, md, steps, stream, device):
     host[1][:n_par].copy_(host[0][:n_par])  # the parameters, in both buffers
     n_in, n_out = n_par + n_state, n_state + n_res
     h2d, d2h = 8 * n_in, 8 * n_out
+    # chunk bounds of the state region [n_par, n_par + n_state)
+    bounds = [n_par + (n_state * c) // chunks for c in range(chunks + 1)]
+    down = torch.cuda.Stream(device)
+    up = torch.cuda.Stream(device)
+    ev_down = [torch.cuda.Event() for _ in range(chunks)]
+    ev_comp = torch.cuda.Event()
+    ev_res = torch.cuda.Event()
+    ev_in = torch.cuda.Event()
+    e_idx = n_par + n_state + (n_res - md.energies.numel()) + 2  # energies[2]: total
+    totals = []
     with torch.cuda.stream(stream):
         torch.cuda.synchronize(device)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
+        dev_buf[:n_in].copy_(host[0][:n_in], non_blocking=True)  # step 0's input
         for k in range(steps):
             src, dst = host[k % 2], host[(k + 1) % 2]
-            dev_buf[:n_in].copy_(src[:n_in], non_blocking=True)
-            md.step(1, stream)
-            dst[n_par:].copy_(dev_buf[n_par:], non_blocking=True)
-            stream.synchronize()  # the caller reads the step's results on the host
+            md.step(1, stream)  # its skin check waited for this step's input
+            if k > 0:
+                totals.append(float(src[e_idx]))  # step k - 1's result, read on the host
+            ev_comp.record(stream)
+            down.wait_event(ev_comp)
+            with torch.cuda.stream(down):
+                for c in range(chunks):
+                    dst[bounds[c]:bounds[c + 1]].copy_(dev_buf[bounds[c]:bounds[c + 1]], non_blocking=True)
+                    ev_down[c].record(down)
+                dst[n_par + n_state:].copy_(dev_buf[n_par + n_state:], non_blocking=True)
+                ev_res.record(down)
+            if k + 1 < steps:
+                up.wait_event(ev_comp)
+                with torch.cuda.stream(up):
+                    dev_buf[:n_par].copy_(dst[:n_par], non_blocking=True)
+                    for c in range(chunks):
+                        up.wait_event(ev_down[c])
+                        dev_buf[bounds[c]:bounds[c + 1]].copy_(dst[bounds[c]:bounds[c + 1]],
+                                                                non_blocking=True)
+                    # the results (charges, energies) have landed too before step k + 1
+                    # starts, so its skin check tells the host they can be read
+                    up.wait_event(ev_res)
+                    ev_in.record(up)
+                stream.wait_event(ev_in)
+            else:
+                stream.wait_stream(down)
         t1.record(stream)
         torch.cuda.synchronize(device)
+    totals.append(float(host[steps % 2][e_idx]))
     ms = t0.elapsed_time(t1) / steps
     return {"value": round(1e3 / ms, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4)}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4),
+            "copies": f"D2H and H2D overlapped in {chunks} chunks on two copy streams",
+            "last_total_energy_eV": round(totals[-1], 6)}
 
 
 def roofline(res, precision, n_pairs_rc, peaks, pipes):
