@@ -926,10 +926,12 @@ k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
 #pragma unroll
     for (int k = 0; k < kSpreadThreads / 32; ++k) qsum += qsum_w[k];
     // scale = 2^(30 - e) with wmax qsum < 2^e (rounded up by 1e-5 relative)
-    int e2;
-    frexpf(fmaxf(qsum * w.wmax * 1.00001f, 1e-30f), &e2);
+    // frexp from the exponent bits: x = m 2^e2 with m in [0.5, 1)
+    const float xq = fmaxf(qsum * w.wmax * 1.00001f, 1e-30f);
+    const int e2 = ((__float_as_int(xq) >> 23) & 0xff) - 126;
     const int sh = min(126, 30 - e2);
-    const float scale = ldexpf(1.f, sh);
+    const float scale = __int_as_float((127 + sh) << 23);
+    const float unscale = __int_as_float((127 - sh) << 23);
     for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
         const int4 bs = sbase[i];
         const float4 f = sfrac[i];
@@ -956,16 +958,27 @@ k_spread_brick(SpreadWin w, BrickGeom g, const int32_t *__restrict__ cell_start,
         }
     }
     __syncthreads();
-    // flush: chunks of 4 z-points of each window row, back to FP32 (x 2^-sh)
+    // flush: chunks of 4 z-points of each window row, back to FP32 (x 2^-sh).
+    // The chunk index t splits into (row, chunk) and the row into (ix, iy) by FP32
+    // reciprocals, exact for indices below 2^22 (the product's error stays below
+    // 0.5 / divisor; a window holds at most 12,288 points), and a window index
+    // wraps into the mesh with one conditional add or subtract (it lies in
+    // [-(P - 1), K + P - 1)): runtime integer divisions and remainders made most
+    // of this loop's instructions.
     const int nq = w.E2 / 4;
+    const float inv_nq = 1.0f / (float)nq, inv_e1 = 1.0f / (float)w.E1;
     for (int t = threadIdx.x; t < w.E0 * w.E1 * nq; t += blockDim.x) {
-        const int k = t % nq, row = t / nq;
-        const int iy = row % w.E1, ix = row / w.E1;
+        const int row = __float2int_rz(((float)t + 0.5f) * inv_nq);
+        const int k = t - row * nq;
+        const int ix = __float2int_rz(((float)row + 0.5f) * inv_e1);
+        const int iy = row - ix * w.E1;
         const int4 iv = *(const int4 *)(win + (size_t)row * w.E2 + 4 * k);
         if ((iv.x | iv.y | iv.z | iv.w) == 0) continue;
-        const float vv[4] = {ldexpf((float)iv.x, -sh), ldexpf((float)iv.y, -sh),
-                             ldexpf((float)iv.z, -sh), ldexpf((float)iv.w, -sh)};
-        const int mx = wrap_index(lo0 + ix, w.K0), my = wrap_index(lo1 + iy, w.K1);
+        const float vv[4] = {(float)iv.x * unscale, (float)iv.y * unscale,
+                             (float)iv.z * unscale, (float)iv.w * unscale};
+        int mx = lo0 + ix, my = lo1 + iy;
+        mx += mx < 0 ? w.K0 : (mx >= w.K0 ? -w.K0 : 0);
+        my += my < 0 ? w.K1 : (my >= w.K1 ? -w.K1 : 0);
         const int mz = lo2 + 4 * k;
         float *dst = mesh + ((size_t)mx * w.K1 + my) * w.K2;
         if (w.vec && mz >= 0 && mz + 4 <= w.K2) {
