@@ -322,18 +322,38 @@ k_emit(EmitArgs a, BrickGeom g, int nchunk, const double4_32a *__restrict__ xs64
     const int ncand = dx * dy * dz;
     const int bz = (int)(b % g.nb[2]), by = (int)((b / g.nb[2]) % g.nb[1]);
     const int bx = (int)(b / ((int64_t)g.nb[2] * g.nb[1]));
+    // Bricks are 1 or 2 cells per axis, so every division by B is a shift (lb =
+    // log2 B); the flat index splits by FP32 reciprocals (exact below 2^22); and
+    // with at least reach cells per axis a neighbour cell's image shift is -1, 0
+    // or 1 by comparison (fewer cells take the general floor division).  Runtime
+    // integer divisions made a sizeable part of the emit's instructions.
+    const int lb0 = g.B[0] - 1, lb1 = g.B[1] - 1, lb2 = g.B[2] - 1;
+    const bool near = a.ncx >= a.rx && a.ncy >= a.ry && a.ncz >= a.rz;
+    const float inv_ncand = 1.0f / (float)ncand, inv_yz = 1.0f / (float)(dy * dz),
+                inv_z = 1.0f / (float)dz;
     for (int t = threadIdx.x; t < g.bvol * ncand; t += blockDim.x) {
-        const int lc = t / ncand, kk = t - lc * ncand;
-        const int lz = lc % g.B[2], ly = (lc / g.B[2]) % g.B[1], lx = lc / (g.B[2] * g.B[1]);
-        const int cx = bx * g.B[0] + lx, cy = by * g.B[1] + ly, cz = bz * g.B[2] + lz;
-        const int ox = kk / (dy * dz) - a.rx, oy = (kk / dz) % dy - a.ry, oz = kk % dz - a.rz;
-        const int ux = cx + ox, sx = floor_div(ux, a.ncx), wx = ux - sx * a.ncx;
-        const int uy = cy + oy, sy = floor_div(uy, a.ncy), wy = uy - sy * a.ncy;
-        const int uz = cz + oz, sz = floor_div(uz, a.ncz), wz = uz - sz * a.ncz;
-        const int tx = floor_div(ux, g.B[0]) - bx + g.br[0];
-        const int ty = floor_div(uy, g.B[1]) - by + g.br[1];
-        const int tz = floor_div(uz, g.B[2]) - bz + g.br[2];
-        const int cn = cell_index(g, wx, wy, wz);
+        const int lc = __float2int_rz(((float)t + 0.5f) * inv_ncand), kk = t - lc * ncand;
+        const int lz = lc & lb2, ly = (lc >> lb2) & lb1, lx = lc >> (lb2 + lb1);
+        const int cx = (bx << lb0) + lx, cy = (by << lb1) + ly, cz = (bz << lb2) + lz;
+        const int qx = __float2int_rz(((float)kk + 0.5f) * inv_yz), rem = kk - qx * (dy * dz);
+        const int qy = __float2int_rz(((float)rem + 0.5f) * inv_z);
+        const int ux = cx + qx - a.rx, uy = cy + qy - a.ry, uz = cz + (rem - qy * dz) - a.rz;
+        int sx, sy, sz;
+        if (near) {
+            sx = ux < 0 ? -1 : (ux >= a.ncx ? 1 : 0);
+            sy = uy < 0 ? -1 : (uy >= a.ncy ? 1 : 0);
+            sz = uz < 0 ? -1 : (uz >= a.ncz ? 1 : 0);
+        } else {
+            sx = floor_div(ux, a.ncx);
+            sy = floor_div(uy, a.ncy);
+            sz = floor_div(uz, a.ncz);
+        }
+        const int wx = ux - sx * a.ncx, wy = uy - sy * a.ncy, wz = uz - sz * a.ncz;
+        const int tx = (ux >> lb0) - bx + g.br[0];
+        const int ty = (uy >> lb1) - by + g.br[1];
+        const int tz = (uz >> lb2) - bz + g.br[2];
+        const int cn = (int)(brick_index(g, wx >> lb0, wy >> lb1, wz >> lb2) * g.bvol +
+                             (((wx & lb0) << lb1 | (wy & lb1)) << lb2 | (wz & lb2)));
         ctab[lc][kk] = make_int4(cell_start[cn], cell_start[cn + 1],
                                  t_base[(tx * g.td[1] + ty) * g.td[2] + tz],
                                  (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2));
