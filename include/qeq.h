@@ -430,7 +430,12 @@ int qeq_set_short_range(qeq_ctx *ctx, qeq_short_fn fn, void *user);
  * callback, profiler on) are evaluated kernel by kernel on the same stream.
  * The batch caches that parent graph and rebuilds it only when the member list
  * (order included) or a member's captured step changes.  Each member runs the
- * kernels of its own qeq_shadow_step, so results equal n separate steps.
+ * kernels of its own qeq_shadow_step, so results equal n separate steps.  A
+ * context stepping on its own launches its shadow-step kernels with
+ * programmatic dependent launch (each scheduled while its predecessor
+ * finishes); from its first batched step on, a member launches them without
+ * it, since its evaluation runs beside the other members' (its step graph is
+ * captured again once).
  * `stream` must not be the legacy default stream; the members' earlier work
  * must be ordered before it (same stream, or an event).  A member appears at
  * most once.  Synchronises once (plus once per rebuilding member).
