@@ -406,7 +406,7 @@ def serving_sample(device, n_requests=128, rate=200.0):
             "md_batching": st["md_batching"], "stage_ms_mean": st["stage_ms_mean"]}
 
 
-def e2e_steps(qg, md, steps, stream, device, chunks=8):
+def e2e_steps(qg, md, steps, stream, device, chunks=8, warmup=3):
     """Same step through the C ABI with the state kept in HOST memory: every step
     copies the whole MD state (R, V, F, K f, n history) and the per-atom parameters
     from pinned host memory to the device, runs the step, and copies the advanced
@@ -421,7 +421,9 @@ def e2e_steps(qg, md, steps, stream, device, chunks=8):
     event; the parameters go up once step k's compute is done.  Step k + 1 starts
     when all of its input has arrived, so every byte still makes the round trip
     through host memory.  The host reads step k's energies from its host buffer
-    (their copy is complete once step k + 1's skin check has synchronised)."""
+    (their copy is complete once step k + 1's skin check has synchronised).
+    `warmup` steps of the same loop run untimed first (the step graph is
+    captured again for the packed buffer)."""
     import torch
 
     dev_buf, (n_par, n_state, n_res) = md.pack()
@@ -439,16 +441,14 @@ def e2e_steps(qg, md, steps, stream, device, chunks=8):
     ev_in = torch.cuda.Event()
     e_idx = n_par + n_state + (n_res - md.energies.numel()) + 2  # energies[2]: total
     totals = []
-    with torch.cuda.stream(stream):
-        torch.cuda.synchronize(device)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        dev_buf[:n_in].copy_(host[0][:n_in], non_blocking=True)  # step 0's input
-        for k in range(steps):
+
+    def run(first, count):
+        """Steps first .. first + count - 1 of the pipelined round trip."""
+        dev_buf[:n_in].copy_(host[first % 2][:n_in], non_blocking=True)  # the first input
+        for k in range(first, first + count):
             src, dst = host[k % 2], host[(k + 1) % 2]
             md.step(1, stream)  # its skin check waited for this step's input
-            if k > 0:
+            if k > first:
                 totals.append(float(src[e_idx]))  # step k - 1's result, read on the host
             ev_comp.record(stream)
             down.wait_event(ev_comp)
@@ -458,7 +458,7 @@ def e2e_steps(qg, md, steps, stream, device, chunks=8):
                     ev_down[c].record(down)
                 dst[n_par + n_state:].copy_(dev_buf[n_par + n_state:], non_blocking=True)
                 ev_res.record(down)
-            if k + 1 < steps:
+            if k + 1 < first + count:
                 up.wait_event(ev_comp)
                 with torch.cuda.stream(up):
                     dev_buf[:n_par].copy_(dst[:n_par], non_blocking=True)
@@ -473,9 +473,18 @@ def e2e_steps(qg, md, steps, stream, device, chunks=8):
                 stream.wait_event(ev_in)
             else:
                 stream.wait_stream(down)
+
+    with torch.cuda.stream(stream):
+        # untimed warm-up: the step graph is captured again for the packed buffer
+        run(0, warmup)
+        torch.cuda.synchronize(device)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        run(warmup, steps)
         t1.record(stream)
         torch.cuda.synchronize(device)
-    totals.append(float(host[steps % 2][e_idx]))
+    totals.append(float(host[(warmup + steps) % 2][e_idx]))
     ms = t0.elapsed_time(t1) / steps
     return {"value": round(1e3 / ms, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 4),

@@ -46,17 +46,18 @@ def test_pipelined_host_round_trip_follows_the_resident_run(chunks):
     rng = np.random.default_rng(4)
     V0 = rng.standard_normal(w.R.shape) * np.sqrt(0.0259 / (w.mass[:, None] * qeq.AMU_A2_FS2_IN_EV))
     V0 -= (w.mass[:, None] * V0).sum(0) / w.mass.sum()
-    steps = 12
+    steps, warm = 12, 2  # the warm-up steps hand their state on to the timed ones
     stream = torch.cuda.Stream()
     s_ref, ref = _md(qg, w, V0)
     s_e2e, e2e = _md(qg, w, V0)
     with torch.cuda.stream(stream):
         ref.init(stream)
         e2e.init(stream)
-        for _ in range(steps):
+        for _ in range(warm + steps):
             ref.step(1, stream)
         stream.synchronize()
-    out = bench.e2e_steps(qg, e2e, steps, stream, torch.device("cuda", 0), chunks=chunks)
+    out = bench.e2e_steps(qg, e2e, steps, stream, torch.device("cuda", 0), chunks=chunks,
+                          warmup=warm)
     assert out["h2d_bytes_per_step"] > 0 and out["d2h_bytes_per_step"] > 0
     torch.cuda.synchronize()
     # the pipelined run's state after its last step: its device buffer (the host
